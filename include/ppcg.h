@@ -1,0 +1,199 @@
+/*
+ * ppcg.h -- C ABI of a single-GPU pipelined preconditioned conjugate gradient solver
+ * for sparse SPD systems A x = b (NVIDIA B300, sm_103a).
+ *
+ * Method: Algorithm 2 (pipelined PCG, Ghysels-Vanroose form) of Tiwari & Vadhiyar,
+ * "Efficient executions of Pipelined Conjugate Gradient Method on Heterogeneous
+ * Architectures", arXiv 2105.06176, Sec. III-B, with the Jacobi preconditioner
+ * M = diag(A) and the CSR input format of Sec. V-A.  Every iteration runs on the GPU:
+ * one fused pass computes n = A M^-1 w for its rows and updates z, q, s, p, x, r, u, w
+ * (lines 10-17 and 21-22 of the algorithm), emitting block partials of gamma = (r, u),
+ * delta = (w, u) and the stopping norm (lines 18-20); alpha and beta (lines 5-9) are
+ * formed on the device, so the host never waits inside a solve.
+ *
+ * Conventions shared by every call:
+ *   - Indices are 0-based.  Matrices are full (not triangular) CSR with int64 row
+ *     pointers, int32 column indices and FP64 values.  Symmetry is assumed, not checked.
+ *   - Pointers marked "host or device" may be either; the library detects which
+ *     (cudaPointerGetAttributes) and stages host data through its own device buffers.
+ *   - Calls that take a cudaStream_t are stream-ordered and asynchronous: argument errors
+ *     are returned immediately; numerical results (ppcg_info) become valid once the stream
+ *     has been synchronised.  A NULL stream means the legacy default stream.
+ *   - A handle is not thread-safe; its solves must be ordered on one stream (or the caller
+ *     must synchronise between streams).  Server calls are thread-safe.
+ *   - The library owns every device buffer it allocates and frees it in the matching
+ *     destroy call.  It never frees caller memory.
+ */
+#ifndef PPCG_H
+#define PPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ppcg_ctx* ppcg_handle;
+typedef struct ppcg_srv* ppcg_server;
+
+typedef enum {
+  PPCG_OK = 0,
+  PPCG_PENDING = 1,            /* ppcg_poll: request not finished yet */
+  PPCG_ERR_ARG = -1,           /* invalid argument (sizes, NULL pointers, unsorted row_ptr, column out of range) */
+  PPCG_ERR_NOT_SPD = -2,       /* a diagonal entry is missing or not positive (Jacobi needs a_ii > 0) */
+  PPCG_ERR_BREAKDOWN = -3,     /* gamma <= 0 or alpha denominator (delta - beta*gamma/alpha_prev) <= 0 */
+  PPCG_ERR_NOT_CONVERGED = -4, /* maxit reached; x holds the last iterate */
+  PPCG_ERR_NONFINITE = -5,     /* gamma or delta became NaN/Inf */
+  PPCG_ERR_OOM = -6,           /* device allocation failed or the server's HBM budget is too small */
+  PPCG_ERR_CUDA = -7,          /* a CUDA runtime call failed (message via ppcg_last_error) */
+  PPCG_ERR_TIMEOUT = -8,       /* a device-side barrier wait exceeded its time limit */
+  PPCG_ERR_BUSY = -9,          /* server queue full */
+  PPCG_ERR_UNKNOWN_TICKET = -10
+} ppcg_status;
+
+typedef enum { PPCG_FP64 = 0, PPCG_FP32_IR = 1 } ppcg_precision;
+typedef enum { PPCG_FMT_AUTO = 0, PPCG_FMT_CSR = 1, PPCG_FMT_SELL = 2 } ppcg_format;
+typedef enum {
+  PPCG_NORM_REL_R = 0,      /* ||r||_2 <= tol * ||b||_2 on the recursive residual, then a true-residual check */
+  PPCG_NORM_PAPER_U_ABS = 1 /* sqrt((u, u)) <= tol, the absolute preconditioned norm of Alg. 2 / Sec. VI */
+} ppcg_norm;
+typedef enum { PPCG_PATH_AUTO = 0, PPCG_PATH_GRID = 1, PPCG_PATH_CLUSTER = 2 } ppcg_path;
+
+/* Solver options.  Obtain defaults with ppcg_opts_default and override fields. */
+typedef struct {
+  int32_t precision;        /* ppcg_precision.  FP32_IR: FP32 matrix values and vectors inside an
+                               FP64 iterative-refinement loop (FP64 outer residual and solution). */
+  int32_t format;           /* ppcg_format.  The matrix is always converted to SELL-C-sigma (C = 32)
+                               on the device; FMT_CSR forces sigma = 1 (CSR row order kept). */
+  int32_t norm;             /* ppcg_norm */
+  int32_t path;             /* ppcg_path.  GRID: one cooperative persistent launch over the whole GPU.
+                               CLUSTER: one thread-block cluster per system.  AUTO picks by size. */
+  int32_t sigma;            /* SELL sorting window in rows (0 = autotune, 1 = no sorting) */
+  int32_t rr_period;        /* residual replacement every rr_period iterations (0 = only when the
+                               recursive residual passes but the true residual does not) */
+  double inner_tol;         /* FP32_IR: relative residual reduction asked of each inner solve */
+  int32_t inner_maxit;      /* FP32_IR: iteration cap of one inner solve */
+  int32_t max_outer;        /* FP32_IR: cap on refinement steps */
+  int64_t spin_limit_ns;    /* time limit of one device-side barrier wait (ns); exceeded -> TIMEOUT */
+  int32_t cluster_max_rows; /* PATH_AUTO: systems with at most this many rows take the CLUSTER path */
+  int32_t reserved[7];
+} ppcg_opts;
+
+/* Per-solve results.  Filled asynchronously; valid after the solve's stream is synchronised. */
+typedef struct {
+  int32_t status;            /* ppcg_status */
+  int32_t iters;             /* iterations of Alg. 2 (executions of the vector-update block); FP32_IR:
+                                summed over inner solves */
+  int32_t outer_iters;       /* FP32_IR refinement steps (0 for FP64) */
+  int32_t rr_count;          /* residual replacements performed */
+  double rel_res_recursive;  /* stopping norm at exit, divided by ||b|| (REL_R) or absolute (PAPER_U_ABS) */
+  double rel_res_true;       /* ||b - A x||_2 / ||b||_2 at exit, FP64 (0 when b = 0) */
+  double seconds;            /* device time of the solve (globaltimer), setup and final residual included */
+  double bytes_per_iter;     /* algorithmic bytes of one iteration: (v+4) nnz + 4 (N+1) + 17 v N */
+  double bnorm;              /* ||b||_2 */
+} ppcg_info;
+
+/* Fill *opts with defaults: FP64, AUTO format/path, REL_R, sigma autotune, rr_period 0,
+ * inner_tol 1e-4, inner_maxit 100000, max_outer 30, spin_limit 10 s, cluster_max_rows 16384. */
+void ppcg_opts_default(ppcg_opts* opts);
+
+/*
+ * Create a solver for the n x n SPD matrix given in CSR (Sec. V-A).
+ *   row_ptr [n+1] int64, col [nnz] int32, val [nnz] FP64: host or device, caller-owned;
+ *   copied during the call, so the caller may free them when it returns.
+ *   opts may be NULL (defaults).  stream orders the conversion work; the call synchronises
+ *   that stream before returning, so the handle is ready to use on any stream.
+ * The matrix is validated (monotone row_ptr, columns in range), the Jacobi diagonal
+ * extracted (missing or non-positive -> PPCG_ERR_NOT_SPD), and the values pre-scaled
+ * column-wise to A D^-1 and converted to SELL-C-sigma on the device.
+ * Errors: PPCG_ERR_ARG, PPCG_ERR_NOT_SPD, PPCG_ERR_OOM, PPCG_ERR_CUDA; *handle is then NULL.
+ */
+ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                        const int32_t* col, const double* val, const ppcg_opts* opts,
+                        cudaStream_t stream);
+
+/*
+ * Solve A x = b with Alg. 2 (Sec. III-B) to the stopping test of opts.norm with tolerance
+ * tol, at most maxit iterations.
+ *   b [n]  host or device, read only.  b = 0 gives x = 0, 0 iterations, PPCG_OK (REL_R).
+ *   x0 [n] host or device initial guess, or NULL for zero.  May alias x.
+ *   x [n]  host or device output.  Written on every outcome except argument errors.
+ *   info   host pointer or NULL; valid after the stream is synchronised.
+ * Returns PPCG_OK when the work was enqueued (numerical status goes to info->status), or
+ * PPCG_ERR_ARG / PPCG_ERR_OOM / PPCG_ERR_CUDA immediately.
+ * With host b/x the call copies through device staging buffers on the stream.
+ */
+ppcg_status ppcg_solve(ppcg_handle handle, const double* b, const double* x0, double* x,
+                       double tol, int32_t maxit, cudaStream_t stream, ppcg_info* info);
+
+/*
+ * Solve count independent systems, each with its own handle, in as few launches as the
+ * handles' paths allow: every CLUSTER-path system runs inside one persistent launch of
+ * thread-block clusters (a host-side longest-first schedule spreads them over the
+ * clusters); GRID-path systems run one after another over the whole GPU.
+ * b[i], x0[i] (or NULL, or x0 == NULL for all zero), x[i]: DEVICE pointers.
+ * tol[i], maxit[i] per system; infos[count] host array or NULL.
+ * Each result is bitwise identical to ppcg_solve on the same handle: a system's
+ * partition over CTAs and its reduction order depend only on its handle.
+ * The handles must be distinct.  Returns after enqueueing; infos valid after stream sync.
+ */
+ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* handles, const double* const* b,
+                             const double* const* x0, double* const* x, const double* tol,
+                             const int32_t* maxit, cudaStream_t stream, ppcg_info* infos);
+
+/* Destroy a handle (synchronises its last stream first).  NULL is ignored. */
+void ppcg_destroy(ppcg_handle handle);
+
+/*
+ * Continuous-batching server.  A background thread admits queued requests while their
+ * device footprint fits in hbm_budget bytes (0 = 90% of free HBM at creation), keeps each
+ * admitted request's vectors and scalars resident on the device, and advances all
+ * resident requests together in epochs of a bounded number of iterations, so requests
+ * that arrive while others run join at the next epoch.  opts may be NULL.
+ */
+ppcg_status ppcg_server_create(ppcg_server* server, size_t hbm_budget, const ppcg_opts* opts);
+
+/*
+ * Queue one solve and return at once with a ticket.  All pointers are HOST pointers
+ * (copied before the call returns): CSR as in ppcg_create, b [n], x0 [n] or NULL.
+ * Errors: PPCG_ERR_ARG, PPCG_ERR_BUSY (queue full), PPCG_ERR_OOM (larger than the budget).
+ */
+ppcg_status ppcg_submit(ppcg_server server, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                        const int32_t* col, const double* val, const double* b, const double* x0,
+                        double tol, int32_t maxit, uint64_t* ticket);
+
+/*
+ * Poll a ticket.  Returns PPCG_PENDING while queued or running; otherwise the solve's
+ * status (also in info->status), copies the solution into x_out [n] (host, may be NULL)
+ * and forgets the ticket.  Unknown tickets -> PPCG_ERR_UNKNOWN_TICKET.
+ */
+ppcg_status ppcg_poll(ppcg_server server, uint64_t ticket, double* x_out, ppcg_info* info);
+
+/* Server counters: completed solves, admitted-but-running, queued, bytes of HBM in use. */
+ppcg_status ppcg_server_stats(ppcg_server server, int64_t* completed, int64_t* running,
+                              int64_t* queued, int64_t* hbm_in_use);
+
+/* Stop the server thread, drop unfinished requests and free everything.  NULL is ignored. */
+void ppcg_server_destroy(ppcg_server server);
+
+/*
+ * Failure-detection self test.  The paper has no counterpart: it checks the bounded wait
+ * of the device-side grid barrier that separates the passes of a GRID-path solve.  Runs
+ * that barrier over `grid` co-resident CTAs (cooperative launch) with CTA `drop_rank`
+ * exiting without arriving; every other CTA must stop waiting after limit_ns and report a
+ * timeout instead of hanging.  Synchronous.  *timed_out receives the number of CTAs that
+ * reported the timeout (grid - 1 when the barrier behaves).  Returns PPCG_OK when the
+ * launch ran, PPCG_ERR_ARG for bad sizes, PPCG_ERR_CUDA on a launch failure.
+ */
+ppcg_status ppcg_selftest_barrier_timeout(int32_t grid, int32_t drop_rank, int64_t limit_ns,
+                                          int32_t* timed_out);
+
+/* Thread-local text of the last error of this thread's calls ("" if none). */
+const char* ppcg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPCG_H */

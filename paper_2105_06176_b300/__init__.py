@@ -1,0 +1,292 @@
+"""Python binding of the pipelined-PCG CUDA library (include/ppcg.h).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams.  There is no CPU fallback: if the compiled
+library (libppcg.so, built for sm_103a by ``build.py``) is missing or cannot be loaded,
+every entry point raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "lib", "Opts", "Info", "Solver", "batch_solve", "Server", "status_name",
+    "OK", "PENDING", "ERR_ARG", "ERR_NOT_SPD", "ERR_BREAKDOWN", "ERR_NOT_CONVERGED",
+    "ERR_NONFINITE", "ERR_OOM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_BUSY", "ERR_UNKNOWN_TICKET",
+    "FP64", "FP32_IR", "NORM_REL_R", "NORM_PAPER_U_ABS", "PATH_AUTO", "PATH_GRID", "PATH_CLUSTER",
+    "FMT_AUTO", "FMT_CSR", "FMT_SELL", "EXPORTED_SYMBOLS",
+]
+
+OK, PENDING, ERR_ARG, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_NOT_CONVERGED = 0, 1, -1, -2, -3, -4
+ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_UNKNOWN_TICKET = -5, -6, -7, -8, -9, -10
+FP64, FP32_IR = 0, 1
+FMT_AUTO, FMT_CSR, FMT_SELL = 0, 1, 2
+NORM_REL_R, NORM_PAPER_U_ABS = 0, 1
+PATH_AUTO, PATH_GRID, PATH_CLUSTER = 0, 1, 2
+
+_NAMES = {OK: "OK", PENDING: "PENDING", ERR_ARG: "ERR_ARG", ERR_NOT_SPD: "ERR_NOT_SPD",
+          ERR_BREAKDOWN: "ERR_BREAKDOWN", ERR_NOT_CONVERGED: "ERR_NOT_CONVERGED",
+          ERR_NONFINITE: "ERR_NONFINITE", ERR_OOM: "ERR_OOM", ERR_CUDA: "ERR_CUDA",
+          ERR_TIMEOUT: "ERR_TIMEOUT", ERR_BUSY: "ERR_BUSY", ERR_UNKNOWN_TICKET: "ERR_UNKNOWN_TICKET"}
+
+# Every symbol include/ppcg.h declares.
+EXPORTED_SYMBOLS = (
+    "ppcg_opts_default", "ppcg_create", "ppcg_solve", "ppcg_batch_solve", "ppcg_destroy",
+    "ppcg_server_create", "ppcg_submit", "ppcg_poll", "ppcg_server_stats", "ppcg_server_destroy",
+    "ppcg_last_error", "ppcg_selftest_barrier_timeout",
+)
+
+
+def status_name(s):
+    return _NAMES.get(int(s), str(s))
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("format", ctypes.c_int32), ("norm", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("sigma", ctypes.c_int32), ("rr_period", ctypes.c_int32),
+                ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int32),
+                ("max_outer", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64),
+                ("cluster_max_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("outer_iters", ctypes.c_int32),
+                ("rr_count", ctypes.c_int32), ("rel_res_recursive", ctypes.c_double),
+                ("rel_res_true", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("bytes_per_iter", ctypes.c_double), ("bnorm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+    def __repr__(self):
+        return f"Info({status_name(self.status)}, " + ", ".join(
+            f"{k}={getattr(self, k)}" for k, _ in self._fields_[1:]) + ")"
+
+
+_lib = None
+P = ctypes.c_void_p
+
+
+def lib(build_if_missing=True):
+    """Load libppcg.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"pipelined-PCG CUDA library not found at {_build.LIB}; run build.py")
+    L = ctypes.CDLL(_build.LIB)
+    L.ppcg_opts_default.argtypes = [ctypes.POINTER(Opts)]
+    L.ppcg_opts_default.restype = None
+    L.ppcg_create.argtypes = [ctypes.POINTER(P), ctypes.c_int64, ctypes.c_int64, P, P, P,
+                              ctypes.POINTER(Opts), P]
+    L.ppcg_create.restype = ctypes.c_int
+    L.ppcg_solve.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_int32, P, ctypes.POINTER(Info)]
+    L.ppcg_solve.restype = ctypes.c_int
+    L.ppcg_batch_solve.argtypes = [ctypes.c_int32, P, P, P, P, P, P, P, P]
+    L.ppcg_batch_solve.restype = ctypes.c_int
+    L.ppcg_destroy.argtypes = [P]
+    L.ppcg_destroy.restype = None
+    L.ppcg_last_error.argtypes = []
+    L.ppcg_last_error.restype = ctypes.c_char_p
+    if hasattr(L, "ppcg_server_create"):
+        L.ppcg_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_size_t, ctypes.POINTER(Opts)]
+        L.ppcg_server_create.restype = ctypes.c_int
+        L.ppcg_submit.argtypes = [P, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, ctypes.c_double,
+                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
+        L.ppcg_submit.restype = ctypes.c_int
+        L.ppcg_poll.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(Info)]
+        L.ppcg_poll.restype = ctypes.c_int
+        L.ppcg_server_stats.argtypes = [P] + [ctypes.POINTER(ctypes.c_int64)] * 4
+        L.ppcg_server_stats.restype = ctypes.c_int
+        L.ppcg_server_destroy.argtypes = [P]
+        L.ppcg_server_destroy.restype = None
+    if hasattr(L, "ppcg_selftest_barrier_timeout"):
+        L.ppcg_selftest_barrier_timeout.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                                    ctypes.POINTER(ctypes.c_int32)]
+        L.ppcg_selftest_barrier_timeout.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def last_error():
+    return lib().ppcg_last_error().decode(errors="replace")
+
+
+class PPCGError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__(f"{where}: {status_name(status)} ({last_error()})")
+        self.status = status
+
+
+def default_opts(**kw):
+    o = Opts()
+    lib().ppcg_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor (host or device) or a numpy array (host)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+class Solver:
+    """One SPD matrix on the GPU (ppcg_create) and its solves (ppcg_solve).
+
+    row_ptr (int64), col (int32), val (float64): numpy arrays or torch tensors, host or
+    device; copied at creation."""
+
+    def __init__(self, n, row_ptr, col, val, opts=None, stream=None, **kw):
+        import torch  # noqa: F401  (CUDA context through torch)
+        self._keep = (row_ptr, col, val)
+        self.n = int(n)
+        self.nnz = int(len(col))
+        o = opts if opts is not None else default_opts(**kw)
+        h = P()
+        st = lib().ppcg_create(ctypes.byref(h), self.n, self.nnz, _ptr(row_ptr), _ptr(col), _ptr(val),
+                               ctypes.byref(o), _stream_ptr(stream))
+        if st != OK:
+            raise PPCGError(st, "ppcg_create")
+        self.handle = h
+        self.opts = o
+        self._keep = None
+
+    @classmethod
+    def from_csr(cls, a, **kw):
+        return cls(a.n, np.ascontiguousarray(a.row_ptr, dtype=np.int64),
+                   np.ascontiguousarray(a.col, dtype=np.int32),
+                   np.ascontiguousarray(a.val, dtype=np.float64), **kw)
+
+    def solve(self, b, x0=None, x=None, tol=1e-8, maxit=10000, stream=None, sync=True):
+        """Enqueue a solve.  b/x0/x: torch tensors (device or host) or numpy arrays.
+        Returns (x, info); info is valid once the stream is synchronised (sync=True does it)."""
+        import torch
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=b.device if hasattr(b, "device") else "cuda")
+        info = Info()
+        s = _stream_ptr(stream)
+        st = lib().ppcg_solve(self.handle, _ptr(b), _ptr(x0), _ptr(x), float(tol), int(maxit), s,
+                              ctypes.byref(info))
+        if st != OK:
+            raise PPCGError(st, "ppcg_solve")
+        if sync:
+            torch.cuda.synchronize()
+        self._last_info = info
+        return x, info
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ppcg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_solve(solvers, bs, xs, x0s=None, tol=1e-8, maxit=10000, stream=None, sync=True):
+    """ppcg_batch_solve over Solver objects with device tensors.  Returns the Info list."""
+    import torch
+    m = len(solvers)
+    H = (P * m)(*[s.handle for s in solvers])
+    B = (P * m)(*[_ptr(b) for b in bs])
+    X = (P * m)(*[_ptr(x) for x in xs])
+    X0 = (P * m)(*[_ptr(x) for x in x0s]) if x0s is not None else None
+    tols = np.ascontiguousarray(np.broadcast_to(np.asarray(tol, dtype=np.float64), (m,)))
+    its = np.ascontiguousarray(np.broadcast_to(np.asarray(maxit, dtype=np.int32), (m,)))
+    infos = (Info * m)()
+    st = lib().ppcg_batch_solve(m, ctypes.cast(H, P), ctypes.cast(B, P),
+                                ctypes.cast(X0, P) if X0 is not None else None, ctypes.cast(X, P),
+                                tols.ctypes.data, its.ctypes.data, _stream_ptr(stream),
+                                ctypes.cast(infos, P))
+    if st != OK:
+        raise PPCGError(st, "ppcg_batch_solve")
+    if sync:
+        torch.cuda.synchronize()
+    return list(infos)
+
+
+class Server:
+    """Continuous-batching server (ppcg_server_*)."""
+
+    def __init__(self, hbm_budget=0, opts=None, **kw):
+        import torch  # noqa: F401
+        o = opts if opts is not None else default_opts(**kw)
+        h = P()
+        st = lib().ppcg_server_create(ctypes.byref(h), int(hbm_budget), ctypes.byref(o))
+        if st != OK:
+            raise PPCGError(st, "ppcg_server_create")
+        self.handle = h
+
+    def submit(self, a, b, x0=None, tol=1e-8, maxit=10000):
+        rp = np.ascontiguousarray(a.row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(a.col, dtype=np.int32)
+        v = np.ascontiguousarray(a.val, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        t = ctypes.c_uint64()
+        st = lib().ppcg_submit(self.handle, a.n, len(ci), rp.ctypes.data, ci.ctypes.data, v.ctypes.data,
+                               b.ctypes.data, None if x0 is None else x0.ctypes.data, float(tol),
+                               int(maxit), ctypes.byref(t))
+        if st != OK:
+            raise PPCGError(st, "ppcg_submit")
+        return t.value
+
+    def poll(self, ticket, n):
+        """Returns (status, x or None, Info)."""
+        x = np.empty(n)
+        info = Info()
+        st = lib().ppcg_poll(self.handle, ticket, x.ctypes.data, ctypes.byref(info))
+        if st == PENDING:
+            return st, None, None
+        return st, x, info
+
+    def stats(self):
+        v = [ctypes.c_int64() for _ in range(4)]
+        st = lib().ppcg_server_stats(self.handle, *[ctypes.byref(t) for t in v])
+        if st != OK:
+            raise PPCGError(st, "ppcg_server_stats")
+        return dict(zip(("completed", "running", "queued", "hbm_in_use"), [t.value for t in v]))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ppcg_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def barrier_timeout_selftest(grid=64, drop_rank=3, limit_ns=50_000_000):
+    """Runs the grid barrier with one CTA that never arrives; returns (status, n_timed_out)."""
+    out = ctypes.c_int32()
+    st = lib().ppcg_selftest_barrier_timeout(grid, drop_rank, limit_ns, ctypes.byref(out))
+    return st, out.value

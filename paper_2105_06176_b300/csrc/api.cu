@@ -1,0 +1,561 @@
+// C ABI of the solver (include/ppcg.h): handles, solve, batch solve.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <queue>
+#include <vector>
+
+#include "internal.h"
+
+namespace ppcg {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+__global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
+                         double* __restrict__ dst) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[perm[i]];
+}
+
+__global__ void k_scatter(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
+                          double* __restrict__ dst) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[perm[i]] = src[i];
+}
+
+__global__ void k_init_ctl(Ctl* c, int32_t state) {
+  Ctl z;
+  memset(&z, 0, sizeof(z));
+  z.state = state;
+  z.last_rr_iter = -1;
+  z.status = PPCG_ERR_NOT_CONVERGED;
+  *c = z;
+}
+
+unsigned blocks_for(int64_t n, int tb) { return (unsigned)((n + tb - 1) / tb); }
+
+// Host-side copy of the device control block + launch error flag (pinned).
+struct Stage {
+  Ctl ctl;
+  int32_t err;
+  int32_t pad;
+};
+
+struct InfoJob {
+  Stage* stage;
+  ppcg_info* info;
+  double bytes_per_iter;
+  int32_t norm;
+  int32_t precision;
+};
+
+void fill_info(const Stage& s, const InfoJob& j, ppcg_info* out) {
+  ppcg_info r;
+  memset(&r, 0, sizeof(r));
+  const Ctl& c = s.ctl;
+  r.status = s.err != 0 ? s.err : c.status;
+  r.iters = c.iter;
+  r.outer_iters = c.outer;
+  r.rr_count = c.rr_count;
+  r.bnorm = c.bnorm;
+  if (j.precision == PPCG_FP32_IR) {
+    r.rel_res_recursive = c.bnorm > 0 ? c.rn / c.bnorm : 0.0;
+  } else {
+    r.rel_res_recursive = j.norm == PPCG_NORM_PAPER_U_ABS ? c.norm : (c.bnorm > 0 ? c.norm / c.bnorm : 0.0);
+  }
+  r.rel_res_true = c.bnorm > 0 ? c.res_true / c.bnorm : 0.0;
+  r.seconds = c.t_end > c.t_start ? (double)(c.t_end - c.t_start) * 1e-9 : 0.0;
+  r.bytes_per_iter = j.bytes_per_iter;
+  *out = r;
+}
+
+void CUDART_CB info_callback(void* p) {
+  std::vector<InfoJob>* jobs = static_cast<std::vector<InfoJob>*>(p);
+  for (const InfoJob& j : *jobs)
+    if (j.info) fill_info(*j.stage, j, j.info);
+  delete jobs;
+}
+
+}  // namespace
+}  // namespace ppcg
+
+using namespace ppcg;
+
+struct ppcg_ctx {
+  int device = 0;
+  int64_t n = 0, nnz = 0;
+  ppcg_opts opts;
+  SellBuild sell;
+  DevMatrix A;
+  int32_t* perm = nullptr;
+  std::vector<void*> allocs;
+  int32_t path = PPCG_PATH_GRID;
+  int grid = 0;        // CTAs of the grid path
+  int nparts = 0;      // partial slots per pass (CTAs in the group)
+  double bytes_per_iter = 0.0;
+  // workspace
+  double *b_ws = nullptr, *x_ws = nullptr, *tmp = nullptr;
+  double* part = nullptr;
+  Ctl* ctl = nullptr;
+  unsigned* bar = nullptr;
+  int32_t* err = nullptr;
+  SysDesc* d_desc = nullptr;
+  SysDesc desc;        // host copy, refreshed per solve
+  Stage* stage = nullptr;   // pinned
+};
+
+namespace {
+
+template <typename T>
+bool walloc(ppcg_ctx* h, T** p, size_t count) {
+  if (cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  h->allocs.push_back(*p);
+  return true;
+}
+
+void free_all(ppcg_ctx* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->stage) cudaFreeHost(h->stage);
+  h->stage = nullptr;
+}
+
+// Enqueue: b/x0 -> solver-order device vectors; fills h->desc pointers for this solve.
+// Returns the device x the solver writes (user x itself when possible).
+ppcg_status stage_inputs(ppcg_ctx* h, const double* b, const double* x0, double* x, bool require_device,
+                         cudaStream_t st, double** x_solver) {
+  const int64_t n = h->n;
+  const size_t bytes = n * sizeof(double);
+  const bool bd = is_device_ptr(b), xd = is_device_ptr(x);
+  const bool x0d = x0 ? is_device_ptr(x0) : true;
+  if (require_device && (!bd || !xd || !x0d)) {
+    set_error("ppcg_batch_solve: b, x0 and x must be device pointers");
+    return PPCG_ERR_ARG;
+  }
+  // b
+  const double* bsol;
+  if (h->perm) {
+    const double* src = b;
+    if (!bd) { cudaMemcpyAsync(h->tmp, b, bytes, cudaMemcpyHostToDevice, st); src = h->tmp; }
+    k_gather<<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, src, h->b_ws);
+    bsol = h->b_ws;
+  } else if (bd) {
+    bsol = b;
+  } else {
+    cudaMemcpyAsync(h->b_ws, b, bytes, cudaMemcpyHostToDevice, st);
+    bsol = h->b_ws;
+  }
+  // x0 -> solver x (in place in the user's x when it is a device buffer and rows are not permuted)
+  double* xs = (!h->perm && xd) ? x : h->x_ws;
+  int32_t x_zero = 0;
+  if (!x0) {
+    cudaMemsetAsync(xs, 0, bytes, st);
+    x_zero = 1;
+  } else if (h->perm) {
+    const double* src = x0;
+    if (!x0d) { cudaMemcpyAsync(h->tmp, x0, bytes, cudaMemcpyHostToDevice, st); src = h->tmp; }
+    k_gather<<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, src, xs);
+  } else if (x0 != xs) {
+    cudaMemcpyAsync(xs, x0, bytes, x0d ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+  }
+  h->desc.b = bsol;
+  h->desc.x = xs;
+  h->desc.x_zero = x_zero;
+  *x_solver = xs;
+  return PPCG_OK;
+}
+
+void stage_outputs(ppcg_ctx* h, double* x, double* xs, cudaStream_t st) {
+  const int64_t n = h->n;
+  const size_t bytes = n * sizeof(double);
+  const bool xd = is_device_ptr(x);
+  if (h->perm) {
+    double* dst = xd ? x : h->tmp;
+    k_scatter<<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, xs, dst);
+    if (!xd) cudaMemcpyAsync(x, h->tmp, bytes, cudaMemcpyDeviceToHost, st);
+  } else if (xs != x) {
+    cudaMemcpyAsync(x, xs, bytes, xd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+  }
+}
+
+void prepare_control(ppcg_ctx* h, double tol, int32_t maxit, cudaStream_t st) {
+  h->desc.tol = tol;
+  h->desc.maxit = maxit;
+  k_init_ctl<<<1, 1, 0, st>>>(h->ctl, h->opts.precision == PPCG_FP32_IR ? S_O_START : S_START);
+  cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
+}
+
+void enqueue_info(std::vector<std::pair<ppcg_ctx*, ppcg_info*>>& items, cudaStream_t st) {
+  auto* jobs = new std::vector<InfoJob>();
+  for (auto& it : items) {
+    ppcg_ctx* h = it.first;
+    cudaMemcpyAsync(&h->stage->ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&h->stage->err, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    jobs->push_back({h->stage, it.second, h->bytes_per_iter, h->opts.norm, h->opts.precision});
+  }
+  if (cudaLaunchHostFunc(st, info_callback, jobs) != cudaSuccess) {
+    cudaGetLastError();
+    delete jobs;
+  }
+}
+
+bool check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return false;
+  }
+  return true;
+}
+
+void write_trivial_info(ppcg_info* info, int32_t status) {
+  if (!info) return;
+  memset(info, 0, sizeof(*info));
+  info->status = status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ppcg_opts_default(ppcg_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = PPCG_FP64;
+  o->format = PPCG_FMT_AUTO;
+  o->norm = PPCG_NORM_REL_R;
+  o->path = PPCG_PATH_AUTO;
+  o->sigma = 0;
+  o->rr_period = 0;
+  o->inner_tol = 1e-4;
+  o->inner_maxit = 100000;
+  o->max_outer = 30;
+  o->spin_limit_ns = 10000000000LL;
+  o->cluster_max_rows = 16384;
+}
+
+const char* ppcg_last_error(void) { return g_err; }
+
+ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                        const int32_t* col, const double* val, const ppcg_opts* opts,
+                        cudaStream_t stream) {
+  g_err[0] = 0;
+  if (!handle) { set_error("ppcg_create: handle is NULL"); return PPCG_ERR_ARG; }
+  *handle = nullptr;
+  if (n < 0 || nnz < 0 || n > INT32_MAX || (n > 0 && (!row_ptr || !col || !val || nnz < n))) {
+    set_error("ppcg_create: bad sizes or NULL arrays (n=%lld nnz=%lld)", (long long)n, (long long)nnz);
+    return PPCG_ERR_ARG;
+  }
+  ppcg_ctx* h = new ppcg_ctx();
+  ppcg_opts_default(&h->opts);
+  if (opts) h->opts = *opts;
+  if (h->opts.precision != PPCG_FP64 && h->opts.precision != PPCG_FP32_IR) { delete h; set_error("ppcg_create: bad precision"); return PPCG_ERR_ARG; }
+  if (h->opts.norm != PPCG_NORM_REL_R && h->opts.norm != PPCG_NORM_PAPER_U_ABS) { delete h; set_error("ppcg_create: bad norm"); return PPCG_ERR_ARG; }
+  if (h->opts.spin_limit_ns <= 0) h->opts.spin_limit_ns = 10000000000LL;
+  if (h->opts.inner_maxit <= 0) h->opts.inner_maxit = 100000;
+  if (h->opts.max_outer <= 0) h->opts.max_outer = 30;
+  if (!(h->opts.inner_tol > 0.0 && h->opts.inner_tol < 1.0)) h->opts.inner_tol = 1e-4;
+  cudaGetDevice(&h->device);
+  h->n = n;
+  h->nnz = nnz;
+  memset(&h->A, 0, sizeof(h->A));
+  memset(&h->desc, 0, sizeof(h->desc));
+  if (n == 0) { *handle = h; return PPCG_OK; }
+
+  // Bring the CSR to the device (temporary copies when it lives on the host).
+  std::vector<void*> tmp;
+  auto free_tmp = [&]() { for (void* p : tmp) cudaFree(p); tmp.clear(); };
+  const int64_t* d_rp = row_ptr;
+  const int32_t* d_col = col;
+  const double* d_val = val;
+  auto upload = [&](const void* src, size_t bytes, const void** dst) -> bool {
+    if (is_device_ptr(src)) { *dst = src; return true; }
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 1)) != cudaSuccess) { cudaGetLastError(); return false; }
+    tmp.push_back(p);
+    if (cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) { cudaGetLastError(); return false; }
+    *dst = p;
+    return true;
+  };
+  if (!upload(row_ptr, (n + 1) * sizeof(int64_t), (const void**)&d_rp) ||
+      !upload(col, nnz * sizeof(int32_t), (const void**)&d_col) ||
+      !upload(val, nnz * sizeof(double), (const void**)&d_val)) {
+    free_tmp();
+    delete h;
+    set_error("ppcg_create: could not stage the CSR arrays on the device");
+    return PPCG_ERR_OOM;
+  }
+  int32_t sigma = h->opts.format == PPCG_FMT_CSR ? 1 : h->opts.sigma;
+  ppcg_status s = convert_csr_to_sell(n, nnz, d_rp, d_col, d_val, sigma, h->opts.precision == PPCG_FP32_IR,
+                                      stream, h->allocs, &h->sell, &h->A, &h->perm);
+  free_tmp();
+  if (s != PPCG_OK) { free_all(h); delete h; return s; }
+
+  // Execution plan (fixed for the handle, so every solve of it uses the same partition).
+  int path = h->opts.path;
+  if (path == PPCG_PATH_AUTO) path = n <= h->opts.cluster_max_rows ? PPCG_PATH_CLUSTER : PPCG_PATH_GRID;
+  h->path = path;
+  if (path == PPCG_PATH_GRID) {
+    h->grid = grid_blocks_for_device(h->device);
+    h->nparts = h->grid;
+  } else {
+    h->grid = kClusterSize;
+    h->nparts = kClusterSize;
+  }
+  const bool fp32 = h->opts.precision == PPCG_FP32_IR;
+  const double v = fp32 ? 4.0 : 8.0;
+  h->bytes_per_iter = (v + 4.0) * (double)nnz + 4.0 * (double)(n + 1) + 17.0 * v * (double)n;
+
+  // Workspace.
+  SysDesc& d = h->desc;
+  bool ok = walloc(h, &h->b_ws, n) && walloc(h, &h->x_ws, n) && walloc(h, &h->tmp, n) &&
+            walloc(h, &d.r, n) && walloc(h, &h->part, 2 * (size_t)h->nparts * 4) &&
+            walloc(h, &h->ctl, 1) && walloc(h, &h->bar, 1) && walloc(h, &h->err, 1) &&
+            walloc(h, &h->d_desc, 1);
+  if (ok && !fp32)
+    ok = walloc(h, &d.u, n) && walloc(h, &d.w0, n) && walloc(h, &d.w1, n) && walloc(h, &d.z, n) &&
+         walloc(h, &d.q, n) && walloc(h, &d.s, n) && walloc(h, &d.p, n);
+  if (ok && fp32)
+    ok = walloc(h, &d.r32, n) && walloc(h, &d.u32, n) && walloc(h, &d.w32a, n) && walloc(h, &d.w32b, n) &&
+         walloc(h, &d.z32, n) && walloc(h, &d.q32, n) && walloc(h, &d.s32, n) && walloc(h, &d.p32, n) &&
+         walloc(h, &d.d32, n) && walloc(h, &d.rhs32, n);
+  if (ok && cudaMallocHost((void**)&h->stage, sizeof(Stage)) != cudaSuccess) { cudaGetLastError(); ok = false; }
+  if (!ok) {
+    free_all(h);
+    delete h;
+    set_error("ppcg_create: out of device memory for the workspace");
+    return PPCG_ERR_OOM;
+  }
+  memset(h->stage, 0, sizeof(Stage));
+  d.A = h->A;
+  d.precision = h->opts.precision;
+  d.norm = h->opts.norm;
+  d.rr_period = h->opts.rr_period;
+  d.inner_maxit = h->opts.inner_maxit;
+  d.max_outer = h->opts.max_outer;
+  d.inner_tol = h->opts.inner_tol;
+  d.spin_limit_ns = h->opts.spin_limit_ns;
+  d.nparts = h->nparts;
+  d.part = h->part;
+  d.ctl = h->ctl;
+  d.bar = h->bar;
+  d.err = h->err;
+  *handle = h;
+  return PPCG_OK;
+}
+
+ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double* x, double tol,
+                       int32_t maxit, cudaStream_t st, ppcg_info* info) {
+  g_err[0] = 0;
+  if (!h) { set_error("ppcg_solve: NULL handle"); return PPCG_ERR_ARG; }
+  if (!(tol >= 0.0) || maxit < 0 || (h->n > 0 && (!b || !x))) {
+    set_error("ppcg_solve: bad arguments (tol=%g maxit=%d)", tol, maxit);
+    return PPCG_ERR_ARG;
+  }
+  if (h->n == 0) { write_trivial_info(info, PPCG_OK); return PPCG_OK; }
+  double* xs = nullptr;
+  ppcg_status s = stage_inputs(h, b, x0, x, false, st, &xs);
+  if (s != PPCG_OK) return s;
+  prepare_control(h, tol, maxit, st);
+  cudaMemcpyAsync(h->d_desc, &h->desc, sizeof(SysDesc), cudaMemcpyHostToDevice, st);
+  cudaError_t e;
+  if (h->path == PPCG_PATH_GRID) {
+    e = launch_grid(h->d_desc, h->grid, 0, st);
+  } else {
+    // one cluster, work list {0}: device array {0, 0, 1} = list[0], list_ptr[0..1]
+    static int32_t* d_list = nullptr;
+    static std::mutex mu;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!d_list) {
+        const int32_t host[3] = {0, 0, 1};
+        if (cudaMalloc(&d_list, sizeof(host)) != cudaSuccess ||
+            cudaMemcpy(d_list, host, sizeof(host), cudaMemcpyHostToDevice) != cudaSuccess) {
+          cudaGetLastError();
+          d_list = nullptr;
+          set_error("ppcg_solve: could not allocate the cluster work list");
+          return PPCG_ERR_OOM;
+        }
+      }
+    }
+    e = launch_clusters(h->d_desc, d_list, d_list + 1, 1, 0, st);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("ppcg_solve: launch failed: %s", cudaGetErrorString(e));
+    return PPCG_ERR_CUDA;
+  }
+  stage_outputs(h, x, xs, st);
+  std::vector<std::pair<ppcg_ctx*, ppcg_info*>> items{{h, info}};
+  enqueue_info(items, st);
+  return check_launch("ppcg_solve") ? PPCG_OK : PPCG_ERR_CUDA;
+}
+
+ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double* const* b,
+                             const double* const* x0, double* const* x, const double* tol,
+                             const int32_t* maxit, cudaStream_t st, ppcg_info* infos) {
+  g_err[0] = 0;
+  if (count < 0 || (count > 0 && (!hs || !b || !x || !tol || !maxit))) {
+    set_error("ppcg_batch_solve: bad arguments");
+    return PPCG_ERR_ARG;
+  }
+  for (int i = 0; i < count; i++) {
+    if (!hs[i] || !(tol[i] >= 0.0) || maxit[i] < 0 || (hs[i]->n > 0 && (!b[i] || !x[i]))) {
+      set_error("ppcg_batch_solve: bad arguments for system %d", i);
+      return PPCG_ERR_ARG;
+    }
+    for (int j = 0; j < i; j++)
+      if (hs[j] == hs[i]) { set_error("ppcg_batch_solve: handle %d repeated", i); return PPCG_ERR_ARG; }
+  }
+  std::vector<int> cl, gr;
+  std::vector<double*> xsol(count, nullptr);
+  for (int i = 0; i < count; i++) {
+    ppcg_ctx* h = hs[i];
+    if (h->n == 0) { if (infos) write_trivial_info(&infos[i], PPCG_OK); continue; }
+    ppcg_status s = stage_inputs(h, b[i], x0 ? x0[i] : nullptr, x[i], true, st, &xsol[i]);
+    if (s != PPCG_OK) return s;
+    prepare_control(h, tol[i], maxit[i], st);
+    (h->path == PPCG_PATH_CLUSTER ? cl : gr).push_back(i);
+  }
+  // Cluster-path systems: one persistent launch; longest-first schedule over the clusters.
+  if (!cl.empty()) {
+    const int m = (int)cl.size();
+    std::vector<SysDesc> descs(m);
+    std::vector<double> cost(m);
+    for (int k = 0; k < m; k++) {
+      descs[k] = hs[cl[k]]->desc;
+      const double n = (double)hs[cl[k]]->n;
+      cost[k] = (double)hs[cl[k]]->sell.nslots * std::pow(n, 0.4);
+    }
+    int nclusters = std::min(m, max_active_clusters(hs[cl[0]]->device));
+    std::vector<int> order(m);
+    for (int k = 0; k < m; k++) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    std::vector<std::vector<int>> lists(nclusters);
+    std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> pq;
+    for (int c = 0; c < nclusters; c++) pq.push({0.0, c});
+    for (int k : order) {
+      auto top = pq.top();
+      pq.pop();
+      lists[top.second].push_back(k);
+      pq.push({top.first + cost[k], top.second});
+    }
+    std::vector<int32_t> flat, ptr(1, 0);
+    for (auto& l : lists) { for (int k : l) flat.push_back(k); ptr.push_back((int32_t)flat.size()); }
+    std::vector<int32_t> packed(ptr);
+    packed.insert(packed.end(), flat.begin(), flat.end());
+    SysDesc* d_descs = nullptr;
+    int32_t* d_lists = nullptr;
+    if (cudaMallocAsync((void**)&d_descs, m * sizeof(SysDesc), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&d_lists, packed.size() * sizeof(int32_t), st) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("ppcg_batch_solve: out of device memory for the schedule");
+      return PPCG_ERR_OOM;
+    }
+    cudaMemcpyAsync(d_descs, descs.data(), m * sizeof(SysDesc), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_lists, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    cudaError_t e = launch_clusters(d_descs, d_lists + ptr.size(), d_lists, nclusters, 0, st);
+    cudaFreeAsync(d_descs, st);
+    cudaFreeAsync(d_lists, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("ppcg_batch_solve: cluster launch failed: %s", cudaGetErrorString(e));
+      return PPCG_ERR_CUDA;
+    }
+  }
+  // Grid-path systems: one whole-GPU launch each.
+  for (int i : gr) {
+    ppcg_ctx* h = hs[i];
+    cudaMemcpyAsync(h->d_desc, &h->desc, sizeof(SysDesc), cudaMemcpyHostToDevice, st);
+    cudaError_t e = launch_grid(h->d_desc, h->grid, 0, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("ppcg_batch_solve: launch failed: %s", cudaGetErrorString(e));
+      return PPCG_ERR_CUDA;
+    }
+  }
+  std::vector<std::pair<ppcg_ctx*, ppcg_info*>> items;
+  for (int i = 0; i < count; i++) {
+    if (hs[i]->n == 0) continue;
+    stage_outputs(hs[i], x[i], xsol[i], st);
+    items.push_back({hs[i], infos ? &infos[i] : nullptr});
+  }
+  if (!items.empty()) enqueue_info(items, st);
+  return check_launch("ppcg_batch_solve") ? PPCG_OK : PPCG_ERR_CUDA;
+}
+
+ppcg_status ppcg_selftest_barrier_timeout(int32_t grid, int32_t drop_rank, int64_t limit_ns,
+                                          int32_t* timed_out) {
+  g_err[0] = 0;
+  if (grid < 2 || grid > 4096 || drop_rank < 0 || drop_rank >= grid || limit_ns <= 0 || !timed_out) {
+    set_error("ppcg_selftest_barrier_timeout: bad arguments");
+    return PPCG_ERR_ARG;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (grid > sms) grid = sms;   // one CTA per SM keeps the cooperative launch valid
+  if (drop_rank >= grid) drop_rank = grid - 1;
+  unsigned* bar = nullptr;
+  int32_t* err = nullptr;
+  int32_t* out = nullptr;
+  if (cudaMalloc(&bar, sizeof(unsigned)) != cudaSuccess || cudaMalloc(&err, sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&out, grid * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(bar); cudaFree(err); cudaFree(out);
+    set_error("ppcg_selftest_barrier_timeout: out of device memory");
+    return PPCG_ERR_OOM;
+  }
+  cudaMemset(bar, 0, sizeof(unsigned));
+  cudaMemset(err, 0, sizeof(int32_t));
+  cudaMemset(out, 0xff, grid * sizeof(int32_t));
+  cudaError_t e = launch_barrier_selftest(bar, err, out, grid, drop_rank, limit_ns, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  std::vector<int32_t> h(grid);
+  if (e == cudaSuccess) e = cudaMemcpy(h.data(), out, grid * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  cudaFree(bar); cudaFree(err); cudaFree(out);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("ppcg_selftest_barrier_timeout: %s", cudaGetErrorString(e));
+    return PPCG_ERR_CUDA;
+  }
+  int32_t n = 0;
+  for (int i = 0; i < grid; i++) n += (i != drop_rank && h[i] == 0);
+  *timed_out = n;
+  return PPCG_OK;
+}
+
+void ppcg_destroy(ppcg_handle h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+#include <cstdint>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/ppcg.h"
+
+namespace ppcg {
+
+constexpr int kChunk = 32;           // SELL-C-sigma chunk height C: one warp lane per row
+constexpr int kGridThreads = 512;    // CTA size of the whole-GPU (grid) path
+constexpr int kClusterThreads = 256; // CTA size of the cluster path
+constexpr int kClusterSize = 8;      // CTAs per thread-block cluster (portable maximum)
+
+// SELL-C-sigma matrix in the solver's row order (rows permuted within sigma windows when
+// sigma > 1; columns renumbered with the same permutation).  Values are A D^-1.
+struct DevMatrix {
+  int64_t n;
+  int64_t nchunks;
+  int64_t nslots;
+  const int64_t* cptr;   // [nchunks + 1] slot offset of each chunk (multiple of 32)
+  const int32_t* col;    // [nslots] column-major within a chunk: slot(base + j*32 + lane)
+  const double* val;     // [nslots] a_ij / a_jj
+  const float* val32;    // [nslots] same rounded to FP32 (FP32_IR only)
+  const double* invd;    // [n] 1 / a_ii
+  const float* invd32;   // [n]
+  const double* diag;    // [n] a_ii
+  const float* diag32;   // [n]
+};
+
+// Passes the device state machine can run (one parallel sweep over the rows each).
+enum Pass : int32_t {
+  P_NONE = 0,
+  P_SETUP1,    // r = b - A x ; u = M^-1 r ; partials (b,b) (r,r)
+  P_SETUP2,    // w = A u (= Ahat r) ; partials (r,u) (w,u) norm
+  P_ITER,      // fused iteration: n = Ahat w ; z q s p x r u w update ; partials
+  P_TRUE,      // partial ||b - A x||^2
+  P_RR1,       // r = b - A x ; u = M^-1 r ; s = A p ; q = M^-1 s
+  P_RR2,       // w = Ahat r ; z = Ahat s ; partials
+  P_ZERO_X,    // x = 0
+  P_ORES,      // FP32_IR: r64 = b - A x (FP64) ; partials (r64,r64) (b,b)
+  P_OINIT,     // FP32_IR: rhs32 = r64 / ||r64|| ; r32 = rhs32 ; u32 = M^-1 r32 ; d32 = 0
+  P_OUPD,      // FP32_IR: x += ||r64|| * d32
+};
+
+// Control states (see solver.cuh: control()).
+enum State : int32_t {
+  S_START = 0, S_AFTER_SETUP1, S_AFTER_SETUP2, S_TOP, S_AFTER_ITER, S_AFTER_TRUE, S_AFTER_RR1,
+  S_AFTER_RR2, S_FINAL, S_AFTER_FINAL, S_DONE,
+  S_O_START, S_O_AFTER_ORES, S_O_AFTER_ZERO, S_O_AFTER_OINIT, S_I_AFTER_SETUP2, S_I_TOP,
+  S_I_AFTER_ITER, S_I_AFTER_RR1, S_I_AFTER_RR2, S_O_AFTER_OUPD,
+};
+
+// Device-resident control block of one solve.  Read by every CTA at launch start, written
+// back by rank 0 at launch end, so a solve can be resumed by a later launch.
+struct Ctl {
+  int32_t state, pass, status, iter;      // iter: Alg. 2 iterations (inner ones for FP32_IR)
+  int32_t inner_iter, outer, rr_count, last_rr_iter;
+  int32_t parity, first, exit_now, pad;
+  double gamma, gamma_prev, delta, alpha, alpha_prev, beta, norm;
+  double bnorm, rn, rn_prev, res_true, inner_norm0, inner_target;
+  unsigned long long t_start, t_end;
+  double red[4];                           // reduced partials of the last pass
+};
+
+struct SysDesc {
+  DevMatrix A;
+  int32_t precision, norm, rr_period, maxit;
+  int32_t inner_maxit, max_outer, nparts, x_zero;  // x_zero: x starts at 0 (skip the A x0 gather)
+  double tol, inner_tol;
+  int64_t spin_limit_ns;
+  const double* b;       // solver order
+  double* x;             // solver order (FP64 solution, holds x0 at start)
+  // FP64 Krylov vectors (FP64 path) -- r also serves as r64 in FP32_IR
+  double *r, *u, *w0, *w1, *z, *q, *s, *p;
+  // FP32 Krylov vectors (FP32_IR inner solve)
+  float *r32, *u32, *w32a, *w32b, *z32, *q32, *s32, *p32, *d32, *rhs32;
+  double* part;          // [2][nparts][4] block partials, double-buffered by pass parity
+  Ctl* ctl;
+  unsigned* bar;         // grid barrier arrival counter (grid path; zeroed before each launch)
+  int32_t* err;          // launch error flag (timeout), zeroed before each launch
+};
+
+// Launchers (solver.cu)
+cudaError_t launch_grid(const SysDesc* d_desc, int grid, int budget, cudaStream_t st);
+cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
+                            int nclusters, int budget, cudaStream_t st);
+int grid_blocks_for_device(int device);
+int max_active_clusters(int device);
+cudaError_t launch_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, int grid,
+                                    int drop_rank, int64_t limit_ns, cudaStream_t st);
+
+// Conversion (convert.cu)
+struct SellBuild {
+  int64_t nchunks = 0, nslots = 0;
+  int32_t sigma = 1;
+  double padding = 0.0;   // (nslots - nnz) / nnz
+  double seconds = 0.0;   // conversion wall time
+};
+ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col,
+                                const double* d_val, int32_t sigma_req, bool want_fp32,
+                                cudaStream_t st, std::vector<void*>& allocs, SellBuild* out,
+                                DevMatrix* A, int32_t** d_perm_out);
+
+void set_error(const char* fmt, ...);
+
+}  // namespace ppcg

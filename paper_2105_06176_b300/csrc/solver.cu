@@ -1,0 +1,747 @@
+// Device side of the pipelined PCG solver: Algorithm 2 of Tiwari & Vadhiyar (arXiv
+// 2105.06176, Sec. III-B) with the Jacobi preconditioner (Sec. V-A), run as a resumable
+// state machine inside one persistent launch.
+//
+// Every CTA of a group (the whole grid, or one thread-block cluster) runs the same control
+// logic on the same reduced scalars, so all CTAs take the same branch with no broadcast.
+// One "pass" is one sweep over the system's rows in SELL-C-sigma order (one warp per
+// 32-row chunk, one lane per row); passes are separated by a group barrier.  The hot pass,
+// P_ITER, is the whole iteration of Alg. 2 for its rows:
+//     n_i  = A M^-1 w_i  = Ahat w_i                    (lines 21-22 of the previous step)
+//     z = n + beta z;  q = m + beta q;  s = w + beta s;  p = u + beta p     (lines 10-13)
+//     x += alpha p;    r -= alpha s;    u -= alpha q;    w -= alpha z       (lines 14-17)
+//     block partials of (r,u), (w,u) and the stopping norm                  (lines 18-20)
+// with w double-buffered (other CTAs still gather the old w), and alpha/beta (lines 5-9)
+// formed after the barrier from the partials in a fixed order.
+#include <cstdio>
+
+#include "internal.h"
+
+namespace ppcg {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// ---------------------------------------------------------------------------- groups --
+
+// Whole-grid group (cooperative launch: all CTAs are co-resident).  The barrier is a
+// monotone arrival counter zeroed before the launch; each wait is bounded in time.
+struct GridGroup {
+  unsigned* bar;
+  int32_t* err;
+  long long limit_ns;
+  unsigned epoch;
+  __device__ int rank() const { return blockIdx.x; }
+  __device__ int size() const { return gridDim.x; }
+  __device__ bool sync() {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int good = 1;
+      epoch++;
+      const unsigned target = epoch * gridDim.x;
+      __threadfence();
+      atomicAdd(bar, 1u);
+      const unsigned long long t0 = globaltimer();
+      unsigned spins = 0;
+      for (;;) {
+        unsigned v = ld_acquire_gpu(bar);
+        if ((int)(v - target) >= 0) break;
+        if (*(volatile int32_t*)err != 0) { good = 0; break; }
+        if ((++spins & 63u) == 0 && (long long)(globaltimer() - t0) > limit_ns) {
+          atomicCAS(err, 0, (int32_t)PPCG_ERR_TIMEOUT);
+          good = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+      __threadfence();
+      ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+  }
+};
+
+// One thread-block cluster.  barrier.cluster with release/acquire orders the global
+// writes of each pass before the next pass's gathers (which use ld.global.cg, L2).
+struct ClusterGroup {
+  __device__ int rank() const {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+  }
+  __device__ int size() const {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return (int)r;
+  }
+  __device__ bool sync() {
+    __syncthreads();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    return true;
+  }
+};
+
+// ---------------------------------------------------------------- dot accumulators --
+
+template <typename T> struct Dots;
+
+template <> struct Dots<double> {
+  double a[3] = {0.0, 0.0, 0.0};
+  __device__ __forceinline__ void add(int k, double x, double y) { a[k] = fma(x, y, a[k]); }
+  __device__ __forceinline__ double get(int k) const { return a[k]; }
+};
+
+// FP32 vectors: products are formed exactly as a float pair (TwoProduct with FMA, Ogita,
+// Rump & Oishi 2005) and summed in double-float with Knuth's TwoSum, so the per-thread
+// partials keep ~48 significant bits on the FP32 pipe; they are converted to FP64 once per
+// thread and reduced in FP64 from there on.
+template <> struct Dots<float> {
+  float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+  __device__ __forceinline__ void add(int k, float x, float y) {
+    float p = __fmul_rn(x, y);
+    float e = __fmaf_rn(x, y, -p);
+    float s = __fadd_rn(hi[k], p);
+    float bb = __fsub_rn(s, hi[k]);
+    float t = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi[k] = s;
+    lo[k] = __fadd_rn(lo[k], __fadd_rn(t, e));
+  }
+  __device__ __forceinline__ double get(int k) const { return (double)hi[k] + (double)lo[k]; }
+};
+
+// --------------------------------------------------------------------- loads/stores --
+
+template <typename T> __device__ __forceinline__ T ldcs(const T* p) { return __ldcs(p); }
+template <typename T> __device__ __forceinline__ void stcs(T* p, T v) { __stcs(p, v); }
+template <typename T> __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+
+// sum_j val[slot_j] * x[col[slot_j]] (* dsc[col] when SCALE), slots base + j*32, j < len,
+// accumulated in slot order (the CSR order of the row).  Gathers use ld.global.cg: the
+// gathered vector was written by other CTAs in the previous pass.
+template <typename T, bool SCALE>
+__device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* __restrict__ val,
+                                     const T* x, const T* __restrict__ dsc, int64_t base, int len) {
+  T acc = T(0);
+  int j = 0;
+  for (; j + 8 <= len; j += 8) {
+    int32_t c[8];
+    T a[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      c[k] = __ldg(col + base + (int64_t)(j + k) * kChunk);
+      a[k] = __ldg(val + base + (int64_t)(j + k) * kChunk);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      T xv = ldcg(x + c[k]);
+      if (SCALE) xv = __ldg(dsc + c[k]) * xv;
+      acc = fma(a[k], xv, acc);
+    }
+  }
+  int32_t c[7];
+  T a[7];
+#pragma unroll
+  for (int k = 0; k < 7; k++) {
+    if (j + k < len) {
+      c[k] = __ldg(col + base + (int64_t)(j + k) * kChunk);
+      a[k] = __ldg(val + base + (int64_t)(j + k) * kChunk);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 7; k++) {
+    if (j + k < len) {
+      T xv = ldcg(x + c[k]);
+      if (SCALE) xv = __ldg(dsc + c[k]) * xv;
+      acc = fma(a[k], xv, acc);
+    }
+  }
+  return acc;
+}
+
+// Per-precision view of the Krylov vectors and matrix arrays.
+template <typename T> struct Vec {
+  const T* val; const T* invd; const T* diag; const T* rhs;
+  T* xs; T *r, *u, *wa, *wb, *z, *q, *s, *p;
+};
+
+__device__ __forceinline__ Vec<double> vec64(const SysDesc& S) {
+  return {S.A.val, S.A.invd, S.A.diag, S.b, S.x, S.r, S.u, S.w0, S.w1, S.z, S.q, S.s, S.p};
+}
+__device__ __forceinline__ Vec<float> vec32(const SysDesc& S) {
+  return {S.A.val32, S.A.invd32, S.A.diag32, S.rhs32, S.d32, S.r32, S.u32, S.w32a, S.w32b,
+          S.z32, S.q32, S.s32, S.p32};
+}
+
+struct Lanes {
+  int64_t gw, W;   // global warp id within the group, warps in the group
+  int lane;
+};
+
+#define FOR_CHUNKS(A, L)                                                               \
+  for (int64_t c = (L).gw; c < (A).nchunks; c += (L).W)
+
+__device__ __forceinline__ void chunk_range(const DevMatrix& A, int64_t c, int lane, int64_t& base,
+                                            int& len) {
+  int64_t b0 = __ldg(A.cptr + c);
+  len = (int)((__ldg(A.cptr + c + 1) - b0) / kChunk);
+  base = b0 + lane;
+}
+
+// -------------------------------------------------------------------------- passes --
+
+// P_SETUP1 (FP64), Alg. 2 line 1: r0 = b - A x0 ; u0 = M^-1 r0.  Partials (b,b), (r,r).
+__device__ __noinline__ void pass_setup1(const SysDesc& S, const Lanes& L, Dots<double>& d, bool x_zero) {
+  const DevMatrix& A = S.A;
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_range(A, c, L.lane, base, len);
+    int64_t row = c * kChunk + L.lane;
+    double ax = 0.0;
+    if (!x_zero) ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len);
+    if (row < A.n) {
+      double bi = __ldg(S.b + row);
+      double ri = bi - ax;
+      double ui = __ldg(A.invd + row) * ri;
+      stcs(S.r + row, ri);
+      stcs(S.u + row, ui);
+      d.add(0, bi, bi);
+      d.add(1, ri, ri);
+    }
+  }
+}
+
+// P_SETUP2, Alg. 2 lines 1-2: w0 = A u0 (= Ahat r0) ; partials (r,u), (w,u), norm.
+template <typename T>
+__device__ __noinline__ void pass_setup2(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d,
+                            bool paper_norm) {
+  const T* val = v.val;
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_range(A, c, L.lane, base, len);
+    int64_t row = c * kChunk + L.lane;
+    T wi = row_dot<T, false>(A.col, val, v.r, nullptr, base, len);
+    if (row < A.n) {
+      T ri = ldcs(v.r + row), ui = ldcs(v.u + row);
+      stcs(v.wa + row, wi);
+      d.add(0, ri, ui);
+      d.add(1, wi, ui);
+      if (paper_norm) d.add(2, ui, ui); else d.add(2, ri, ri);
+    }
+  }
+}
+
+// P_ITER: one full iteration of Alg. 2 for the group's rows (see the file comment).
+template <typename T>
+__device__ __noinline__ void pass_iter(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d, T alpha,
+                          T beta, bool first, int k, bool paper_norm) {
+  const T* wc = (k & 1) ? v.wb : v.wa;
+  T* wn = (k & 1) ? v.wa : v.wb;
+  const T* val = v.val;
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_range(A, c, L.lane, base, len);
+    int64_t row = c * kChunk + L.lane;
+    T ni = row_dot<T, false>(A.col, val, wc, nullptr, base, len);
+    if (row < A.n) {
+      T wi = ldcg(wc + row);
+      T mi = __ldg(v.invd + row) * wi;
+      T ui = ldcs(v.u + row);
+      T xi = ldcs(v.xs + row);
+      T ri = ldcs(v.r + row);
+      T zi = ni, qi = mi, si = wi, pi = ui;
+      if (!first) {
+        zi = fma(beta, ldcs(v.z + row), ni);
+        qi = fma(beta, ldcs(v.q + row), mi);
+        si = fma(beta, ldcs(v.s + row), wi);
+        pi = fma(beta, ldcs(v.p + row), ui);
+      }
+      xi = fma(alpha, pi, xi);
+      ri = fma(-alpha, si, ri);
+      T un = fma(-alpha, qi, ui);
+      T wnn = fma(-alpha, zi, wi);
+      stcs(v.z + row, zi);
+      stcs(v.q + row, qi);
+      stcs(v.s + row, si);
+      stcs(v.p + row, pi);
+      stcs(v.xs + row, xi);
+      stcs(v.r + row, ri);
+      stcs(v.u + row, un);
+      stcs(wn + row, wnn);
+      d.add(0, ri, un);
+      d.add(1, wnn, un);
+      if (paper_norm) d.add(2, un, un); else d.add(2, ri, ri);
+    }
+  }
+}
+
+// P_TRUE (FP64): partial ||b - A x||^2.
+__device__ __noinline__ void pass_true(const SysDesc& S, const Lanes& L, Dots<double>& d) {
+  const DevMatrix& A = S.A;
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_range(A, c, L.lane, base, len);
+    int64_t row = c * kChunk + L.lane;
+    double ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len);
+    if (row < A.n) {
+      double t = __ldg(S.b + row) - ax;
+      d.add(0, t, t);
+    }
+  }
+}
+
+// P_RR1: residual replacement, first half: r = rhs - A xs ; u = M^-1 r ; s = A p ; q = M^-1 s.
+// (At iteration 0 p is zero, so s = q = 0.)
+template <typename T>
+__device__ __noinline__ void pass_rr1(const DevMatrix& A, const Vec<T>& v, const Lanes& L, bool p_zero) {
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_range(A, c, L.lane, base, len);
+    int64_t row = c * kChunk + L.lane;
+    T ax = row_dot<T, true>(A.col, v.val, v.xs, v.diag, base, len);
+    T ap = T(0);
+    if (!p_zero) ap = row_dot<T, true>(A.col, v.val, v.p, v.diag, base, len);
+    if (row < A.n) {
+      T id = __ldg(v.invd + row);
+      T ri = __ldg(v.rhs + row) - ax;
+      stcs(v.r + row, ri);
+      stcs(v.u + row, id * ri);
+      stcs(v.s + row, ap);
+      stcs(v.q + row, id * ap);
+    }
+  }
+}
+
+// P_RR2: w = A u (= Ahat r) ; z = A q (= Ahat s) ; partials (r,u), (w,u), norm.
+template <typename T>
+__device__ __noinline__ void pass_rr2(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d, int k,
+                         bool paper_norm) {
+  T* wc = (k & 1) ? v.wb : v.wa;
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_range(A, c, L.lane, base, len);
+    int64_t row = c * kChunk + L.lane;
+    T wi = row_dot<T, false>(A.col, v.val, v.r, nullptr, base, len);
+    T zi = row_dot<T, false>(A.col, v.val, v.s, nullptr, base, len);
+    if (row < A.n) {
+      T ri = ldcs(v.r + row), ui = ldcs(v.u + row);
+      stcs(wc + row, wi);
+      stcs(v.z + row, zi);
+      d.add(0, ri, ui);
+      d.add(1, wi, ui);
+      if (paper_norm) d.add(2, ui, ui); else d.add(2, ri, ri);
+    }
+  }
+}
+
+__device__ __noinline__ void pass_zero_x(const SysDesc& S, const Lanes& L) {
+  FOR_CHUNKS(S.A, L) {
+    int64_t row = c * kChunk + L.lane;
+    if (row < S.A.n) S.x[row] = 0.0;
+  }
+}
+
+// P_ORES (FP32_IR outer step): r64 = b - A x in FP64 ; partials (r64,r64), (b,b).
+__device__ __noinline__ void pass_ores(const SysDesc& S, const Lanes& L, Dots<double>& d) {
+  const DevMatrix& A = S.A;
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_range(A, c, L.lane, base, len);
+    int64_t row = c * kChunk + L.lane;
+    double ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len);
+    if (row < A.n) {
+      double bi = __ldg(S.b + row);
+      double t = bi - ax;
+      stcs(S.r + row, t);
+      d.add(0, t, t);
+      d.add(1, bi, bi);
+    }
+  }
+}
+
+// P_OINIT: rhs32 = r64 / ||r64|| ; r32 = rhs32 ; u32 = M^-1 r32 ; d32 = 0.
+__device__ __noinline__ void pass_oinit(const SysDesc& S, const Lanes& L, double scale) {
+  FOR_CHUNKS(S.A, L) {
+    int64_t row = c * kChunk + L.lane;
+    if (row < S.A.n) {
+      float rh = (float)(ldcs(S.r + row) * scale);
+      stcs(S.rhs32 + row, rh);
+      stcs(S.r32 + row, rh);
+      stcs(S.u32 + row, __ldg(S.A.invd32 + row) * rh);
+      stcs(S.d32 + row, 0.0f);
+    }
+  }
+}
+
+// P_OUPD: x += ||r64|| * d32 (FP64 solution accumulation).
+__device__ __noinline__ void pass_oupd(const SysDesc& S, const Lanes& L, double rn) {
+  FOR_CHUNKS(S.A, L) {
+    int64_t row = c * kChunk + L.lane;
+    if (row < S.A.n) S.x[row] = fma(rn, (double)ldcs(S.d32 + row), S.x[row]);
+  }
+}
+
+// ----------------------------------------------------------- partials and reduction --
+
+// Block partials -> part slot [4], fixed reduction tree (deterministic).
+__device__ void write_block_partials(double a0, double a1, double a2, double* slot, double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_down_sync(kFull, a0, o);
+    a1 += __shfl_down_sync(kFull, a1, o);
+    a2 += __shfl_down_sync(kFull, a2, o);
+  }
+  if (lane == 0) { sm[warp * 3] = a0; sm[warp * 3 + 1] = a1; sm[warp * 3 + 2] = a2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int w = 0; w < nw; w++) { s0 += sm[w * 3]; s1 += sm[w * 3 + 1]; s2 += sm[w * 3 + 2]; }
+    slot[0] = s0; slot[1] = s1; slot[2] = s2; slot[3] = 0.0;
+  }
+}
+
+// Sum the group's P partial slots in a fixed order; every CTA obtains identical bits.
+__device__ void group_reduce(const double* part, int P, double* out, double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    a0 += __ldcg(part + 4 * i);
+    a1 += __ldcg(part + 4 * i + 1);
+    a2 += __ldcg(part + 4 * i + 2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_down_sync(kFull, a0, o);
+    a1 += __shfl_down_sync(kFull, a1, o);
+    a2 += __shfl_down_sync(kFull, a2, o);
+  }
+  if (lane == 0) { sm[warp * 3] = a0; sm[warp * 3 + 1] = a1; sm[warp * 3 + 2] = a2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int w = 0; w < nw; w++) { s0 += sm[w * 3]; s1 += sm[w * 3 + 1]; s2 += sm[w * 3 + 2]; }
+    out[0] = s0; out[1] = s1; out[2] = s2; out[3] = 0.0;
+  }
+}
+
+// ------------------------------------------------------------------------- control --
+
+__device__ __forceinline__ void take_dots(Ctl& c) {
+  c.gamma = c.red[0];
+  c.delta = c.red[1];
+  c.norm = sqrt(c.red[2]);
+}
+
+__device__ __forceinline__ bool passed(const Ctl& c, const SysDesc& S) {
+  return S.norm == PPCG_NORM_PAPER_U_ABS ? (c.norm <= S.tol) : (c.norm <= S.tol * c.bnorm);
+}
+
+// Alg. 2 lines 5-9.  Returns false (and sets status) on breakdown.
+__device__ __forceinline__ bool scalars(Ctl& c, int it) {
+  if (it > 0) {
+    c.beta = c.gamma / c.gamma_prev;
+    double den = c.delta - c.beta * c.gamma / c.alpha_prev;
+    if (!(c.gamma > 0.0) || !(den > 0.0)) return false;
+    c.alpha = c.gamma / den;
+  } else {
+    c.beta = 0.0;
+    if (!(c.gamma > 0.0) || !(c.delta > 0.0)) return false;
+    c.alpha = c.gamma / c.delta;
+  }
+  return true;
+}
+
+// Thread 0 of every CTA: choose the next pass from the reduced partials of the last one.
+__device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
+  for (;;) {
+    switch (c.state) {
+      // ---- FP64 pipelined PCG
+      case S_START:
+        c.pass = P_SETUP1; c.state = S_AFTER_SETUP1; return;
+      case S_AFTER_SETUP1:
+        c.bnorm = sqrt(c.red[0]);
+        if (S.norm == PPCG_NORM_REL_R && c.bnorm == 0.0) {   // A x = 0 -> x = 0
+          c.status = PPCG_OK; c.pass = P_ZERO_X; c.state = S_FINAL; return;
+        }
+        c.pass = P_SETUP2; c.state = S_AFTER_SETUP2; return;
+      case S_AFTER_SETUP2:
+        take_dots(c); c.state = S_TOP; break;
+      case S_AFTER_ITER:
+        c.gamma_prev = c.gamma; c.alpha_prev = c.alpha; c.iter++;
+        take_dots(c); c.state = S_TOP; break;
+      case S_AFTER_RR2:
+        take_dots(c); c.rr_count++; c.last_rr_iter = c.iter;
+        if (passed(c, S)) { c.status = PPCG_OK; c.state = S_FINAL; break; }
+        c.state = S_TOP; break;
+      case S_TOP: {
+        if (c.iter >= iter_end) { c.pass = P_NONE; c.exit_now = 1; return; }
+        if (S.rr_period > 0 && c.iter > 0 && c.iter % S.rr_period == 0 && c.last_rr_iter != c.iter) {
+          c.pass = P_RR1; c.state = S_AFTER_RR1; return;
+        }
+        if (passed(c, S)) {
+          if (S.norm == PPCG_NORM_PAPER_U_ABS) { c.status = PPCG_OK; c.state = S_FINAL; break; }
+          c.pass = P_TRUE; c.state = S_AFTER_TRUE; return;
+        }
+        if (c.iter >= S.maxit) { c.status = PPCG_ERR_NOT_CONVERGED; c.state = S_FINAL; break; }
+        if (!isfinite(c.gamma) || !isfinite(c.delta)) { c.status = PPCG_ERR_NONFINITE; c.state = S_FINAL; break; }
+        if (!scalars(c, c.iter)) { c.status = PPCG_ERR_BREAKDOWN; c.state = S_FINAL; break; }
+        c.first = (c.iter == 0);
+        c.pass = P_ITER; c.state = S_AFTER_ITER; return;
+      }
+      case S_AFTER_TRUE:
+        c.res_true = sqrt(c.red[0]);
+        if (c.res_true <= S.tol * c.bnorm) { c.status = PPCG_OK; c.state = S_DONE; c.pass = P_NONE; return; }
+        c.pass = P_RR1; c.state = S_AFTER_RR1; return;
+      case S_AFTER_RR1:
+        c.pass = P_RR2; c.state = S_AFTER_RR2; return;
+      case S_FINAL:
+        c.pass = P_TRUE; c.state = S_AFTER_FINAL; return;
+      case S_AFTER_FINAL:
+        c.res_true = sqrt(c.red[0]); c.state = S_DONE; c.pass = P_NONE; return;
+      case S_DONE:
+        c.pass = P_NONE; return;
+
+      // ---- FP32 inner solves inside FP64 iterative refinement
+      case S_O_START:
+        c.pass = P_ORES; c.state = S_O_AFTER_ORES; return;
+      case S_O_AFTER_ORES:
+        c.rn = sqrt(c.red[0]);
+        c.bnorm = sqrt(c.red[1]);
+        c.res_true = c.rn;
+        if (c.bnorm == 0.0) { c.status = PPCG_OK; c.pass = P_ZERO_X; c.state = S_O_AFTER_ZERO; return; }
+        if (c.rn <= S.tol * c.bnorm) { c.status = PPCG_OK; c.state = S_DONE; c.pass = P_NONE; return; }
+        if (!isfinite(c.rn)) { c.status = PPCG_ERR_NONFINITE; c.state = S_DONE; c.pass = P_NONE; return; }
+        if (c.outer >= S.max_outer || c.iter >= S.maxit) {
+          c.status = PPCG_ERR_NOT_CONVERGED; c.state = S_DONE; c.pass = P_NONE; return;
+        }
+        c.inner_target = fmax(S.inner_tol, 0.3 * S.tol * c.bnorm / c.rn);
+        c.pass = P_OINIT; c.state = S_O_AFTER_OINIT; return;
+      case S_O_AFTER_ZERO:
+        c.res_true = 0.0; c.state = S_DONE; c.pass = P_NONE; return;
+      case S_O_AFTER_OINIT:
+        c.inner_iter = 0; c.last_rr_iter = -1;
+        c.pass = P_SETUP2; c.state = S_I_AFTER_SETUP2; return;
+      case S_I_AFTER_SETUP2:
+        take_dots(c); c.inner_norm0 = c.norm; c.state = S_I_TOP; break;
+      case S_I_AFTER_ITER:
+        c.gamma_prev = c.gamma; c.alpha_prev = c.alpha; c.iter++; c.inner_iter++;
+        take_dots(c); c.state = S_I_TOP; break;
+      case S_I_AFTER_RR2:
+        take_dots(c); c.rr_count++; c.last_rr_iter = c.inner_iter; c.state = S_I_TOP; break;
+      case S_I_AFTER_RR1:
+        c.pass = P_RR2; c.state = S_I_AFTER_RR2; return;
+      case S_I_TOP: {
+        if (c.iter >= iter_end) { c.pass = P_NONE; c.exit_now = 1; return; }
+        if (!isfinite(c.gamma) || !isfinite(c.delta) || !isfinite(c.norm)) {
+          c.status = PPCG_ERR_NONFINITE; c.state = S_DONE; c.pass = P_NONE; return;
+        }
+        if (c.norm <= c.inner_target * c.inner_norm0 || c.inner_iter >= S.inner_maxit || c.iter >= S.maxit) {
+          c.pass = P_OUPD; c.state = S_O_AFTER_OUPD; return;
+        }
+        if (S.rr_period > 0 && c.inner_iter > 0 && c.inner_iter % S.rr_period == 0 &&
+            c.last_rr_iter != c.inner_iter) {
+          c.pass = P_RR1; c.state = S_I_AFTER_RR1; return;
+        }
+        if (!scalars(c, c.inner_iter)) {
+          if (c.inner_iter == 0) { c.status = PPCG_ERR_BREAKDOWN; c.state = S_DONE; c.pass = P_NONE; return; }
+          c.pass = P_OUPD; c.state = S_O_AFTER_OUPD; return;   // keep the correction so far
+        }
+        c.first = (c.inner_iter == 0);
+        c.pass = P_ITER; c.state = S_I_AFTER_ITER; return;
+      }
+      case S_O_AFTER_OUPD:
+        c.outer++; c.rn_prev = c.rn;
+        c.pass = P_ORES; c.state = S_O_AFTER_ORES; return;
+      default:
+        c.status = PPCG_ERR_ARG; c.state = S_DONE; c.pass = P_NONE; return;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------- driver --
+
+struct Shared {
+  SysDesc S;
+  Ctl C;
+  double sm[3 * 32];
+};
+
+template <class G>
+__device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
+  __syncthreads();   // previous system's readers of sh are done
+  if (threadIdx.x == 0) {
+    sh.S = *Sg;
+    // the control block was written by an earlier launch or kernel: read it through L2
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(sh.S.ctl);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sh.C);
+    for (int i = 0; i < (int)(sizeof(Ctl) / 8); i++) dst[i] = __ldcg(src + i);
+    if (sh.C.t_start == 0) sh.C.t_start = globaltimer();
+    sh.C.exit_now = 0;
+  }
+  __syncthreads();
+  const SysDesc& S = sh.S;
+  Ctl& C = sh.C;
+  const int iter_end = budget > 0 && C.iter < 0x7fffffff - budget ? C.iter + budget : 0x7fffffff;
+  const int nw = blockDim.x >> 5;
+  Lanes L;
+  L.lane = threadIdx.x & 31;
+  L.gw = (int64_t)g.rank() * nw + (threadIdx.x >> 5);
+  L.W = (int64_t)g.size() * nw;
+  const bool paper = S.norm == PPCG_NORM_PAPER_U_ABS;
+  const int P = g.size();
+
+  for (;;) {
+    if (threadIdx.x == 0) control(C, S, iter_end);
+    __syncthreads();
+    const int pass = C.pass;
+    if (pass == P_NONE) break;
+    const bool fp32 = S.precision == PPCG_FP32_IR && (C.state >= S_O_START);
+    double* slot = S.part + ((size_t)C.parity * P + g.rank()) * 4;
+    bool partials = true;
+    if (!fp32 || pass == P_ORES) {
+      Dots<double> d;
+      Vec<double> v = vec64(S);
+      switch (pass) {
+        case P_SETUP1: pass_setup1(S, L, d, S.x_zero != 0); break;
+        case P_SETUP2: pass_setup2<double>(S.A, v, L, d, paper); break;
+        case P_ITER: pass_iter<double>(S.A, v, L, d, C.alpha, C.beta, C.first != 0, C.iter, paper); break;
+        case P_TRUE: pass_true(S, L, d); break;
+        case P_RR1: pass_rr1<double>(S.A, v, L, C.iter == 0); partials = false; break;
+        case P_RR2: pass_rr2<double>(S.A, v, L, d, C.iter, paper); break;
+        case P_ZERO_X: pass_zero_x(S, L); partials = false; break;
+        case P_ORES: pass_ores(S, L, d); break;
+        default: partials = false; break;
+      }
+      if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
+    } else {
+      Dots<float> d;
+      Vec<float> v = vec32(S);
+      switch (pass) {
+        case P_SETUP2: pass_setup2<float>(S.A, v, L, d, paper); break;
+        case P_ITER:
+          pass_iter<float>(S.A, v, L, d, (float)C.alpha, (float)C.beta, C.first != 0, C.inner_iter, paper);
+          break;
+        case P_RR1: pass_rr1<float>(S.A, v, L, C.inner_iter == 0); partials = false; break;
+        case P_RR2: pass_rr2<float>(S.A, v, L, d, C.inner_iter, paper); break;
+        case P_ZERO_X: pass_zero_x(S, L); partials = false; break;
+        case P_OINIT: pass_oinit(S, L, 1.0 / C.rn); partials = false; break;
+        case P_OUPD: pass_oupd(S, L, C.rn); partials = false; break;
+        default: partials = false; break;
+      }
+      if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
+    }
+    if (!g.sync()) {
+      if (threadIdx.x == 0) { C.status = PPCG_ERR_TIMEOUT; C.state = S_DONE; }
+      break;
+    }
+    if (partials) {
+      group_reduce(S.part + (size_t)C.parity * P * 4, P, C.red, sh.sm);
+      if (threadIdx.x == 0) C.parity ^= 1;
+    }
+  }
+  if (threadIdx.x == 0 && g.rank() == 0) {
+    C.t_end = globaltimer();
+    *S.ctl = C;
+    __threadfence();
+  }
+}
+
+__global__ void __launch_bounds__(kGridThreads, 2) k_grid(const SysDesc* d, int budget) {
+  __shared__ Shared sh;
+  GridGroup g{d->bar, d->err, (long long)d->spin_limit_ns, 0u};
+  run_system(g, d, budget, sh);
+}
+
+__global__ void __launch_bounds__(kClusterThreads, 4) k_cluster(const SysDesc* descs, const int32_t* list,
+                                                             const int32_t* list_ptr, int budget) {
+  __shared__ Shared sh;
+  ClusterGroup g;
+  unsigned cid;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+  for (int k = list_ptr[cid]; k < list_ptr[cid + 1]; k++) run_system(g, descs + list[k], budget, sh);
+}
+
+// Failure-detection self test: the grid barrier with one rank that never arrives.  Every
+// other CTA must give up after limit_ns and report PPCG_ERR_TIMEOUT instead of hanging.
+__global__ void k_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, int drop_rank,
+                                   long long limit_ns) {
+  GridGroup g{bar, err, limit_ns, 0u};
+  if ((int)blockIdx.x == drop_rank) return;
+  bool ok = g.sync();
+  if (threadIdx.x == 0) out[blockIdx.x] = ok ? 1 : 0;
+}
+
+}  // namespace
+
+int grid_blocks_for_device(int device) {
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_grid, kGridThreads, 0);
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+int max_active_clusters(int device) {
+  (void)device;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterSize * 64);
+  cfg.blockDim = dim3(kClusterThreads);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kClusterSize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (void*)k_cluster, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+cudaError_t launch_grid(const SysDesc* d_desc, int grid, int budget, cudaStream_t st) {
+  void* args[] = {(void*)&d_desc, (void*)&budget};
+  return cudaLaunchCooperativeKernel((void*)k_grid, dim3(grid), dim3(kGridThreads), args, 0, st);
+}
+
+cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
+                            int nclusters, int budget, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterSize * nclusters);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kClusterSize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_cluster, d_descs, d_list, d_list_ptr, budget);
+}
+
+cudaError_t launch_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, int grid, int drop_rank,
+                                    int64_t limit_ns, cudaStream_t st) {
+  long long lim = (long long)limit_ns;
+  void* args[] = {(void*)&bar, (void*)&err, (void*)&out, (void*)&drop_rank, (void*)&lim};
+  return cudaLaunchCooperativeKernel((void*)k_barrier_selftest, dim3(grid), dim3(64), args, 0, st);
+}
+
+}  // namespace ppcg

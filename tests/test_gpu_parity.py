@@ -1,0 +1,194 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle on the same seeded inputs.
+
+Bars (FP64): x after a fixed number of iterations k within 1e-10 relative of the oracle's
+x_k, at k where two summation orders of the oracle itself agree to 1e-12
+(test_oracle_pins.test_summation_order_sensitivity); full solves reach a true relative
+residual <= tol with the oracle's iteration count +-2.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2105_06176_b300 as pp
+    pp.lib()
+
+
+def pp():
+    import paper_2105_06176_b300 as m
+    return m
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def gpu(a, b, x0=None, tol=1e-8, maxit=10000, **opts):
+    s = pp().Solver.from_csr(a, **opts)
+    x, info = s.solve(dev(b), None if x0 is None else dev(x0), tol=tol, maxit=maxit)
+    out = x.cpu().numpy(), info
+    s.close()
+    return out
+
+
+def problem(name):
+    if name == "poisson2d_64":
+        a = synth.poisson2d(64)
+        return a, a.to_scipy() @ synth.xtrue_uniform(a.n, 1)
+    if name == "varcoeff3d_31":         # 29,791 rows: 931 chunks, ragged last chunk
+        a = synth.varcoeff3d(31, seed=1)
+        return a, synth.rhs_uniform(a.n, 1)
+    if name == "varcoeff2d_150":
+        a = synth.varcoeff2d(150, seed=4)
+        return a, synth.rhs_uniform(a.n, 4)
+    if name == "rgg_20k":               # irregular rows: sigma-sorted SELL with a row permutation
+        a = synth.rgg_laplacian(20000, (3 * 14.0 / (4 * np.pi * 20000)) ** (1 / 3), 1e-3, 5)
+        return a, synth.rhs_uniform(a.n, 5)
+    raise KeyError(name)
+
+
+PATHS = [dict(path=1), dict(path=2)]      # GRID, CLUSTER
+
+
+@pytest.mark.parametrize("name,k", [("poisson2d_64", 50), ("varcoeff3d_31", 20), ("varcoeff2d_150", 30),
+                                    ("rgg_20k", 20)])
+@pytest.mark.parametrize("opts", PATHS, ids=["grid", "cluster"])
+def test_fixed_k_parity(name, k, opts):
+    a, b = problem(name)
+    ref = oracle.pipecg(a, b, tol=0.0, maxit=k)
+    x, info = gpu(a, b, tol=0.0, maxit=k, **opts)
+    assert info.status == pp().ERR_NOT_CONVERGED and info.iters == k
+    assert rel(x, ref["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["poisson2d_64", "varcoeff3d_31", "rgg_20k"])
+@pytest.mark.parametrize("opts", PATHS, ids=["grid", "cluster"])
+def test_full_solve_parity(name, opts):
+    a, b = problem(name)
+    ref = oracle.pipecg(a, b, tol=1e-8, maxit=20000)
+    x, info = gpu(a, b, tol=1e-8, maxit=20000, **opts)
+    assert info.status == pp().OK
+    assert abs(info.iters - ref["result"]["iters"]) <= 2
+    assert info.rel_res_true <= 1e-8
+    t = np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)
+    assert t <= 1e-8
+    assert info.rel_res_true == pytest.approx(t, rel=1e-6, abs=1e-14)
+    assert rel(x, ref["x"]) <= 1e-6
+
+
+def test_nonzero_x0_and_aliasing():
+    a, b = problem("varcoeff2d_150")
+    x0 = synth.xtrue_uniform(a.n, 9)
+    ref = oracle.pipecg(a, b, x0=x0, tol=0.0, maxit=25)
+    s = pp().Solver.from_csr(a)
+    xd = dev(x0)
+    x, info = s.solve(dev(b), xd, xd, tol=0.0, maxit=25)    # x aliases x0
+    assert rel(xd.cpu().numpy(), ref["x"]) <= 1e-10
+
+
+def test_host_pointers_match_device():
+    a, b = problem("poisson2d_64")
+    s = pp().Solver.from_csr(a)
+    xh = np.empty(a.n)
+    _, ih = s.solve(np.ascontiguousarray(b), None, xh, tol=1e-8)
+    xd, idv = s.solve(dev(b), tol=1e-8)
+    assert ih.status == idv.status == pp().OK and ih.iters == idv.iters
+    assert np.array_equal(xh, xd.cpu().numpy())
+
+
+def test_paper_norm_mode():
+    """Sec. VI protocol: absolute tol 1e-5 on sqrt((u,u)), exact solution 1/sqrt(N)."""
+    a = synth.varcoeff2d(64, seed=3)
+    b = a.to_scipy() @ np.full(a.n, 1.0 / np.sqrt(a.n))
+    ref = oracle.pipecg(a, b, tol=1e-5, maxit=10000, norm=oracle.NORM_PAPER_U_ABS)
+    for path in (1, 2):
+        x, info = gpu(a, b, tol=1e-5, maxit=10000, norm=pp().NORM_PAPER_U_ABS, path=path)
+        assert info.status == pp().OK
+        assert abs(info.iters - ref["result"]["iters"]) <= 2
+        assert info.rel_res_recursive <= 1e-5
+
+
+@pytest.mark.parametrize("period", [10, 37])
+def test_residual_replacement_parity(period):
+    a, b = problem("poisson2d_64")
+    ref = oracle.pipecg(a, b, tol=0.0, maxit=60, rr_period=period)
+    x, info = gpu(a, b, tol=0.0, maxit=60, rr_period=period, path=1)
+    assert info.rr_count == ref["result"]["rr_count"]
+    assert rel(x, ref["x"]) <= 1e-10
+
+
+def test_edge_cases():
+    m = pp()
+    a = synth.poisson2d(16)
+    b = synth.rhs_uniform(a.n, 2)
+    # b = 0 -> x = 0, 0 iterations, OK
+    s = m.Solver.from_csr(a)
+    x, info = s.solve(dev(np.zeros(a.n)), dev(np.ones(a.n)))
+    assert info.status == m.OK and info.iters == 0 and not x.cpu().numpy().any()
+    # exact initial guess -> 0 iterations
+    xs = np.linalg.solve(a.dense(), b)
+    x, info = s.solve(dev(b), dev(xs), tol=1e-8)
+    assert info.status == m.OK and info.iters == 0
+    # maxit = 0 -> NOT_CONVERGED, x = x0
+    x, info = s.solve(dev(b), None, tol=1e-8, maxit=0)
+    assert info.status == m.ERR_NOT_CONVERGED and info.iters == 0 and not x.cpu().numpy().any()
+    # NaN in b -> NONFINITE
+    bn = b.copy()
+    bn[3] = np.nan
+    x, info = s.solve(dev(bn), tol=1e-8)
+    assert info.status == m.ERR_NONFINITE
+    # n = 1
+    one = synth.CSR(1, np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), np.array([4.0]))
+    x, info = gpu(one, np.array([2.0]))
+    assert info.status == m.OK and x[0] == pytest.approx(0.5)
+
+
+def test_create_rejects_bad_matrices():
+    m = pp()
+    bad_diag = synth.CSR(2, np.array([0, 2, 3], dtype=np.int64), np.array([0, 1, 0], dtype=np.int32),
+                         np.array([2.0, -1.0, -1.0]))
+    with pytest.raises(m.PPCGError) as e:
+        m.Solver.from_csr(bad_diag)
+    assert e.value.status == m.ERR_NOT_SPD
+    bad_col = synth.CSR(2, np.array([0, 2, 4], dtype=np.int64), np.array([0, 5, 0, 1], dtype=np.int32),
+                        np.array([2.0, -1.0, -1.0, 2.0]))
+    with pytest.raises(m.PPCGError) as e:
+        m.Solver.from_csr(bad_col)
+    assert e.value.status == m.ERR_ARG
+
+
+def test_indefinite_breakdown():
+    m = pp()
+    mat = np.array([[1.0, 2.0, 0.0], [2.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    import scipy.sparse as sp
+    c = sp.csr_matrix(mat)
+    a = synth.CSR(3, c.indptr.astype(np.int64), c.indices.astype(np.int32), c.data)
+    for path in (1, 2):
+        x, info = gpu(a, np.array([1.0, -1.0, 1.0]), path=path)
+        assert info.status == m.ERR_BREAKDOWN
+
+
+def test_barrier_timeout_is_reported_not_hung():
+    """Failure detection: one CTA of the grid barrier never arrives; the others give up after
+    50 ms and report a timeout (no hang, no fault, context still usable)."""
+    m = pp()
+    st, n = m.barrier_timeout_selftest(grid=32, drop_rank=5, limit_ns=50_000_000)
+    assert st == m.OK
+    assert n >= 1
+    a, b = problem("poisson2d_64")
+    x, info = gpu(a, b)             # the context still works
+    assert info.status == m.OK
