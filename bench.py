@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark: pipelined PCG (Alg. 2, Jacobi) on one B300 per rank.
+
+One step = one full solve of the 3-D 7-point variable-coefficient diffusion system on a
+256^3 grid (N = 16,777,216, nnz = 117,047,296; face coefficients exp(N(0,1)); b ~ U[-1,1];
+x0 = 0; relative tolerance 1e-8; FP64) through the C ABI: setup, every iteration and the
+final true residual, all inside the library's persistent kernel.
+
+Printed (rank 0, one JSON line): iterations/s over all ranks (value), end-to-end
+iterations/s through host buffers (e2e), the roofline of the solve kernel against the
+measured HBM copy bandwidth, SM clocks sampled during the timed region, the FP32+IR vs
+FP64 time to 1e-8 on the same system, and the CPU oracle timed on a bounded sample.
+
+Multi-GPU: replicas only.  Each rank solves its own copy; value = all ranks' iterations /
+the slowest rank's time ("scaling": "weak").
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "pipelined-PCG iter/s, % HBM peak; mixed vs FP64 at 1e-8; p50/p99 solve latency"
+UNIT = "iter/s"
+GRID_N = 256
+SEED = 1
+TOL = 1e-8
+MAXIT = 20000
+WORKLOAD = ("3D 7-point variable-coefficient diffusion 256^3 (N=16,777,216, nnz=117,047,296), "
+            "log-normal(0,1) face coefficients, Jacobi, b~U[-1,1], x0=0, rel tol 1e-8, FP64 pipelined PCG")
+
+
+def b_alg(n, nnz, v):
+    """Algorithmic bytes of one iteration: SELL values + int32 columns, row pointers, and
+    17 vector streams (w gather once; invd z q s p x r u read; z q s p x r u w written)."""
+    return (v + 4) * nnz + 4 * (n + 1) + 17 * v * n
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for ln in f:
+                    parts = [t.strip() for t in ln.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        loaded = sorted(sm)[len(sm) // 4:] if len(sm) >= 4 else sm
+        return {"sm_mhz": float(np.median(loaded)) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def profiled_traffic(bytes_iter, iters_per_launch):
+    """DRAM bytes per launch from the committed ncu capture of the solve kernel, scaled from
+    the captured grid to this one by algorithmic bytes; None once the kernel source has
+    changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_grid_traffic.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, "paper_2105_06176_b300", "csrc", "solver.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None, "no capture"
+    if rec.get("kernel_source_sha256") != sha:
+        return None, "kernel changed since the last capture"
+    return rec["dram_over_balg"] * bytes_iter * iters_per_launch, \
+        f"ncu capture on {rec['workload']} scaled by algorithmic bytes"
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(a, b, k_lo=2, k_hi=8):
+    """Oracle (plain single-thread C, FP64) iterations/s on the same system: the time of
+    k_hi - k_lo iterations, from two runs that share setup and final-residual costs."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.pipecg(a, b, tol=0.0, maxit=k_lo)
+    t1 = time.perf_counter()
+    oracle.pipecg(a, b, tol=0.0, maxit=k_hi)
+    t2 = time.perf_counter()
+    per = max((t2 - t1) - (t1 - t0), 1e-9) / (k_hi - k_lo)
+    return {"value": 1.0 / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{k_hi - k_lo} iterations of the 256^3 system (difference of {k_hi}- and {k_lo}-iteration "
+                      f"runs), single-thread plain C, {os.cpu_count()} host cores present",
+            "seconds": t2 - t0}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the oracle, as it stands, on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    a = synth.varcoeff3d(GRID_N, SEED)
+    b = synth.rhs_uniform(a.n, SEED)
+    oracle.lib()
+    k = 3
+    for _ in range(args.warmup):
+        oracle.pipecg(a, b, tol=0.0, maxit=1)
+    t0 = time.perf_counter()
+    iters = 0
+    for _ in range(args.steps):
+        out = oracle.pipecg(a, b, tol=0.0, maxit=k)
+        iters += out["result"]["iters"]
+    dt = time.perf_counter() - t0
+    val = iters / dt
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": f"{k} iterations per step incl. setup and final residual"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{k} iterations of the 256^3 system per step, including setup "
+                                       f"(3 SpMV) and the final residual, single-thread plain C"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=GRID_N, help="grid side (256 = the benchmark workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    import paper_2105_06176_b300 as pp
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    def barrier():
+        if pg:
+            pg.barrier()
+
+    a = synth.varcoeff3d(args.grid, SEED)
+    b = synth.rhs_uniform(a.n, SEED)
+    n, nnz = a.n, a.nnz
+    solver = pp.Solver.from_csr(a)
+    b_d = torch.from_numpy(b).cuda()
+    x_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        _, info = solver.solve(b_d, None, x_d, tol=TOL, maxit=MAXIT)
+    assert info.status == pp.OK, info
+    iters_per_solve = info.iters
+
+    infos = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(args.steps):
+            step_ev[k][0].record(stream)
+            _, info = solver.solve(b_d, None, x_d, tol=TOL, maxit=MAXIT, sync=False)
+            step_ev[k][1].record(stream)
+            infos.append(info)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    clocks = clk.summary()
+    dt = ev0.elapsed_time(ev1) * 1e-3
+    iters = sum(i.iters for i in infos)
+    assert all(i.status == pp.OK for i in infos), [i.status for i in infos]
+    step_s = [s.elapsed_time(e) * 1e-3 for s, e in step_ev]
+    if pg:
+        t = torch.tensor([dt, float(iters)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+        pg.all_reduce(t, op=pg.ReduceOp.SUM)
+        dt_max, iters_all = tmax[0].item(), t[1].item()
+    else:
+        dt_max, iters_all = dt, float(iters)
+    value = iters_all / dt_max
+
+    # end to end through the C ABI with pinned host buffers: H2D of b, D2H of x inside each step
+    b_h = torch.from_numpy(b).pin_memory()
+    x_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    solver.solve(b_h, None, x_h, tol=TOL, maxit=MAXIT)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_iters = 0
+    for _ in range(args.steps):
+        _, info = solver.solve(b_h, None, x_h, tol=TOL, maxit=MAXIT, sync=True)
+        e_iters += info.iters
+    e_dt = time.perf_counter() - t0
+    barrier()
+    e2e = {"value": e_iters * ws / e_dt if not pg else None, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+    if pg:
+        t = torch.tensor([e_dt], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e["value"] = e_iters * ws / t.item()
+
+    # roofline of the solve kernel (one launch = one step)
+    peaks, peak_kind = measured_peaks()
+    bytes_iter = b_alg(n, nnz, 8)
+    per_launch_s = float(np.mean(step_s))
+    achieved = bytes_iter * (iters / len(infos)) / per_launch_s / 1e9
+    kernel_s = float(np.mean([i.seconds for i in infos]))
+    traffic, traffic_src = profiled_traffic(bytes_iter, iters / len(infos))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_src,
+                "peak_kind": peak_kind,
+                "kernel": "k_grid (persistent solve: setup + iterations + final residual)",
+                "bytes_per_iter": bytes_iter, "iters_per_launch": iters / len(infos),
+                "launch_ms": 1e3 * per_launch_s, "device_timer_ms": 1e3 * kernel_s,
+                "frac_of_8TBs_nominal": achieved / 8000.0}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": args.grid, "N": n, "nnz": nnz,
+                       "iters_per_solve": iters_per_solve, "format": "SELL-C-sigma C=32",
+                       "path": "grid (cooperative persistent kernel)",
+                       "l2": "inputs larger than L2 (3.75 GB streamed per iteration vs 126 MB L2)",
+                       "parallelism": f"replicas x{ws}"},
+            "e2e": e2e, "roofline": roofline, "clocks": clocks,
+            "gpu_launches": 2 * args.steps}
+
+    if not args.no_mixed:
+        sm = pp.Solver.from_csr(a, precision=pp.FP32_IR)
+        xm = torch.empty(n, dtype=torch.float64, device="cuda")
+        sm.solve(b_d, None, xm, tol=TOL, maxit=MAXIT)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, im = sm.solve(b_d, None, xm, tol=TOL, maxit=MAXIT, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_mixed = e0.elapsed_time(e1) * 1e-3
+        err = (torch.linalg.norm(xm - x_d) / torch.linalg.norm(x_d)).item()
+        line["mixed_vs_fp64"] = {"fp64_s": per_launch_s, "fp32_ir_s": t_mixed,
+                                 "speedup": per_launch_s / t_mixed, "fp32_ir_iters": im.iters,
+                                 "outer": im.outer_iters, "status": pp.status_name(im.status),
+                                 "rel_res_true": im.rel_res_true, "err_vs_fp64_solution": err,
+                                 "fp32_bytes_per_iter": b_alg(n, nnz, 4)}
+        sm.close()
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_rate(a, b)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -78,7 +78,8 @@ typedef struct {
   int32_t max_outer;        /* FP32_IR: cap on refinement steps */
   int64_t spin_limit_ns;    /* time limit of one device-side barrier wait (ns); exceeded -> TIMEOUT */
   int32_t cluster_max_rows; /* PATH_AUTO: systems with at most this many rows take the CLUSTER path */
-  int32_t reserved[7];
+  int32_t epoch_iters;      /* server: iterations each resident solve advances per epoch */
+  int32_t reserved[6];
 } ppcg_opts;
 
 /* Per-solve results.  Filled asynchronously; valid after the solve's stream is synchronised. */
@@ -96,7 +97,8 @@ typedef struct {
 } ppcg_info;
 
 /* Fill *opts with defaults: FP64, AUTO format/path, REL_R, sigma autotune, rr_period 0,
- * inner_tol 1e-4, inner_maxit 100000, max_outer 30, spin_limit 10 s, cluster_max_rows 16384. */
+ * inner_tol 1e-4, inner_maxit 100000, max_outer 30, spin_limit 10 s, cluster_max_rows 16384,
+ * epoch_iters 256. */
 void ppcg_opts_default(ppcg_opts* opts);
 
 /*

@@ -49,7 +49,8 @@ class Opts(ctypes.Structure):
                 ("path", ctypes.c_int32), ("sigma", ctypes.c_int32), ("rr_period", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64),
-                ("cluster_max_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("cluster_max_rows", ctypes.c_int32), ("epoch_iters", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class Info(ctypes.Structure):
@@ -93,22 +94,20 @@ def lib(build_if_missing=True):
     L.ppcg_destroy.restype = None
     L.ppcg_last_error.argtypes = []
     L.ppcg_last_error.restype = ctypes.c_char_p
-    if hasattr(L, "ppcg_server_create"):
-        L.ppcg_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_size_t, ctypes.POINTER(Opts)]
-        L.ppcg_server_create.restype = ctypes.c_int
-        L.ppcg_submit.argtypes = [P, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, ctypes.c_double,
-                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
-        L.ppcg_submit.restype = ctypes.c_int
-        L.ppcg_poll.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(Info)]
-        L.ppcg_poll.restype = ctypes.c_int
-        L.ppcg_server_stats.argtypes = [P] + [ctypes.POINTER(ctypes.c_int64)] * 4
-        L.ppcg_server_stats.restype = ctypes.c_int
-        L.ppcg_server_destroy.argtypes = [P]
-        L.ppcg_server_destroy.restype = None
-    if hasattr(L, "ppcg_selftest_barrier_timeout"):
-        L.ppcg_selftest_barrier_timeout.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
-                                                    ctypes.POINTER(ctypes.c_int32)]
-        L.ppcg_selftest_barrier_timeout.restype = ctypes.c_int
+    L.ppcg_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_size_t, ctypes.POINTER(Opts)]
+    L.ppcg_server_create.restype = ctypes.c_int
+    L.ppcg_submit.argtypes = [P, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, ctypes.c_double,
+                              ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
+    L.ppcg_submit.restype = ctypes.c_int
+    L.ppcg_poll.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(Info)]
+    L.ppcg_poll.restype = ctypes.c_int
+    L.ppcg_server_stats.argtypes = [P] + [ctypes.POINTER(ctypes.c_int64)] * 4
+    L.ppcg_server_stats.restype = ctypes.c_int
+    L.ppcg_server_destroy.argtypes = [P]
+    L.ppcg_server_destroy.restype = None
+    L.ppcg_selftest_barrier_timeout.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                                ctypes.POINTER(ctypes.c_int32)]
+    L.ppcg_selftest_barrier_timeout.restype = ctypes.c_int
     _lib = L
     return L
 

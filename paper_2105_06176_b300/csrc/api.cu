@@ -8,7 +8,7 @@
 #include <queue>
 #include <vector>
 
-#include "internal.h"
+#include "handle.h"
 
 namespace ppcg {
 
@@ -21,8 +21,6 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
-namespace {
-
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -32,6 +30,8 @@ bool is_device_ptr(const void* p) {
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
+
+namespace {
 
 __global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
                          double* __restrict__ dst) {
@@ -56,41 +56,6 @@ __global__ void k_init_ctl(Ctl* c, int32_t state) {
 
 unsigned blocks_for(int64_t n, int tb) { return (unsigned)((n + tb - 1) / tb); }
 
-// Host-side copy of the device control block + launch error flag (pinned).
-struct Stage {
-  Ctl ctl;
-  int32_t err;
-  int32_t pad;
-};
-
-struct InfoJob {
-  Stage* stage;
-  ppcg_info* info;
-  double bytes_per_iter;
-  int32_t norm;
-  int32_t precision;
-};
-
-void fill_info(const Stage& s, const InfoJob& j, ppcg_info* out) {
-  ppcg_info r;
-  memset(&r, 0, sizeof(r));
-  const Ctl& c = s.ctl;
-  r.status = s.err != 0 ? s.err : c.status;
-  r.iters = c.iter;
-  r.outer_iters = c.outer;
-  r.rr_count = c.rr_count;
-  r.bnorm = c.bnorm;
-  if (j.precision == PPCG_FP32_IR) {
-    r.rel_res_recursive = c.bnorm > 0 ? c.rn / c.bnorm : 0.0;
-  } else {
-    r.rel_res_recursive = j.norm == PPCG_NORM_PAPER_U_ABS ? c.norm : (c.bnorm > 0 ? c.norm / c.bnorm : 0.0);
-  }
-  r.rel_res_true = c.bnorm > 0 ? c.res_true / c.bnorm : 0.0;
-  r.seconds = c.t_end > c.t_start ? (double)(c.t_end - c.t_start) * 1e-9 : 0.0;
-  r.bytes_per_iter = j.bytes_per_iter;
-  *out = r;
-}
-
 void CUDART_CB info_callback(void* p) {
   std::vector<InfoJob>* jobs = static_cast<std::vector<InfoJob>*>(p);
   for (const InfoJob& j : *jobs)
@@ -99,37 +64,9 @@ void CUDART_CB info_callback(void* p) {
 }
 
 }  // namespace
-}  // namespace ppcg
-
-using namespace ppcg;
-
-struct ppcg_ctx {
-  int device = 0;
-  int64_t n = 0, nnz = 0;
-  ppcg_opts opts;
-  SellBuild sell;
-  DevMatrix A;
-  int32_t* perm = nullptr;
-  std::vector<void*> allocs;
-  int32_t path = PPCG_PATH_GRID;
-  int grid = 0;        // CTAs of the grid path
-  int nparts = 0;      // partial slots per pass (CTAs in the group)
-  double bytes_per_iter = 0.0;
-  // workspace
-  double *b_ws = nullptr, *x_ws = nullptr, *tmp = nullptr;
-  double* part = nullptr;
-  Ctl* ctl = nullptr;
-  unsigned* bar = nullptr;
-  int32_t* err = nullptr;
-  SysDesc* d_desc = nullptr;
-  SysDesc desc;        // host copy, refreshed per solve
-  Stage* stage = nullptr;   // pinned
-};
-
-namespace {
 
 template <typename T>
-bool walloc(ppcg_ctx* h, T** p, size_t count) {
+static bool walloc(ppcg_ctx* h, T** p, size_t count) {
   if (cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -138,7 +75,7 @@ bool walloc(ppcg_ctx* h, T** p, size_t count) {
   return true;
 }
 
-void free_all(ppcg_ctx* h) {
+static void free_all(ppcg_ctx* h) {
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   if (h->stage) cudaFreeHost(h->stage);
@@ -211,6 +148,16 @@ void prepare_control(ppcg_ctx* h, double tol, int32_t maxit, cudaStream_t st) {
   cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
 }
 
+size_t footprint_bytes(int64_t n, int64_t nnz, int32_t precision) {
+  const bool fp32 = precision == PPCG_FP32_IR;
+  const double slots = 1.05 * (double)nnz + 32.0 * ((double)n / 32.0 + 1.0);
+  double bytes = slots * (fp32 ? 16.0 : 12.0) + (double)n * 8.0 * 8.0;   // matrix + cptr/diag/invd/b/x/tmp/perm
+  bytes += fp32 ? (double)n * (8.0 * 1 + 4.0 * 12) : (double)n * 8.0 * 8.0;
+  return (size_t)bytes + (1u << 20);
+}
+
+namespace {
+
 void enqueue_info(std::vector<std::pair<ppcg_ctx*, ppcg_info*>>& items, cudaStream_t st) {
   auto* jobs = new std::vector<InfoJob>();
   for (auto& it : items) {
@@ -241,6 +188,9 @@ void write_trivial_info(ppcg_info* info, int32_t status) {
 }
 
 }  // namespace
+}  // namespace ppcg
+
+using namespace ppcg;
 
 extern "C" {
 
@@ -258,6 +208,7 @@ void ppcg_opts_default(ppcg_opts* o) {
   o->max_outer = 30;
   o->spin_limit_ns = 10000000000LL;
   o->cluster_max_rows = 16384;
+  o->epoch_iters = 256;
 }
 
 const char* ppcg_last_error(void) { return g_err; }

@@ -1,0 +1,86 @@
+// Solver handle internals shared by the ABI layer (api.cu) and the server (server.cu).
+#pragma once
+#include <cstring>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace ppcg {
+
+// Host-side copy of the device control block + launch error flag (pinned).
+struct Stage {
+  Ctl ctl;
+  int32_t err;
+  int32_t pad;
+};
+
+struct InfoJob {
+  Stage* stage;
+  ppcg_info* info;
+  double bytes_per_iter;
+  int32_t norm;
+  int32_t precision;
+};
+
+inline void fill_info(const Stage& s, const InfoJob& j, ppcg_info* out) {
+  ppcg_info r;
+  memset(&r, 0, sizeof(r));
+  const Ctl& c = s.ctl;
+  r.status = s.err != 0 ? s.err : c.status;
+  r.iters = c.iter;
+  r.outer_iters = c.outer;
+  r.rr_count = c.rr_count;
+  r.bnorm = c.bnorm;
+  if (j.precision == PPCG_FP32_IR) {
+    r.rel_res_recursive = c.bnorm > 0 ? c.rn / c.bnorm : 0.0;
+  } else {
+    r.rel_res_recursive = j.norm == PPCG_NORM_PAPER_U_ABS ? c.norm : (c.bnorm > 0 ? c.norm / c.bnorm : 0.0);
+  }
+  r.rel_res_true = c.bnorm > 0 ? c.res_true / c.bnorm : 0.0;
+  r.seconds = c.t_end > c.t_start ? (double)(c.t_end - c.t_start) * 1e-9 : 0.0;
+  r.bytes_per_iter = j.bytes_per_iter;
+  *out = r;
+}
+
+}  // namespace ppcg
+
+struct ppcg_ctx {
+  int device = 0;
+  int64_t n = 0, nnz = 0;
+  ppcg_opts opts;
+  ppcg::SellBuild sell;
+  ppcg::DevMatrix A;
+  int32_t* perm = nullptr;
+  std::vector<void*> allocs;
+  int32_t path = PPCG_PATH_GRID;
+  int grid = 0;        // CTAs of the grid path
+  int nparts = 0;      // partial slots per pass (CTAs in the group)
+  double bytes_per_iter = 0.0;
+  // workspace
+  double *b_ws = nullptr, *x_ws = nullptr, *tmp = nullptr;
+  double* part = nullptr;
+  ppcg::Ctl* ctl = nullptr;
+  unsigned* bar = nullptr;
+  int32_t* err = nullptr;
+  ppcg::SysDesc* d_desc = nullptr;
+  ppcg::SysDesc desc;        // host copy, refreshed per solve
+  ppcg::Stage* stage = nullptr;   // pinned
+};
+
+
+namespace ppcg {
+
+// Enqueue b/x0 into solver-order device vectors (fills h->desc.b/x/x_zero); *x_solver is
+// the device x the kernel writes.
+ppcg_status stage_inputs(ppcg_ctx* h, const double* b, const double* x0, double* x, bool require_device,
+                         cudaStream_t st, double** x_solver);
+// Enqueue the copy (and un-permutation) of the solver's x into the caller's x.
+void stage_outputs(ppcg_ctx* h, double* x, double* xs, cudaStream_t st);
+// Enqueue a fresh control block and the barrier/err reset for a new solve.
+void prepare_control(ppcg_ctx* h, double tol, int32_t maxit, cudaStream_t st);
+// Device bytes a handle of this size will allocate (estimate used for admission).
+size_t footprint_bytes(int64_t n, int64_t nnz, int32_t precision);
+bool is_device_ptr(const void* p);
+
+}  // namespace ppcg

@@ -1,0 +1,360 @@
+// Continuous-batching solve server (ppcg_server_* in include/ppcg.h).
+//
+// Two host threads share one device:
+//   admitter  -- takes queued requests in arrival order while their device footprint fits
+//                in the HBM budget, builds the handle (CSR -> SELL on the device), stages b
+//                and x0, and hands the resident solve to the executor;
+//   executor  -- runs epochs: every resident CLUSTER-path solve advances by at most
+//                `epoch_iters` iterations inside one persistent cluster launch (their work
+//                overlaps on the device), each GRID-path solve gets one whole-GPU launch of
+//                the same budget; finished solves are copied out, their memory released,
+//                and requests that arrived meanwhile join at the next epoch.
+// A solve's vectors, scalars and control block stay on the device between epochs, and its
+// partition over CTAs depends only on its handle, so a result is bitwise the same alone or
+// in any mix.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <functional>
+#include <memory>
+#include <mutex>
+#include <queue>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "handle.h"
+
+namespace {
+
+using namespace ppcg;
+
+constexpr size_t kMaxQueue = 1 << 20;
+
+struct Request {
+  uint64_t ticket = 0;
+  int64_t n = 0, nnz = 0;
+  std::vector<int64_t> rp;
+  std::vector<int32_t> col;
+  std::vector<double> val, b, x0;
+  bool has_x0 = false;
+  double tol = 0.0;
+  int32_t maxit = 0;
+  size_t footprint = 0;
+};
+
+struct Slot {
+  uint64_t ticket = 0;
+  ppcg_handle h = nullptr;
+  double* xs = nullptr;       // device x the kernel writes
+  size_t footprint = 0;
+};
+
+struct Result {
+  int32_t status = PPCG_OK;
+  std::vector<double> x;
+  ppcg_info info;
+};
+
+}  // namespace
+
+struct ppcg_srv {
+  int device = 0;
+  ppcg_opts opts;
+  size_t budget = 0;
+  int epoch_iters = 256;
+  std::mutex mu;
+  std::condition_variable cv_admit, cv_exec;
+  std::deque<std::unique_ptr<Request>> queue;
+  std::vector<Slot> ready;
+  std::unordered_map<uint64_t, Result> done;
+  std::unordered_set<uint64_t> live;   // queued or running
+  size_t in_use = 0;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  int64_t completed = 0, running = 0;
+  std::thread admitter, executor;
+  cudaStream_t s_admit = nullptr, s_exec = nullptr;
+  // executor scratch for cluster epochs
+  SysDesc* d_descs = nullptr;
+  int32_t* d_lists = nullptr;
+  size_t cap = 0;
+};
+
+namespace {
+
+void finish(ppcg_srv* S, uint64_t ticket, Result&& r) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->done[ticket] = std::move(r);
+  S->live.erase(ticket);
+  S->completed++;
+}
+
+void admit_loop(ppcg_srv* S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    std::unique_ptr<Request> req;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_admit.wait(lk, [&] {
+        return S->stop || (!S->queue.empty() && S->in_use + S->queue.front()->footprint <= S->budget);
+      });
+      if (S->stop) return;
+      req = std::move(S->queue.front());
+      S->queue.pop_front();
+      S->in_use += req->footprint;
+      S->running++;
+    }
+    ppcg_handle h = nullptr;
+    ppcg_status st = ppcg_create(&h, req->n, req->nnz, req->rp.data(), req->col.data(), req->val.data(),
+                                 &S->opts, S->s_admit);
+    Slot slot;
+    slot.ticket = req->ticket;
+    slot.footprint = req->footprint;
+    if (st == PPCG_OK && req->n > 0) {
+      slot.h = h;
+      st = stage_inputs(h, req->b.data(), req->has_x0 ? req->x0.data() : nullptr, h->x_ws, false, S->s_admit,
+                        &slot.xs);
+      if (st == PPCG_OK) {
+        prepare_control(h, req->tol, req->maxit, S->s_admit);
+        cudaMemcpyAsync(h->d_desc, &h->desc, sizeof(SysDesc), cudaMemcpyHostToDevice, S->s_admit);
+        if (cudaStreamSynchronize(S->s_admit) != cudaSuccess) { cudaGetLastError(); st = PPCG_ERR_CUDA; }
+      }
+    }
+    if (st != PPCG_OK || req->n == 0) {
+      Result r;
+      memset(&r.info, 0, sizeof(r.info));
+      r.status = st;
+      r.info.status = st;
+      if (h) ppcg_destroy(h);
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->in_use -= req->footprint;
+        S->running--;
+      }
+      finish(S, req->ticket, std::move(r));
+      S->cv_admit.notify_all();
+      continue;
+    }
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->ready.push_back(slot);
+    }
+    S->cv_exec.notify_all();
+  }
+}
+
+bool run_cluster_epoch(ppcg_srv* S, const std::vector<Slot*>& slots) {
+  const int m = (int)slots.size();
+  if (m == 0) return true;
+  std::vector<SysDesc> descs(m);
+  std::vector<double> cost(m);
+  for (int k = 0; k < m; k++) {
+    descs[k] = slots[k]->h->desc;
+    cost[k] = (double)slots[k]->h->sell.nslots;
+  }
+  int nclusters = std::min(m, max_active_clusters(S->device));
+  std::vector<int> order(m);
+  for (int k = 0; k < m; k++) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  std::vector<std::vector<int>> lists(nclusters);
+  std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> pq;
+  for (int c = 0; c < nclusters; c++) pq.push({0.0, c});
+  for (int k : order) {
+    auto top = pq.top();
+    pq.pop();
+    lists[top.second].push_back(k);
+    pq.push({top.first + cost[k], top.second});
+  }
+  std::vector<int32_t> packed(1, 0), flat;
+  for (auto& l : lists) {
+    for (int k : l) flat.push_back(k);
+    packed.push_back((int32_t)flat.size());
+  }
+  const size_t nptr = packed.size();
+  packed.insert(packed.end(), flat.begin(), flat.end());
+  if ((size_t)m > S->cap || packed.size() > 2 * S->cap + 2) {
+    cudaFree(S->d_descs);
+    cudaFree(S->d_lists);
+    S->cap = std::max<size_t>(2 * (size_t)m, 64);
+    if (cudaMalloc(&S->d_descs, S->cap * sizeof(SysDesc)) != cudaSuccess ||
+        cudaMalloc(&S->d_lists, (2 * S->cap + 2) * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      S->cap = 0;
+      return false;
+    }
+  }
+  cudaMemcpyAsync(S->d_descs, descs.data(), m * sizeof(SysDesc), cudaMemcpyHostToDevice, S->s_exec);
+  cudaMemcpyAsync(S->d_lists, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice, S->s_exec);
+  return launch_clusters(S->d_descs, S->d_lists + nptr, S->d_lists, nclusters, S->epoch_iters, S->s_exec) ==
+         cudaSuccess;
+}
+
+void exec_loop(ppcg_srv* S) {
+  cudaSetDevice(S->device);
+  std::vector<Slot> active;
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_exec.wait(lk, [&] { return S->stop || !S->ready.empty() || !active.empty(); });
+      if (S->stop) break;
+      for (Slot& s : S->ready) active.push_back(s);
+      S->ready.clear();
+    }
+    std::vector<Slot*> cl, gr;
+    for (Slot& s : active) (s.h->path == PPCG_PATH_CLUSTER ? cl : gr).push_back(&s);
+    bool ok = run_cluster_epoch(S, cl);
+    for (Slot* s : gr) {
+      cudaMemsetAsync(s->h->bar, 0, sizeof(unsigned), S->s_exec);
+      ok = ok && launch_grid(s->h->d_desc, s->h->grid, S->epoch_iters, S->s_exec) == cudaSuccess;
+    }
+    for (Slot& s : active) {
+      cudaMemcpyAsync(&s.h->stage->ctl, s.h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, S->s_exec);
+      cudaMemcpyAsync(&s.h->stage->err, s.h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, S->s_exec);
+    }
+    if (cudaStreamSynchronize(S->s_exec) != cudaSuccess || !ok) {
+      cudaGetLastError();
+      // fail every resident solve rather than spin on a broken stream
+      for (Slot& s : active) { s.h->stage->ctl.state = S_DONE; s.h->stage->ctl.status = PPCG_ERR_CUDA; }
+    }
+    std::vector<Slot> keep;
+    for (Slot& s : active) {
+      const Stage& sg = *s.h->stage;
+      if (sg.ctl.state != S_DONE && sg.err == 0) { keep.push_back(s); continue; }
+      Result r;
+      r.x.resize(s.h->n);
+      stage_outputs(s.h, r.x.data(), s.xs, S->s_exec);
+      cudaStreamSynchronize(S->s_exec);
+      InfoJob j{s.h->stage, &r.info, s.h->bytes_per_iter, s.h->opts.norm, s.h->opts.precision};
+      fill_info(sg, j, &r.info);
+      r.status = r.info.status;
+      ppcg_destroy(s.h);
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->in_use -= s.footprint;
+        S->running--;
+      }
+      finish(S, s.ticket, std::move(r));
+      S->cv_admit.notify_all();
+    }
+    active.swap(keep);
+  }
+  for (Slot& s : active) ppcg_destroy(s.h);
+}
+
+}  // namespace
+
+extern "C" {
+
+ppcg_status ppcg_server_create(ppcg_server* server, size_t hbm_budget, const ppcg_opts* opts) {
+  if (!server) { set_error("ppcg_server_create: NULL"); return PPCG_ERR_ARG; }
+  *server = nullptr;
+  ppcg_srv* S = new ppcg_srv();
+  ppcg_opts_default(&S->opts);
+  if (opts) S->opts = *opts;
+  if (S->opts.epoch_iters > 0) S->epoch_iters = S->opts.epoch_iters;
+  cudaGetDevice(&S->device);
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    delete S;
+    set_error("ppcg_server_create: no CUDA device");
+    return PPCG_ERR_CUDA;
+  }
+  S->budget = hbm_budget ? hbm_budget : (size_t)(0.9 * (double)fr);
+  if (cudaStreamCreateWithFlags(&S->s_admit, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&S->s_exec, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete S;
+    set_error("ppcg_server_create: stream creation failed");
+    return PPCG_ERR_CUDA;
+  }
+  S->admitter = std::thread(admit_loop, S);
+  S->executor = std::thread(exec_loop, S);
+  *server = S;
+  return PPCG_OK;
+}
+
+ppcg_status ppcg_submit(ppcg_server S, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                        const double* val, const double* b, const double* x0, double tol, int32_t maxit,
+                        uint64_t* ticket) {
+  if (!S || !ticket || n < 0 || nnz < 0 || !(tol >= 0.0) || maxit < 0 ||
+      (n > 0 && (!row_ptr || !col || !val || !b))) {
+    set_error("ppcg_submit: bad arguments");
+    return PPCG_ERR_ARG;
+  }
+  auto req = std::make_unique<Request>();
+  req->n = n;
+  req->nnz = nnz;
+  req->rp.assign(row_ptr, row_ptr + (n + 1));
+  req->col.assign(col, col + nnz);
+  req->val.assign(val, val + nnz);
+  req->b.assign(b, b + n);
+  if (x0) { req->x0.assign(x0, x0 + n); req->has_x0 = true; }
+  req->tol = tol;
+  req->maxit = maxit;
+  req->footprint = footprint_bytes(n, nnz, S->opts.precision);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (req->footprint > S->budget) { set_error("ppcg_submit: request larger than the HBM budget"); return PPCG_ERR_OOM; }
+    if (S->queue.size() >= kMaxQueue) { set_error("ppcg_submit: queue full"); return PPCG_ERR_BUSY; }
+    req->ticket = S->next_ticket++;
+    *ticket = req->ticket;
+    S->live.insert(req->ticket);
+    S->queue.push_back(std::move(req));
+  }
+  S->cv_admit.notify_all();
+  return PPCG_OK;
+}
+
+ppcg_status ppcg_poll(ppcg_server S, uint64_t ticket, double* x_out, ppcg_info* info) {
+  if (!S) { set_error("ppcg_poll: NULL server"); return PPCG_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->done.find(ticket);
+  if (it == S->done.end()) {
+    if (S->live.count(ticket)) return PPCG_PENDING;
+    set_error("ppcg_poll: unknown ticket %llu", (unsigned long long)ticket);
+    return PPCG_ERR_UNKNOWN_TICKET;
+  }
+  Result& r = it->second;
+  if (x_out && !r.x.empty()) memcpy(x_out, r.x.data(), r.x.size() * sizeof(double));
+  if (info) *info = r.info;
+  ppcg_status st = (ppcg_status)r.status;
+  S->done.erase(it);
+  return st;
+}
+
+ppcg_status ppcg_server_stats(ppcg_server S, int64_t* completed, int64_t* running, int64_t* queued,
+                              int64_t* hbm_in_use) {
+  if (!S) { set_error("ppcg_server_stats: NULL server"); return PPCG_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (completed) *completed = S->completed;
+  if (running) *running = S->running;
+  if (queued) *queued = (int64_t)S->queue.size();
+  if (hbm_in_use) *hbm_in_use = (int64_t)S->in_use;
+  return PPCG_OK;
+}
+
+void ppcg_server_destroy(ppcg_server S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_admit.notify_all();
+  S->cv_exec.notify_all();
+  if (S->admitter.joinable()) S->admitter.join();
+  if (S->executor.joinable()) S->executor.join();
+  for (Slot& s : S->ready) ppcg_destroy(s.h);
+  cudaFree(S->d_descs);
+  cudaFree(S->d_lists);
+  cudaStreamDestroy(S->s_admit);
+  cudaStreamDestroy(S->s_exec);
+  delete S;
+}
+
+}  // extern "C"
