@@ -71,8 +71,9 @@ typedef struct {
   int32_t path;             /* ppcg_path.  GRID: one cooperative persistent launch over the whole GPU.
                                CLUSTER: one thread-block cluster per system.  AUTO picks by size. */
   int32_t sigma;            /* SELL sorting window in rows (0 = autotune, 1 = no sorting) */
-  int32_t rr_period;        /* residual replacement every rr_period iterations (0 = only when the
-                               recursive residual passes but the true residual does not) */
+  int32_t rr_period;        /* residual replacement every rr_period iterations.  FP64: 0 = only when the
+                               recursive residual passes but the true residual does not.  FP32_IR: the
+                               period inside each inner solve, 0 = 25 */
   double inner_tol;         /* FP32_IR: relative residual reduction asked of each inner solve */
   int32_t inner_maxit;      /* FP32_IR: iteration cap of one inner solve */
   int32_t max_outer;        /* FP32_IR: cap on refinement steps */
@@ -97,7 +98,7 @@ typedef struct {
 } ppcg_info;
 
 /* Fill *opts with defaults: FP64, AUTO format/path, REL_R, sigma autotune, rr_period 0,
- * inner_tol 1e-4, inner_maxit 100000, max_outer 30, spin_limit 10 s, cluster_max_rows 16384,
+ * inner_tol 1e-2, inner_maxit 100000, max_outer 30, spin_limit 10 s, cluster_max_rows 16384,
  * epoch_iters 256. */
 void ppcg_opts_default(ppcg_opts* opts);
 

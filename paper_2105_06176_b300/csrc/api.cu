@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <queue>
@@ -107,8 +108,8 @@ ppcg_status stage_inputs(ppcg_ctx* h, const double* b, const double* x0, double*
     cudaMemcpyAsync(h->b_ws, b, bytes, cudaMemcpyHostToDevice, st);
     bsol = h->b_ws;
   }
-  // x0 -> solver x (in place in the user's x when it is a device buffer and rows are not permuted)
-  double* xs = (!h->perm && xd) ? x : h->x_ws;
+  // x0 -> the solver's x (a slot of the handle's vector block, in solver row order)
+  double* xs = h->desc.x;
   int32_t x_zero = 0;
   if (!x0) {
     cudaMemsetAsync(xs, 0, bytes, st);
@@ -117,11 +118,10 @@ ppcg_status stage_inputs(ppcg_ctx* h, const double* b, const double* x0, double*
     const double* src = x0;
     if (!x0d) { cudaMemcpyAsync(h->tmp, x0, bytes, cudaMemcpyHostToDevice, st); src = h->tmp; }
     k_gather<<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, src, xs);
-  } else if (x0 != xs) {
+  } else {
     cudaMemcpyAsync(xs, x0, bytes, x0d ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
   }
   h->desc.b = bsol;
-  h->desc.x = xs;
   h->desc.x_zero = x_zero;
   *x_solver = xs;
   return PPCG_OK;
@@ -151,8 +151,8 @@ void prepare_control(ppcg_ctx* h, double tol, int32_t maxit, cudaStream_t st) {
 size_t footprint_bytes(int64_t n, int64_t nnz, int32_t precision) {
   const bool fp32 = precision == PPCG_FP32_IR;
   const double slots = 1.05 * (double)nnz + 32.0 * ((double)n / 32.0 + 1.0);
-  double bytes = slots * (fp32 ? 16.0 : 12.0) + (double)n * 8.0 * 8.0;   // matrix + cptr/diag/invd/b/x/tmp/perm
-  bytes += fp32 ? (double)n * (8.0 * 1 + 4.0 * 12) : (double)n * 8.0 * 8.0;
+  double bytes = slots * (fp32 ? 16.0 : 12.0) + (double)n * 8.0 * 6.0;   // matrix + cptr/diag/invd/b/tmp/perm
+  bytes += fp32 ? (double)n * (8.0 * 2 + 4.0 * 12 + 8.0) : (double)n * 8.0 * 10.0;
   return (size_t)bytes + (1u << 20);
 }
 
@@ -203,7 +203,7 @@ void ppcg_opts_default(ppcg_opts* o) {
   o->path = PPCG_PATH_AUTO;
   o->sigma = 0;
   o->rr_period = 0;
-  o->inner_tol = 1e-4;
+  o->inner_tol = 1e-2;
   o->inner_maxit = 100000;
   o->max_outer = 30;
   o->spin_limit_ns = 10000000000LL;
@@ -231,7 +231,7 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   if (h->opts.spin_limit_ns <= 0) h->opts.spin_limit_ns = 10000000000LL;
   if (h->opts.inner_maxit <= 0) h->opts.inner_maxit = 100000;
   if (h->opts.max_outer <= 0) h->opts.max_outer = 30;
-  if (!(h->opts.inner_tol > 0.0 && h->opts.inner_tol < 1.0)) h->opts.inner_tol = 1e-4;
+  if (!(h->opts.inner_tol > 0.0 && h->opts.inner_tol < 1.0)) h->opts.inner_tol = 1e-2;
   cudaGetDevice(&h->device);
   h->n = n;
   h->nnz = nnz;
@@ -273,7 +273,10 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   if (path == PPCG_PATH_AUTO) path = n <= h->opts.cluster_max_rows ? PPCG_PATH_CLUSTER : PPCG_PATH_GRID;
   h->path = path;
   if (path == PPCG_PATH_GRID) {
-    h->grid = grid_blocks_for_device(h->device);
+    h->shape = 0;
+    if (const char* e = getenv("PPCG_GRID_SHAPE")) h->shape = atoi(e);   // launch-shape tuning knob
+    if (h->shape < 0 || h->shape >= grid_shape_count()) h->shape = 0;
+    h->grid = grid_blocks_for_device(h->device, h->shape);
     h->nparts = h->grid;
   } else {
     h->grid = kClusterSize;
@@ -285,17 +288,25 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
 
   // Workspace.
   SysDesc& d = h->desc;
-  bool ok = walloc(h, &h->b_ws, n) && walloc(h, &h->x_ws, n) && walloc(h, &h->tmp, n) &&
-            walloc(h, &d.r, n) && walloc(h, &h->part, 2 * (size_t)h->nparts * 4) &&
-            walloc(h, &h->ctl, 1) && walloc(h, &h->bar, 1) && walloc(h, &h->err, 1) &&
-            walloc(h, &h->d_desc, 1);
-  if (ok && !fp32)
-    ok = walloc(h, &d.u, n) && walloc(h, &d.w0, n) && walloc(h, &d.w1, n) && walloc(h, &d.z, n) &&
-         walloc(h, &d.q, n) && walloc(h, &d.s, n) && walloc(h, &d.p, n);
-  if (ok && fp32)
-    ok = walloc(h, &d.r32, n) && walloc(h, &d.u32, n) && walloc(h, &d.w32a, n) && walloc(h, &d.w32b, n) &&
-         walloc(h, &d.z32, n) && walloc(h, &d.q32, n) && walloc(h, &d.s32, n) && walloc(h, &d.p32, n) &&
-         walloc(h, &d.d32, n) && walloc(h, &d.rhs32, n);
+  d.vs = (n + 63) / 64 * 64;            // keeps every vector 512-byte aligned
+  // FP64 block: r u wa wb z q s p x invd.  FP32_IR: FP64 block r64 x; FP32 block
+  // r u wa wb z q s p d invd rhs diag.
+  bool ok = walloc(h, &h->b_ws, n) && walloc(h, &h->tmp, n) &&
+            walloc(h, &h->part, 2 * (size_t)h->nparts * 4) && walloc(h, &h->ctl, 1) &&
+            walloc(h, &h->bar, 1) && walloc(h, &h->err, 1) && walloc(h, &h->d_desc, 1) &&
+            walloc(h, &d.v64, (size_t)d.vs * (fp32 ? 2 : 10));
+  if (ok && fp32) ok = walloc(h, &d.v32, (size_t)d.vs * 12);
+  if (ok) {
+    d.x = d.v64 + (fp32 ? 1 : 8) * d.vs;
+    h->x_ws = d.x;
+    if (fp32) {
+      cudaMemcpyAsync(d.v32 + 9 * d.vs, h->A.invd32, n * sizeof(float), cudaMemcpyDeviceToDevice, stream);
+      cudaMemcpyAsync(d.v32 + 11 * d.vs, h->A.diag32, n * sizeof(float), cudaMemcpyDeviceToDevice, stream);
+    } else {
+      cudaMemcpyAsync(d.v64 + 9 * d.vs, h->A.invd, n * sizeof(double), cudaMemcpyDeviceToDevice, stream);
+    }
+    ok = cudaStreamSynchronize(stream) == cudaSuccess;
+  }
   if (ok && cudaMallocHost((void**)&h->stage, sizeof(Stage)) != cudaSuccess) { cudaGetLastError(); ok = false; }
   if (!ok) {
     free_all(h);
@@ -307,7 +318,9 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   d.A = h->A;
   d.precision = h->opts.precision;
   d.norm = h->opts.norm;
-  d.rr_period = h->opts.rr_period;
+  // FP32 pipelined recurrences drift far faster than FP64 ones: replace residuals in the
+  // inner solve every 25 iterations unless the caller chose a period.
+  d.rr_period = fp32 && h->opts.rr_period == 0 ? 25 : h->opts.rr_period;
   d.inner_maxit = h->opts.inner_maxit;
   d.max_outer = h->opts.max_outer;
   d.inner_tol = h->opts.inner_tol;
@@ -337,7 +350,7 @@ ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double*
   cudaMemcpyAsync(h->d_desc, &h->desc, sizeof(SysDesc), cudaMemcpyHostToDevice, st);
   cudaError_t e;
   if (h->path == PPCG_PATH_GRID) {
-    e = launch_grid(h->d_desc, h->grid, 0, st);
+    e = launch_grid(h->d_desc, h->shape, h->grid, 0, st);
   } else {
     // one cluster, work list {0}: device array {0, 0, 1} = list[0], list_ptr[0..1]
     static int32_t* d_list = nullptr;
@@ -444,7 +457,7 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
   for (int i : gr) {
     ppcg_ctx* h = hs[i];
     cudaMemcpyAsync(h->d_desc, &h->desc, sizeof(SysDesc), cudaMemcpyHostToDevice, st);
-    cudaError_t e = launch_grid(h->d_desc, h->grid, 0, st);
+    cudaError_t e = launch_grid(h->d_desc, h->shape, h->grid, 0, st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error("ppcg_batch_solve: launch failed: %s", cudaGetErrorString(e));

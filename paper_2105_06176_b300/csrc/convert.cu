@@ -3,7 +3,10 @@
 //
 // The solver keeps the matrix column-scaled, Ahat = A D^-1, so that the preconditioner
 // apply and the SpMV of Alg. 2 lines 21-22 (m = M^-1 w; n = A m) become one product
-// n = Ahat w with no per-iteration multiply by D^-1 inside the gather.
+// n = Ahat w with no per-iteration multiply by D^-1 inside the gather.  The scaling divides
+// (a_ij / a_jj), so every diagonal entry of Ahat is exactly 1.0: the SELL arrays hold the
+// off-diagonal entries only and the kernels add the diagonal term (w_i, or a_ii v_i for
+// A v) exactly, as the first term of each row sum.
 #include <algorithm>
 #include <chrono>
 #include <numeric>
@@ -33,22 +36,24 @@ __global__ void k_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
   if (e - a > INT32_MAX) { f |= F_ARG; e = a; }
   double d = 0.0;
   bool found = false;
+  int32_t off = 0;
   for (int64_t k = a; k < e; k++) {
     int32_t c = col[k];
     if (c < 0 || c >= n) f |= F_ARG;
-    if (c == i) { d += val[k]; found = true; }
+    if (c == i) { d += val[k]; found = true; } else { off++; }
   }
   if (!found || !(d > 0.0)) f |= F_NOT_SPD;
-  rowlen[i] = (int32_t)(e - a);
+  rowlen[i] = off;          // off-diagonal entries of the row
   diag[i] = d;
   invd[i] = found && d > 0.0 ? 1.0 / d : 0.0;
   if (f) atomicOr(flags, f);
 }
 
-// One thread per (chunk row): write the row's slots, column-major inside its chunk.
+// One thread per (chunk row): write the row's off-diagonal slots, column-major inside its
+// chunk, in CSR order.
 __global__ void k_fill(int64_t n, int64_t nchunks, const int64_t* __restrict__ rp,
                        const int32_t* __restrict__ col, const double* __restrict__ val,
-                       const double* __restrict__ invd, const int32_t* __restrict__ rowlen,
+                       const double* __restrict__ diag, const int32_t* __restrict__ rowlen,
                        const int32_t* __restrict__ perm, const int32_t* __restrict__ iperm,
                        const int64_t* __restrict__ cptr, int32_t* __restrict__ scol,
                        double* __restrict__ sval, float* __restrict__ sval32) {
@@ -60,23 +65,24 @@ __global__ void k_fill(int64_t n, int64_t nchunks, const int64_t* __restrict__ r
   int64_t base = cptr[c];
   int len = (int)((cptr[c + 1] - base) / kChunk);
   int64_t o = i < n ? (perm ? perm[i] : i) : 0;
-  int L = i < n ? rowlen[o] : 0;
   int64_t a = i < n ? rp[o] : 0;
-  for (int j = 0; j < len; j++) {
+  int64_t e = i < n ? rp[o + 1] : 0;
+  int j = 0;
+  for (int64_t k = a; k < e; k++) {
+    int32_t oc = col[k];
+    if (oc == o) continue;                       // diagonal: implicit, exactly 1 after scaling
     int64_t slot = base + (int64_t)j * kChunk + lane;
-    int32_t cc;
-    double v;
-    if (j < L) {
-      int32_t oc = col[a + j];
-      v = val[a + j] * invd[oc];
-      cc = iperm ? iperm[oc] : oc;
-    } else {              // padding: a zero that gathers the row's own entry
-      cc = (int32_t)(i < n ? i : n - 1);
-      v = 0.0;
-    }
-    scol[slot] = cc;
+    double v = val[k] / diag[oc];
+    scol[slot] = iperm ? iperm[oc] : oc;
     sval[slot] = v;
     if (sval32) sval32[slot] = (float)v;
+    j++;
+  }
+  for (; j < len; j++) {                         // padding: a zero that gathers the row's own entry
+    int64_t slot = base + (int64_t)j * kChunk + lane;
+    scol[slot] = (int32_t)(i < n ? i : n - 1);
+    sval[slot] = 0.0;
+    if (sval32) sval32[slot] = 0.0f;
   }
 }
 
@@ -205,7 +211,7 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
     // keep iperm alive until the copies and the fill kernel complete (sync below)
     cudaMemcpyAsync(d_cptr, cptr.data(), (nchunks + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
     int64_t threads = nchunks * kChunk;
-    k_fill<<<(unsigned)((threads + tb - 1) / tb), tb, 0, st>>>(n, nchunks, d_rp, d_col, d_val, d_invd0,
+    k_fill<<<(unsigned)((threads + tb - 1) / tb), tb, 0, st>>>(n, nchunks, d_rp, d_col, d_val, d_diag0,
                                                                d_len, d_perm, d_iperm, d_cptr, d_scol,
                                                                d_sval, d_sval32);
     k_permute_diag<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(n, d_perm, d_diag0, d_invd0, d_sdiag,
@@ -214,7 +220,7 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   } else {
     cudaMemcpyAsync(d_cptr, cptr.data(), (nchunks + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
     int64_t threads = nchunks * kChunk;
-    k_fill<<<(unsigned)((threads + tb - 1) / tb), tb, 0, st>>>(n, nchunks, d_rp, d_col, d_val, d_invd0,
+    k_fill<<<(unsigned)((threads + tb - 1) / tb), tb, 0, st>>>(n, nchunks, d_rp, d_col, d_val, d_diag0,
                                                                d_len, nullptr, nullptr, d_cptr, d_scol,
                                                                d_sval, d_sval32);
     k_permute_diag<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(n, nullptr, d_diag0, d_invd0, d_sdiag,
@@ -242,7 +248,7 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   out->nchunks = nchunks;
   out->nslots = nslots;
   out->sigma = (int32_t)sigma;
-  out->padding = nnz > 0 ? (double)(nslots - nnz) / (double)nnz : 0.0;
+  out->padding = nnz > n ? (double)(nslots - (nnz - n)) / (double)(nnz - n) : 0.0;
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return PPCG_OK;
 }

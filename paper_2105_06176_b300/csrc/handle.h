@@ -54,6 +54,7 @@ struct ppcg_ctx {
   int32_t* perm = nullptr;
   std::vector<void*> allocs;
   int32_t path = PPCG_PATH_GRID;
+  int shape = 0;       // grid-path launch shape (index into the kernel variants)
   int grid = 0;        // CTAs of the grid path
   int nparts = 0;      // partial slots per pass (CTAs in the group)
   double bytes_per_iter = 0.0;

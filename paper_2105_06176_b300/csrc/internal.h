@@ -9,7 +9,6 @@
 namespace ppcg {
 
 constexpr int kChunk = 32;           // SELL-C-sigma chunk height C: one warp lane per row
-constexpr int kGridThreads = 512;    // CTA size of the whole-GPU (grid) path
 constexpr int kClusterThreads = 256; // CTA size of the cluster path
 constexpr int kClusterSize = 8;      // CTAs per thread-block cluster (portable maximum)
 
@@ -72,10 +71,12 @@ struct SysDesc {
   int64_t spin_limit_ns;
   const double* b;       // solver order
   double* x;             // solver order (FP64 solution, holds x0 at start)
-  // FP64 Krylov vectors (FP64 path) -- r also serves as r64 in FP32_IR
-  double *r, *u, *w0, *w1, *z, *q, *s, *p;
-  // FP32 Krylov vectors (FP32_IR inner solve)
-  float *r32, *u32, *w32a, *w32b, *z32, *q32, *s32, *p32, *d32, *rhs32;
+  // Per-row vectors, each vs elements apart in one allocation:
+  //   v64: r u wa wb z q s p x invd (FP64 path); in FP32_IR: r64 x (outer residual, solution)
+  //   v32: r u wa wb z q s p d invd rhs diag (FP32_IR inner solve; d is the inner solution)
+  double* v64;
+  float* v32;
+  int64_t vs;
   double* part;          // [2][nparts][4] block partials, double-buffered by pass parity
   Ctl* ctl;
   unsigned* bar;         // grid barrier arrival counter (grid path; zeroed before each launch)
@@ -83,10 +84,11 @@ struct SysDesc {
 };
 
 // Launchers (solver.cu)
-cudaError_t launch_grid(const SysDesc* d_desc, int grid, int budget, cudaStream_t st);
+cudaError_t launch_grid(const SysDesc* d_desc, int shape, int grid, int budget, cudaStream_t st);
 cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
                             int nclusters, int budget, cudaStream_t st);
-int grid_blocks_for_device(int device);
+int grid_shape_count();
+int grid_blocks_for_device(int device, int shape);
 int max_active_clusters(int device);
 cudaError_t launch_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, int grid,
                                     int drop_rank, int64_t limit_ns, cudaStream_t st);
@@ -95,7 +97,7 @@ cudaError_t launch_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, i
 struct SellBuild {
   int64_t nchunks = 0, nslots = 0;
   int32_t sigma = 1;
-  double padding = 0.0;   // (nslots - nnz) / nnz
+  double padding = 0.0;   // padded slots / off-diagonal nonzeros
   double seconds = 0.0;   // conversion wall time
 };
 ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col,

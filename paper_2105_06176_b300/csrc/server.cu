@@ -210,7 +210,7 @@ void exec_loop(ppcg_srv* S) {
     bool ok = run_cluster_epoch(S, cl);
     for (Slot* s : gr) {
       cudaMemsetAsync(s->h->bar, 0, sizeof(unsigned), S->s_exec);
-      ok = ok && launch_grid(s->h->d_desc, s->h->grid, S->epoch_iters, S->s_exec) == cudaSuccess;
+      ok = ok && launch_grid(s->h->d_desc, s->h->shape, s->h->grid, S->epoch_iters, S->s_exec) == cudaSuccess;
     }
     for (Slot& s : active) {
       cudaMemcpyAsync(&s.h->stage->ctl, s.h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, S->s_exec);

@@ -130,21 +130,38 @@ template <typename T> __device__ __forceinline__ T ldcs(const T* p) { return __l
 template <typename T> __device__ __forceinline__ void stcs(T* p, T v) { __stcs(p, v); }
 template <typename T> __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 
-// sum_j val[slot_j] * x[col[slot_j]] (* dsc[col] when SCALE), slots base + j*32, j < len,
-// accumulated in slot order (the CSR order of the row).  Gathers use ld.global.cg: the
-// gathered vector was written by other CTAs in the previous pass.
+// Streaming load of read-only matrix data: no L1 allocation, so L1 stays with the gathers.
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
+  int32_t v;
+  asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
+// acc + sum_j val[slot_j] * x[col[slot_j]] (* dsc[col] when SCALE) over the row's
+// off-diagonal slots base + j*32, j < len, in CSR order; acc enters holding the diagonal
+// term.  Gathers use ld.global.cg: the gathered vector was written by other CTAs in the
+// previous pass.
 template <typename T, bool SCALE>
 __device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* __restrict__ val,
-                                     const T* x, const T* __restrict__ dsc, int64_t base, int len) {
-  T acc = T(0);
+                                     const T* x, const T* __restrict__ dsc, int64_t base, int len, T acc) {
   int j = 0;
   for (; j + 8 <= len; j += 8) {
     int32_t c[8];
     T a[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-      c[k] = __ldg(col + base + (int64_t)(j + k) * kChunk);
-      a[k] = __ldg(val + base + (int64_t)(j + k) * kChunk);
+      c[k] = ld_stream(col + base + (int64_t)(j + k) * kChunk);
+      a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
 #pragma unroll
     for (int k = 0; k < 8; k++) {
@@ -158,8 +175,8 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* _
 #pragma unroll
   for (int k = 0; k < 7; k++) {
     if (j + k < len) {
-      c[k] = __ldg(col + base + (int64_t)(j + k) * kChunk);
-      a[k] = __ldg(val + base + (int64_t)(j + k) * kChunk);
+      c[k] = ld_stream(col + base + (int64_t)(j + k) * kChunk);
+      a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
   }
 #pragma unroll
@@ -173,52 +190,80 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* _
   return acc;
 }
 
-// Per-precision view of the Krylov vectors and matrix arrays.
+// Per-precision view of the Krylov vectors and matrix arrays.  The recurrence vectors, the
+// solution and D^-1 live vs elements apart from one base pointer, so a pass addresses
+// every per-row array from (base + row) and a constant slot stride instead of holding a
+// pointer per vector in registers.
+//   FP64 block: r u wa wb z q s p x invd
+//   FP32 block: r u wa wb z q s p d invd rhs diag   (d: the inner solution)
+enum { V_R = 0, V_U, V_WA, V_WB, V_Z, V_Q, V_S, V_P, V_X, V_INVD, V_RHS, V_DIAG };
 template <typename T> struct Vec {
-  const T* val; const T* invd; const T* diag; const T* rhs;
-  T* xs; T *r, *u, *wa, *wb, *z, *q, *s, *p;
+  const T* val; const T* diag; const T* rhs;
+  T* vb; int64_t vs;
+  __device__ __forceinline__ T* at(int k) const { return vb + (int64_t)k * vs; }
 };
 
 __device__ __forceinline__ Vec<double> vec64(const SysDesc& S) {
-  return {S.A.val, S.A.invd, S.A.diag, S.b, S.x, S.r, S.u, S.w0, S.w1, S.z, S.q, S.s, S.p};
+  return {S.A.val, S.A.diag, S.b, S.v64, S.vs};
 }
 __device__ __forceinline__ Vec<float> vec32(const SysDesc& S) {
-  return {S.A.val32, S.A.invd32, S.A.diag32, S.rhs32, S.d32, S.r32, S.u32, S.w32a, S.w32b,
-          S.z32, S.q32, S.s32, S.p32};
+  return {S.A.val32, S.v32 + V_DIAG * S.vs, S.v32 + V_RHS * S.vs, S.v32, S.vs};
 }
 
 struct Lanes {
-  int64_t gw, W;   // global warp id within the group, warps in the group
-  int lane;
+  int32_t gw, W;   // global warp id within the group, warps in the group (chunk indices < 2^26)
+  int32_t lane;
 };
 
-#define FOR_CHUNKS(A, L)                                                               \
-  for (int64_t c = (L).gw; c < (A).nchunks; c += (L).W)
+// Walks the group's chunks (warp gw, gw + W, ...) with the next chunk's slot range loaded
+// one step ahead.
+struct ChunkIter {
+  const int64_t* cptr;
+  int32_t c, W, nchunks, len, nlen;
+  int64_t b0, nb0;
+  __device__ __forceinline__ ChunkIter(const DevMatrix& A, const Lanes& L)
+      : cptr(A.cptr), c(L.gw), W(L.W), nchunks((int32_t)A.nchunks), len(0), nlen(0), b0(0), nb0(0) {
+    if (c < nchunks) {
+      b0 = __ldg(cptr + c);
+      len = (int32_t)((__ldg(cptr + c + 1) - b0) / kChunk);
+    }
+    prefetch();
+  }
+  __device__ __forceinline__ void prefetch() {
+    if (c + W < nchunks) {
+      nb0 = __ldg(cptr + c + W);
+      nlen = (int32_t)((__ldg(cptr + c + W + 1) - nb0) / kChunk);
+    }
+  }
+  __device__ __forceinline__ bool ok() const { return c < nchunks; }
+  __device__ __forceinline__ void next() { c += W; b0 = nb0; len = nlen; prefetch(); }
+};
 
-__device__ __forceinline__ void chunk_range(const DevMatrix& A, int64_t c, int lane, int64_t& base,
-                                            int& len) {
-  int64_t b0 = __ldg(A.cptr + c);
-  len = (int)((__ldg(A.cptr + c + 1) - b0) / kChunk);
-  base = b0 + lane;
-}
+#define FOR_CHUNKS(A, L) for (ChunkIter it(A, L); it.ok(); it.next())
+#define CHUNK_ROW(L) (it.c * kChunk + (L).lane)
+#define CHUNK_BASE(L) (it.b0 + (L).lane)
 
 // -------------------------------------------------------------------------- passes --
 
 // P_SETUP1 (FP64), Alg. 2 line 1: r0 = b - A x0 ; u0 = M^-1 r0.  Partials (b,b), (r,r).
-__device__ __noinline__ void pass_setup1(const SysDesc& S, const Lanes& L, Dots<double>& d, bool x_zero) {
+__device__ __forceinline__ void pass_setup1(const SysDesc& S, const Lanes& L, Dots<double>& d, bool x_zero) {
   const DevMatrix& A = S.A;
   FOR_CHUNKS(A, L) {
-    int64_t base; int len;
-    chunk_range(A, c, L.lane, base, len);
-    int64_t row = c * kChunk + L.lane;
-    double ax = 0.0;
-    if (!x_zero) ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len);
-    if (row < A.n) {
-      double bi = __ldg(S.b + row);
+    const int64_t base = CHUNK_BASE(L);
+    const int len = it.len;
+    const int32_t row = CHUNK_ROW(L);
+    const bool in = row < A.n;
+    double ax = 0.0, bi = 0.0, id = 0.0;
+    if (in) {
+      bi = __ldg(S.b + row);
+      id = __ldg(S.v64 + V_INVD * S.vs + row);
+      if (!x_zero) ax = __ldg(A.diag + row) * ldcg(S.x + row);
+    }
+    if (!x_zero) ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len, ax);
+    if (in) {
       double ri = bi - ax;
-      double ui = __ldg(A.invd + row) * ri;
-      stcs(S.r + row, ri);
-      stcs(S.u + row, ui);
+      stcs(S.v64 + V_R * S.vs + row, ri);
+      stcs(S.v64 + V_U * S.vs + row, id * ri);
       d.add(0, bi, bi);
       d.add(1, ri, ri);
     }
@@ -227,17 +272,18 @@ __device__ __noinline__ void pass_setup1(const SysDesc& S, const Lanes& L, Dots<
 
 // P_SETUP2, Alg. 2 lines 1-2: w0 = A u0 (= Ahat r0) ; partials (r,u), (w,u), norm.
 template <typename T>
-__device__ __noinline__ void pass_setup2(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d,
-                            bool paper_norm) {
-  const T* val = v.val;
+__device__ __forceinline__ void pass_setup2(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d,
+                                         bool paper_norm) {
   FOR_CHUNKS(A, L) {
-    int64_t base; int len;
-    chunk_range(A, c, L.lane, base, len);
-    int64_t row = c * kChunk + L.lane;
-    T wi = row_dot<T, false>(A.col, val, v.r, nullptr, base, len);
-    if (row < A.n) {
-      T ri = ldcs(v.r + row), ui = ldcs(v.u + row);
-      stcs(v.wa + row, wi);
+    const int64_t base = CHUNK_BASE(L);
+    const int len = it.len;
+    const int32_t row = CHUNK_ROW(L);
+    const bool in = row < A.n;
+    T ri = T(0), ui = T(0);
+    if (in) { ri = ldcg(v.at(V_R) + row); ui = ldcs(v.at(V_U) + row); }
+    T wi = row_dot<T, false>(A.col, v.val, v.at(V_R), nullptr, base, len, ri);
+    if (in) {
+      stcs(v.at(V_WA) + row, wi);
       d.add(0, ri, ui);
       d.add(1, wi, ui);
       if (paper_norm) d.add(2, ui, ui); else d.add(2, ri, ri);
@@ -245,43 +291,63 @@ __device__ __noinline__ void pass_setup2(const DevMatrix& A, const Vec<T>& v, co
   }
 }
 
-// P_ITER: one full iteration of Alg. 2 for the group's rows (see the file comment).
-template <typename T>
-__device__ __noinline__ void pass_iter(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d, T alpha,
-                          T beta, bool first, int k, bool paper_norm) {
-  const T* wc = (k & 1) ? v.wb : v.wa;
-  T* wn = (k & 1) ? v.wa : v.wb;
-  const T* val = v.val;
-  FOR_CHUNKS(A, L) {
-    int64_t base; int len;
-    chunk_range(A, c, L.lane, base, len);
-    int64_t row = c * kChunk + L.lane;
-    T ni = row_dot<T, false>(A.col, val, wc, nullptr, base, len);
-    if (row < A.n) {
-      T wi = ldcg(wc + row);
-      T mi = __ldg(v.invd + row) * wi;
-      T ui = ldcs(v.u + row);
-      T xi = ldcs(v.xs + row);
-      T ri = ldcs(v.r + row);
-      T zi = ni, qi = mi, si = wi, pi = ui;
-      if (!first) {
-        zi = fma(beta, ldcs(v.z + row), ni);
-        qi = fma(beta, ldcs(v.q + row), mi);
-        si = fma(beta, ldcs(v.s + row), wi);
-        pi = fma(beta, ldcs(v.p + row), ui);
+// P_ITER: one full iteration of Alg. 2 for the group's rows (see the file comment).  The
+// row's own vector entries are loaded before the gather so their latency overlaps it;
+// every per-row array is addressed from one pointer (pr) plus a slot stride.
+template <typename T, bool FIRST>
+__device__ __forceinline__ void pass_iter(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d,
+                                          T alpha, T beta, int k, bool paper_norm) {
+  const int64_t* __restrict__ cptr = A.cptr;
+  const int32_t* __restrict__ col = A.col;
+  const T* __restrict__ val = v.val;
+  T* const vb = v.vb;
+  const int64_t vs = v.vs;
+  const int32_t n = (int32_t)A.n;
+  const int wcs = (k & 1) ? V_WB : V_WA;
+  const int wns = (k & 1) ? V_WA : V_WB;
+  const T* wc = vb + wcs * vs;
+  const int32_t nchunks = (int32_t)A.nchunks;
+  for (int32_t c = L.gw; c < nchunks; c += L.W) {
+    const int64_t b0 = __ldg(cptr + c);
+    const int len = (int)((__ldg(cptr + c + 1) - b0) / kChunk);
+    const int32_t row = c * kChunk + L.lane;
+    const bool in = row < n;
+    T* pr = vb + row;
+    T wi = T(0), id = T(0), ui = T(0), xi = T(0), ri = T(0);
+    T zo = T(0), qo = T(0), so = T(0), po = T(0);
+    if (in) {
+      wi = ldcg(pr + wcs * vs);
+      id = ldcs(pr + V_INVD * vs);
+      ui = ldcs(pr + V_U * vs);
+      xi = ldcs(pr + V_X * vs);
+      ri = ldcs(pr + V_R * vs);
+      if (!FIRST) {
+        zo = ldcs(pr + V_Z * vs);
+        qo = ldcs(pr + V_Q * vs);
+        so = ldcs(pr + V_S * vs);
+        po = ldcs(pr + V_P * vs);
       }
+    }
+    // n_i = (A M^-1 w)_i = w_i + sum_{j != i} ahat_ij w_j
+    const T ni = row_dot<T, false>(col, val, wc, nullptr, b0 + L.lane, len, wi);
+    if (in) {
+      const T mi = id * wi;
+      const T zi = FIRST ? ni : fma(beta, zo, ni);
+      const T qi = FIRST ? mi : fma(beta, qo, mi);
+      const T si = FIRST ? wi : fma(beta, so, wi);
+      const T pi = FIRST ? ui : fma(beta, po, ui);
       xi = fma(alpha, pi, xi);
       ri = fma(-alpha, si, ri);
-      T un = fma(-alpha, qi, ui);
-      T wnn = fma(-alpha, zi, wi);
-      stcs(v.z + row, zi);
-      stcs(v.q + row, qi);
-      stcs(v.s + row, si);
-      stcs(v.p + row, pi);
-      stcs(v.xs + row, xi);
-      stcs(v.r + row, ri);
-      stcs(v.u + row, un);
-      stcs(wn + row, wnn);
+      const T un = fma(-alpha, qi, ui);
+      const T wnn = fma(-alpha, zi, wi);
+      stcs(pr + V_Z * vs, zi);
+      stcs(pr + V_Q * vs, qi);
+      stcs(pr + V_S * vs, si);
+      stcs(pr + V_P * vs, pi);
+      stcs(pr + V_X * vs, xi);
+      stcs(pr + V_R * vs, ri);
+      stcs(pr + V_U * vs, un);
+      stcs(pr + wns * vs, wnn);
       d.add(0, ri, un);
       d.add(1, wnn, un);
       if (paper_norm) d.add(2, un, un); else d.add(2, ri, ri);
@@ -290,15 +356,18 @@ __device__ __noinline__ void pass_iter(const DevMatrix& A, const Vec<T>& v, cons
 }
 
 // P_TRUE (FP64): partial ||b - A x||^2.
-__device__ __noinline__ void pass_true(const SysDesc& S, const Lanes& L, Dots<double>& d) {
+__device__ __forceinline__ void pass_true(const SysDesc& S, const Lanes& L, Dots<double>& d) {
   const DevMatrix& A = S.A;
   FOR_CHUNKS(A, L) {
-    int64_t base; int len;
-    chunk_range(A, c, L.lane, base, len);
-    int64_t row = c * kChunk + L.lane;
-    double ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len);
-    if (row < A.n) {
-      double t = __ldg(S.b + row) - ax;
+    const int64_t base = CHUNK_BASE(L);
+    const int len = it.len;
+    const int32_t row = CHUNK_ROW(L);
+    const bool in = row < A.n;
+    double ax = 0.0, bi = 0.0;
+    if (in) { bi = __ldg(S.b + row); ax = __ldg(A.diag + row) * ldcg(S.x + row); }
+    ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len, ax);
+    if (in) {
+      double t = bi - ax;
       d.add(0, t, t);
     }
   }
@@ -307,40 +376,49 @@ __device__ __noinline__ void pass_true(const SysDesc& S, const Lanes& L, Dots<do
 // P_RR1: residual replacement, first half: r = rhs - A xs ; u = M^-1 r ; s = A p ; q = M^-1 s.
 // (At iteration 0 p is zero, so s = q = 0.)
 template <typename T>
-__device__ __noinline__ void pass_rr1(const DevMatrix& A, const Vec<T>& v, const Lanes& L, bool p_zero) {
+__device__ __forceinline__ void pass_rr1(const DevMatrix& A, const Vec<T>& v, const Lanes& L, bool p_zero) {
   FOR_CHUNKS(A, L) {
-    int64_t base; int len;
-    chunk_range(A, c, L.lane, base, len);
-    int64_t row = c * kChunk + L.lane;
-    T ax = row_dot<T, true>(A.col, v.val, v.xs, v.diag, base, len);
-    T ap = T(0);
-    if (!p_zero) ap = row_dot<T, true>(A.col, v.val, v.p, v.diag, base, len);
-    if (row < A.n) {
-      T id = __ldg(v.invd + row);
-      T ri = __ldg(v.rhs + row) - ax;
-      stcs(v.r + row, ri);
-      stcs(v.u + row, id * ri);
-      stcs(v.s + row, ap);
-      stcs(v.q + row, id * ap);
+    const int64_t base = CHUNK_BASE(L);
+    const int len = it.len;
+    const int32_t row = CHUNK_ROW(L);
+    const bool in = row < A.n;
+    T ax = T(0), ap = T(0), id = T(0), rh = T(0);
+    if (in) {
+      const T di = __ldg(v.diag + row);
+      id = __ldg(v.at(V_INVD) + row);
+      rh = __ldg(v.rhs + row);
+      ax = di * ldcg(v.at(V_X) + row);
+      if (!p_zero) ap = di * ldcg(v.at(V_P) + row);
+    }
+    ax = row_dot<T, true>(A.col, v.val, v.at(V_X), v.diag, base, len, ax);
+    if (!p_zero) ap = row_dot<T, true>(A.col, v.val, v.at(V_P), v.diag, base, len, ap);
+    if (in) {
+      const T ri = rh - ax;
+      stcs(v.at(V_R) + row, ri);
+      stcs(v.at(V_U) + row, id * ri);
+      stcs(v.at(V_S) + row, ap);
+      stcs(v.at(V_Q) + row, id * ap);
     }
   }
 }
 
 // P_RR2: w = A u (= Ahat r) ; z = A q (= Ahat s) ; partials (r,u), (w,u), norm.
 template <typename T>
-__device__ __noinline__ void pass_rr2(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d, int k,
-                         bool paper_norm) {
-  T* wc = (k & 1) ? v.wb : v.wa;
+__device__ __forceinline__ void pass_rr2(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d, int k,
+                                      bool paper_norm) {
+  T* wc = v.at((k & 1) ? V_WB : V_WA);
   FOR_CHUNKS(A, L) {
-    int64_t base; int len;
-    chunk_range(A, c, L.lane, base, len);
-    int64_t row = c * kChunk + L.lane;
-    T wi = row_dot<T, false>(A.col, v.val, v.r, nullptr, base, len);
-    T zi = row_dot<T, false>(A.col, v.val, v.s, nullptr, base, len);
-    if (row < A.n) {
-      T ri = ldcs(v.r + row), ui = ldcs(v.u + row);
+    const int64_t base = CHUNK_BASE(L);
+    const int len = it.len;
+    const int32_t row = CHUNK_ROW(L);
+    const bool in = row < A.n;
+    T ri = T(0), ui = T(0), si = T(0);
+    if (in) { ri = ldcg(v.at(V_R) + row); ui = ldcs(v.at(V_U) + row); si = ldcg(v.at(V_S) + row); }
+    const T wi = row_dot<T, false>(A.col, v.val, v.at(V_R), nullptr, base, len, ri);
+    const T zi = row_dot<T, false>(A.col, v.val, v.at(V_S), nullptr, base, len, si);
+    if (in) {
       stcs(wc + row, wi);
-      stcs(v.z + row, zi);
+      stcs(v.at(V_Z) + row, zi);
       d.add(0, ri, ui);
       d.add(1, wi, ui);
       if (paper_norm) d.add(2, ui, ui); else d.add(2, ri, ri);
@@ -348,25 +426,27 @@ __device__ __noinline__ void pass_rr2(const DevMatrix& A, const Vec<T>& v, const
   }
 }
 
-__device__ __noinline__ void pass_zero_x(const SysDesc& S, const Lanes& L) {
+__device__ __forceinline__ void pass_zero_x(const SysDesc& S, const Lanes& L) {
   FOR_CHUNKS(S.A, L) {
-    int64_t row = c * kChunk + L.lane;
+    const int32_t row = CHUNK_ROW(L);
     if (row < S.A.n) S.x[row] = 0.0;
   }
 }
 
 // P_ORES (FP32_IR outer step): r64 = b - A x in FP64 ; partials (r64,r64), (b,b).
-__device__ __noinline__ void pass_ores(const SysDesc& S, const Lanes& L, Dots<double>& d) {
+__device__ __forceinline__ void pass_ores(const SysDesc& S, const Lanes& L, Dots<double>& d) {
   const DevMatrix& A = S.A;
   FOR_CHUNKS(A, L) {
-    int64_t base; int len;
-    chunk_range(A, c, L.lane, base, len);
-    int64_t row = c * kChunk + L.lane;
-    double ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len);
-    if (row < A.n) {
-      double bi = __ldg(S.b + row);
+    const int64_t base = CHUNK_BASE(L);
+    const int len = it.len;
+    const int32_t row = CHUNK_ROW(L);
+    const bool in = row < A.n;
+    double ax = 0.0, bi = 0.0;
+    if (in) { bi = __ldg(S.b + row); ax = __ldg(A.diag + row) * ldcg(S.x + row); }
+    ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len, ax);
+    if (in) {
       double t = bi - ax;
-      stcs(S.r + row, t);
+      stcs(S.v64 + row, t);
       d.add(0, t, t);
       d.add(1, bi, bi);
     }
@@ -374,24 +454,24 @@ __device__ __noinline__ void pass_ores(const SysDesc& S, const Lanes& L, Dots<do
 }
 
 // P_OINIT: rhs32 = r64 / ||r64|| ; r32 = rhs32 ; u32 = M^-1 r32 ; d32 = 0.
-__device__ __noinline__ void pass_oinit(const SysDesc& S, const Lanes& L, double scale) {
+__device__ __forceinline__ void pass_oinit(const SysDesc& S, const Lanes& L, double scale) {
   FOR_CHUNKS(S.A, L) {
-    int64_t row = c * kChunk + L.lane;
+    const int32_t row = CHUNK_ROW(L);
     if (row < S.A.n) {
-      float rh = (float)(ldcs(S.r + row) * scale);
-      stcs(S.rhs32 + row, rh);
-      stcs(S.r32 + row, rh);
-      stcs(S.u32 + row, __ldg(S.A.invd32 + row) * rh);
-      stcs(S.d32 + row, 0.0f);
+      float rh = (float)(ldcs(S.v64 + row) * scale);
+      stcs(S.v32 + V_RHS * S.vs + row, rh);
+      stcs(S.v32 + V_R * S.vs + row, rh);
+      stcs(S.v32 + V_U * S.vs + row, __ldg(S.v32 + V_INVD * S.vs + row) * rh);
+      stcs(S.v32 + V_X * S.vs + row, 0.0f);
     }
   }
 }
 
 // P_OUPD: x += ||r64|| * d32 (FP64 solution accumulation).
-__device__ __noinline__ void pass_oupd(const SysDesc& S, const Lanes& L, double rn) {
+__device__ __forceinline__ void pass_oupd(const SysDesc& S, const Lanes& L, double rn) {
   FOR_CHUNKS(S.A, L) {
-    int64_t row = c * kChunk + L.lane;
-    if (row < S.A.n) S.x[row] = fma(rn, (double)ldcs(S.d32 + row), S.x[row]);
+    const int32_t row = CHUNK_ROW(L);
+    if (row < S.A.n) S.x[row] = fma(rn, (double)ldcs(S.v32 + V_X * S.vs + row), S.x[row]);
   }
 }
 
@@ -600,8 +680,8 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
   const int nw = blockDim.x >> 5;
   Lanes L;
   L.lane = threadIdx.x & 31;
-  L.gw = (int64_t)g.rank() * nw + (threadIdx.x >> 5);
-  L.W = (int64_t)g.size() * nw;
+  L.gw = g.rank() * nw + (threadIdx.x >> 5);
+  L.W = g.size() * nw;
   const bool paper = S.norm == PPCG_NORM_PAPER_U_ABS;
   const int P = g.size();
 
@@ -619,7 +699,10 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
       switch (pass) {
         case P_SETUP1: pass_setup1(S, L, d, S.x_zero != 0); break;
         case P_SETUP2: pass_setup2<double>(S.A, v, L, d, paper); break;
-        case P_ITER: pass_iter<double>(S.A, v, L, d, C.alpha, C.beta, C.first != 0, C.iter, paper); break;
+        case P_ITER:
+          if (C.first) pass_iter<double, true>(S.A, v, L, d, C.alpha, C.beta, C.iter, paper);
+          else pass_iter<double, false>(S.A, v, L, d, C.alpha, C.beta, C.iter, paper);
+          break;
         case P_TRUE: pass_true(S, L, d); break;
         case P_RR1: pass_rr1<double>(S.A, v, L, C.iter == 0); partials = false; break;
         case P_RR2: pass_rr2<double>(S.A, v, L, d, C.iter, paper); break;
@@ -634,7 +717,8 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
       switch (pass) {
         case P_SETUP2: pass_setup2<float>(S.A, v, L, d, paper); break;
         case P_ITER:
-          pass_iter<float>(S.A, v, L, d, (float)C.alpha, (float)C.beta, C.first != 0, C.inner_iter, paper);
+          if (C.first) pass_iter<float, true>(S.A, v, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
+          else pass_iter<float, false>(S.A, v, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
           break;
         case P_RR1: pass_rr1<float>(S.A, v, L, C.inner_iter == 0); partials = false; break;
         case P_RR2: pass_rr2<float>(S.A, v, L, d, C.inner_iter, paper); break;
@@ -661,11 +745,25 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
   }
 }
 
-__global__ void __launch_bounds__(kGridThreads, 2) k_grid(const SysDesc* d, int budget) {
+template <int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_grid(const SysDesc* d, int budget) {
   __shared__ Shared sh;
   GridGroup g{d->bar, d->err, (long long)d->spin_limit_ns, 0u};
   run_system(g, d, budget, sh);
 }
+
+// Launch shapes of the grid path: (threads per CTA, minimum CTAs per SM for the register
+// budget).  Index 0 is the default (fastest measured on the 256^3 stencil); the others trade
+// registers against resident warps.
+struct GridShape {
+  void (*fn)(const SysDesc*, int);
+  int threads;
+};
+const GridShape kGridShapes[] = {
+    {k_grid<512, 2>, 512}, {k_grid<256, 4>, 256}, {k_grid<256, 3>, 256}, {k_grid<512, 1>, 512},
+    {k_grid<384, 2>, 384}, {k_grid<128, 6>, 128},
+};
+constexpr int kNumGridShapes = (int)(sizeof(kGridShapes) / sizeof(kGridShapes[0]));
 
 __global__ void __launch_bounds__(kClusterThreads, 4) k_cluster(const SysDesc* descs, const int32_t* list,
                                                              const int32_t* list_ptr, int budget) {
@@ -688,10 +786,13 @@ __global__ void k_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, in
 
 }  // namespace
 
-int grid_blocks_for_device(int device) {
+int grid_shape_count() { return kNumGridShapes; }
+
+int grid_blocks_for_device(int device, int shape) {
   int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_grid, kGridThreads, 0);
+  const GridShape& gs = kGridShapes[shape];
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gs.fn, gs.threads, 0);
   if (per < 1) per = 1;
   return sms * per;
 }
@@ -716,9 +817,10 @@ int max_active_clusters(int device) {
   return n > 0 ? n : 1;
 }
 
-cudaError_t launch_grid(const SysDesc* d_desc, int grid, int budget, cudaStream_t st) {
+cudaError_t launch_grid(const SysDesc* d_desc, int shape, int grid, int budget, cudaStream_t st) {
   void* args[] = {(void*)&d_desc, (void*)&budget};
-  return cudaLaunchCooperativeKernel((void*)k_grid, dim3(grid), dim3(kGridThreads), args, 0, st);
+  const GridShape& gs = kGridShapes[shape];
+  return cudaLaunchCooperativeKernel((void*)gs.fn, dim3(grid), dim3(gs.threads), args, 0, st);
 }
 
 cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,

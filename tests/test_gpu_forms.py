@@ -1,0 +1,194 @@
+"""GPU tests of the three forms beside the plain FP64 solve: FP32 + FP64 iterative
+refinement, the batched persistent launch, and the continuous-batching server.
+
+Bars: FP32+IR reaches a true (FP64) relative residual <= 1e-8 and states its error against
+the FP64 oracle; batched and served results are bitwise identical to solo ppcg_solve on the
+same handle settings (each system's partition over CTAs and reduction order depend only on
+the handle), and also meet the oracle bars of the plain solve.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def pp():
+    import paper_2105_06176_b300 as m
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def rgg(npts, seed):
+    return synth.rgg_laplacian(npts, (3 * 14.0 / (4 * np.pi * npts)) ** (1 / 3), 1e-3, seed)
+
+
+# ------------------------------------------------------------------ FP32 + refinement ---
+
+@pytest.mark.parametrize("name", ["varcoeff3d_40", "rgg_30k", "poisson2d_64"])
+@pytest.mark.parametrize("path", [1, 2], ids=["grid", "cluster"])
+def test_fp32_ir_reaches_fp64_accuracy(name, path):
+    m = pp()
+    if name == "varcoeff3d_40":
+        a = synth.varcoeff3d(40, seed=2); b = synth.rhs_uniform(a.n, 2)
+    elif name == "rgg_30k":
+        a = rgg(30000, 3); b = synth.rhs_uniform(a.n, 3)
+    else:
+        a = synth.poisson2d(64); b = a.to_scipy() @ synth.xtrue_uniform(a.n, 1)
+    ref = oracle.pipecg(a, b, tol=1e-10, maxit=50000)
+    s = m.Solver.from_csr(a, precision=m.FP32_IR, path=path)
+    x, info = s.solve(dev(b), tol=1e-8, maxit=50000)
+    x = x.cpu().numpy()
+    assert info.status == m.OK, info
+    t = np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)
+    assert t <= 1e-8 and info.rel_res_true <= 1e-8
+    assert info.outer_iters >= 2
+    err = rel(x, ref["x"])
+    # x error is bounded by cond(A) times the residual gap; both solves sit at <= 1e-8
+    assert err <= 1e-4, err
+
+
+# ------------------------------------------------------------------ batched ------------
+
+def _batch_systems():
+    specs = synth.batch_mix(10, 7, lo=1e3, hi=3e4)
+    return [synth.build_spec(s) for s in specs]
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32_ir"])
+def test_batch_bitwise_equals_solo(precision):
+    m = pp()
+    systems = _batch_systems()
+    solvers, bs = [], []
+    for k, (a, b) in enumerate(systems):
+        path = m.PATH_GRID if k == 3 else m.PATH_CLUSTER     # one whole-GPU system in the mix
+        solvers.append(m.Solver.from_csr(a, precision=precision, path=path))
+        bs.append(dev(b))
+    solo = []
+    for s, b in zip(solvers, bs):
+        x, info = s.solve(b, tol=1e-8, maxit=20000)
+        solo.append((x.cpu().numpy(), info.iters, info.status))
+    xs = [torch.empty_like(b) for b in bs]
+    infos = m.batch_solve(solvers, bs, xs, tol=1e-8, maxit=20000)
+    for k, ((a, b), (xs0, it0, st0), xb, inf) in enumerate(zip(systems, solo, xs, infos)):
+        assert inf.status == st0 == m.OK, (k, inf)
+        assert inf.iters == it0, k
+        assert np.array_equal(xb.cpu().numpy(), xs0), k
+        t = np.linalg.norm(b - a.to_scipy() @ xs0) / np.linalg.norm(b)
+        assert t <= 1e-8
+    if precision == 0:
+        for (a, b), (_, it0, _) in zip(systems[:4], solo[:4]):
+            assert abs(it0 - oracle.pipecg(a, b, tol=1e-8, maxit=20000)["result"]["iters"]) <= 2
+
+
+def test_batch_fixed_k_parity():
+    m = pp()
+    systems = _batch_systems()[:6]
+    solvers = [m.Solver.from_csr(a, path=m.PATH_CLUSTER) for a, _ in systems]
+    bs = [dev(b) for _, b in systems]
+    xs = [torch.empty_like(b) for b in bs]
+    infos = m.batch_solve(solvers, bs, xs, tol=0.0, maxit=30)
+    for (a, b), x, inf in zip(systems, xs, infos):
+        assert inf.iters == 30
+        assert rel(x.cpu().numpy(), oracle.pipecg(a, b, tol=0.0, maxit=30)["x"]) <= 1e-10
+
+
+# ------------------------------------------------------------------ server -------------
+
+def _wait(srv, tickets, n_of, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets) and time.time() - t0 < timeout:
+        for t in tickets:
+            if t in out:
+                continue
+            st, x, info = srv.poll(t, n_of[t])
+            if st != pp().PENDING:
+                out[t] = (st, x, info)
+        time.sleep(0.002)
+    assert len(out) == len(tickets), "server did not finish in time"
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32_ir"])
+def test_server_results_same_alone_and_in_mix(precision):
+    m = pp()
+    systems = _batch_systems()[:6] + [(rgg(40000, 9), synth.rhs_uniform(40000, 9))]
+    # alone: one request at a time
+    alone = []
+    srv = m.Server(precision=precision, epoch_iters=64)
+    for a, b in systems:
+        t = srv.submit(a, b, tol=1e-8, maxit=20000)
+        res = _wait(srv, [t], {t: a.n})[t]
+        alone.append(res)
+    srv.close()
+    # mix: staggered arrivals while earlier requests are resident
+    srv = m.Server(precision=precision, epoch_iters=64)
+    tickets, n_of = [], {}
+    for k, (a, b) in enumerate(systems):
+        t = srv.submit(a, b, tol=1e-8, maxit=20000)
+        tickets.append(t)
+        n_of[t] = a.n
+        if k % 2 == 1:
+            time.sleep(0.01)
+    mix = _wait(srv, tickets, n_of)
+    srv.close()
+    for (a, b), (st0, x0, i0), t in zip(systems, alone, tickets):
+        st1, x1, i1 = mix[t]
+        assert st0 == st1 == m.OK, (i0, i1)
+        assert i0.iters == i1.iters
+        assert np.array_equal(x0, x1)
+        r = np.linalg.norm(b - a.to_scipy() @ x1) / np.linalg.norm(b)
+        assert r <= 1e-8
+    # and the served result equals a solo ppcg_solve with the same settings
+    a, b = systems[0]
+    s = m.Solver.from_csr(a, precision=precision)
+    xs, info = s.solve(dev(b), tol=1e-8, maxit=20000)
+    assert np.array_equal(xs.cpu().numpy(), alone[0][1])
+
+
+def test_server_admission_by_budget_and_errors():
+    m = pp()
+    systems = _batch_systems()[:5]
+
+    def footprint(a):      # the library's FP64 admission estimate
+        slots = 1.05 * a.nnz + 32.0 * (a.n / 32.0 + 1.0)
+        return int(slots * 12 + a.n * 48 + a.n * 80) + (1 << 20)
+    # a budget that admits about one request at a time
+    srv = m.Server(hbm_budget=int(1.3 * max(footprint(a) for a, _ in systems)), epoch_iters=32)
+    tickets, n_of = [], {}
+    for a, b in systems:
+        t = srv.submit(a, b, tol=1e-8, maxit=20000)
+        tickets.append(t)
+        n_of[t] = a.n
+    st = srv.stats()
+    assert st["queued"] + st["running"] + st["completed"] == len(systems)
+    res = _wait(srv, tickets, n_of)
+    assert all(v[0] == m.OK for v in res.values())
+    assert srv.stats()["completed"] == len(systems) and srv.stats()["hbm_in_use"] == 0
+    # unknown ticket, too-large request
+    st, _, _ = srv.poll(987654321, 1)
+    assert st == m.ERR_UNKNOWN_TICKET
+    huge = synth.poisson2d(400)
+    with pytest.raises(m.PPCGError) as e:
+        srv.submit(huge, np.ones(huge.n))
+    assert e.value.status == m.ERR_OOM
+    srv.close()
