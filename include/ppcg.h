@@ -193,6 +193,30 @@ void ppcg_server_destroy(ppcg_server server);
 ppcg_status ppcg_selftest_barrier_timeout(int32_t grid, int32_t drop_rank, int64_t limit_ns,
                                           int32_t* timed_out);
 
+/*
+ * Allocation-free solve.  The paper has no counterpart: this entry point exists for callers
+ * that may not allocate device memory while solving -- code whose device memory is owned by
+ * a framework pool, real-time loops where cudaMalloc/cudaFree (which can synchronise the
+ * whole device) are not allowed, or plug-ins whose host forbids allocation after start-up.
+ * It runs Alg. 2 with the Jacobi preconditioner straight from the caller's device CSR on one
+ * thread-block cluster, keeping every working vector in a statically sized device array of
+ * the library (4.5 MiB on each GPU that loads the library, held until the process exits).
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   n <= 65536 rows; larger n returns PPCG_ERR_ARG (use ppcg_create/ppcg_solve instead).
+ *   row_ptr [n+1] int64, col [nnz] int32, val [nnz], b [n], x [n]: DEVICE pointers, caller-owned.
+ *   x0: device initial guess or NULL for zero; may alias x.  Stopping test: REL_R (||r|| <=
+ *   tol ||b||), maxit as in ppcg_solve; no residual replacement.
+ *   info: NULL, or a host struct filled after the call waits for the solve to finish.
+ * The first call on a device looks up the scratch array's device address (once per device,
+ * with that device current); make that first call before capturing the stream into a graph.
+ * All calls on a device share the scratch array: calls whose GPU work overlaps (other streams
+ * or host threads) race on it, so order them.  Each call rewrites the scratch it reads, so
+ * earlier calls' contents never affect a result.
+ */
+ppcg_status ppcg_solve_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                               const double* val, const double* b, const double* x0, double* x,
+                               double tol, int32_t maxit, cudaStream_t stream, ppcg_info* info);
+
 /* Thread-local text of the last error of this thread's calls ("" if none). */
 const char* ppcg_last_error(void);
 

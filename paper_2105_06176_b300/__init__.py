@@ -36,7 +36,7 @@ _NAMES = {OK: "OK", PENDING: "PENDING", ERR_ARG: "ERR_ARG", ERR_NOT_SPD: "ERR_NO
 EXPORTED_SYMBOLS = (
     "ppcg_opts_default", "ppcg_create", "ppcg_solve", "ppcg_batch_solve", "ppcg_destroy",
     "ppcg_server_create", "ppcg_submit", "ppcg_poll", "ppcg_server_stats", "ppcg_server_destroy",
-    "ppcg_last_error", "ppcg_selftest_barrier_timeout",
+    "ppcg_last_error", "ppcg_selftest_barrier_timeout", "ppcg_solve_noalloc",
 )
 
 
@@ -108,6 +108,9 @@ def lib(build_if_missing=True):
     L.ppcg_selftest_barrier_timeout.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                                 ctypes.POINTER(ctypes.c_int32)]
     L.ppcg_selftest_barrier_timeout.restype = ctypes.c_int
+    L.ppcg_solve_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, P, ctypes.c_double,
+                                     ctypes.c_int32, P, ctypes.POINTER(Info)]
+    L.ppcg_solve_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
