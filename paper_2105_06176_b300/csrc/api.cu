@@ -40,10 +40,30 @@ __global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const doub
   if (i < n) dst[i] = src[perm[i]];
 }
 
-__global__ void k_scatter(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
-                          double* __restrict__ dst) {
+// Slot `slot` of a chunk-interleaved block with ns slots: element i at
+// (i / 32) * ns * 32 + slot * 32 + i % 32.
+__host__ __device__ __forceinline__ int64_t slot_index(int64_t i, int ns, int slot) {
+  return (i >> 5) * (int64_t)ns * kChunk + (int64_t)slot * kChunk + (i & 31);
+}
+
+// plain vector (optionally read through the row permutation) -> block slot
+template <typename T>
+__global__ void k_to_slot(int64_t n, const int32_t* __restrict__ perm, const T* __restrict__ src,
+                          T* __restrict__ blk, int ns, int slot) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) dst[perm[i]] = src[i];
+  if (i < n) blk[slot_index(i, ns, slot)] = src[perm ? perm[i] : i];
+}
+
+__global__ void k_fill_slot(int64_t n, double* __restrict__ blk, int ns, int slot, double v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) blk[slot_index(i, ns, slot)] = v;
+}
+
+// block slot -> plain vector (optionally written through the row permutation)
+__global__ void k_from_slot(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ blk, int ns,
+                            int slot, double* __restrict__ dst) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[perm ? perm[i] : i] = blk[slot_index(i, ns, slot)];
 }
 
 __global__ void k_init_ctl(Ctl* c, int32_t state) {
@@ -85,17 +105,16 @@ static void free_all(ppcg_ctx* h) {
 
 // Enqueue: b/x0 -> solver-order device vectors; fills h->desc pointers for this solve.
 // Returns the device x the solver writes (user x itself when possible).
-ppcg_status stage_inputs(ppcg_ctx* h, const double* b, const double* x0, double* x, bool require_device,
-                         cudaStream_t st, double** x_solver) {
+ppcg_status stage_inputs(ppcg_ctx* h, const double* b, const double* x0, bool require_device, cudaStream_t st) {
   const int64_t n = h->n;
   const size_t bytes = n * sizeof(double);
-  const bool bd = is_device_ptr(b), xd = is_device_ptr(x);
+  const bool bd = is_device_ptr(b);
   const bool x0d = x0 ? is_device_ptr(x0) : true;
-  if (require_device && (!bd || !xd || !x0d)) {
+  if (require_device && (!bd || !x0d)) {
     set_error("ppcg_batch_solve: b, x0 and x must be device pointers");
     return PPCG_ERR_ARG;
   }
-  // b
+  // b: used in place when it is a device vector in solver order, else staged into b_ws
   const double* bsol;
   if (h->perm) {
     const double* src = b;
@@ -108,36 +127,26 @@ ppcg_status stage_inputs(ppcg_ctx* h, const double* b, const double* x0, double*
     cudaMemcpyAsync(h->b_ws, b, bytes, cudaMemcpyHostToDevice, st);
     bsol = h->b_ws;
   }
-  // x0 -> the solver's x (a slot of the handle's vector block, in solver row order)
-  double* xs = h->desc.x;
+  // x0 -> the x slot of the vector block, in solver row order
   int32_t x_zero = 0;
   if (!x0) {
-    cudaMemsetAsync(xs, 0, bytes, st);
+    k_fill_slot<<<blocks_for(n, 256), 256, 0, st>>>(n, h->desc.v64, h->ns64, h->xslot, 0.0);
     x_zero = 1;
-  } else if (h->perm) {
+  } else {
     const double* src = x0;
     if (!x0d) { cudaMemcpyAsync(h->tmp, x0, bytes, cudaMemcpyHostToDevice, st); src = h->tmp; }
-    k_gather<<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, src, xs);
-  } else {
-    cudaMemcpyAsync(xs, x0, bytes, x0d ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    k_to_slot<double><<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, src, h->desc.v64, h->ns64, h->xslot);
   }
   h->desc.b = bsol;
   h->desc.x_zero = x_zero;
-  *x_solver = xs;
   return PPCG_OK;
 }
 
-void stage_outputs(ppcg_ctx* h, double* x, double* xs, cudaStream_t st) {
+void stage_outputs(ppcg_ctx* h, double* x, cudaStream_t st) {
   const int64_t n = h->n;
-  const size_t bytes = n * sizeof(double);
   const bool xd = is_device_ptr(x);
-  if (h->perm) {
-    double* dst = xd ? x : h->tmp;
-    k_scatter<<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, xs, dst);
-    if (!xd) cudaMemcpyAsync(x, h->tmp, bytes, cudaMemcpyDeviceToHost, st);
-  } else if (xs != x) {
-    cudaMemcpyAsync(x, xs, bytes, xd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
-  }
+  k_from_slot<<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, h->desc.v64, h->ns64, h->xslot, xd ? x : h->tmp);
+  if (!xd) cudaMemcpyAsync(x, h->tmp, n * sizeof(double), cudaMemcpyDeviceToHost, st);
 }
 
 void prepare_control(ppcg_ctx* h, double tol, int32_t maxit, cudaStream_t st) {
@@ -288,24 +297,23 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
 
   // Workspace.
   SysDesc& d = h->desc;
-  d.vs = (n + 63) / 64 * 64;            // keeps every vector 512-byte aligned
-  // FP64 block: r u wa wb z q s p x invd.  FP32_IR: FP64 block r64 x; FP32 block
-  // r u wa wb z q s p d invd rhs diag.
+  // Chunk-interleaved vector blocks.  FP64: r u wa wb z q s p x invd.  FP32_IR: FP64 block
+  // r64 x and FP32 block r u wa wb z q s p d invd rhs.
+  h->ns64 = fp32 ? kSlotsIR : kSlots64;
+  h->xslot = fp32 ? kSlotXIR : kSlotX64;
+  const size_t rows_padded = (size_t)h->A.nchunks * kChunk;
   bool ok = walloc(h, &h->b_ws, n) && walloc(h, &h->tmp, n) &&
             walloc(h, &h->part, 2 * (size_t)h->nparts * 4) && walloc(h, &h->ctl, 1) &&
             walloc(h, &h->bar, 1) && walloc(h, &h->err, 1) && walloc(h, &h->d_desc, 1) &&
-            walloc(h, &d.v64, (size_t)d.vs * (fp32 ? 2 : 10));
-  if (ok && fp32) ok = walloc(h, &d.v32, (size_t)d.vs * 12);
+            walloc(h, &d.v64, rows_padded * h->ns64);
+  if (ok && fp32) ok = walloc(h, &d.v32, rows_padded * kSlots32);
   if (ok) {
-    d.x = d.v64 + (fp32 ? 1 : 8) * d.vs;
-    h->x_ws = d.x;
     if (fp32) {
-      cudaMemcpyAsync(d.v32 + 9 * d.vs, h->A.invd32, n * sizeof(float), cudaMemcpyDeviceToDevice, stream);
-      cudaMemcpyAsync(d.v32 + 11 * d.vs, h->A.diag32, n * sizeof(float), cudaMemcpyDeviceToDevice, stream);
+      k_to_slot<float><<<blocks_for(n, 256), 256, 0, stream>>>(n, nullptr, h->A.invd32, d.v32, kSlots32, kSlotInvd);
     } else {
-      cudaMemcpyAsync(d.v64 + 9 * d.vs, h->A.invd, n * sizeof(double), cudaMemcpyDeviceToDevice, stream);
+      k_to_slot<double><<<blocks_for(n, 256), 256, 0, stream>>>(n, nullptr, h->A.invd, d.v64, kSlots64, kSlotInvd);
     }
-    ok = cudaStreamSynchronize(stream) == cudaSuccess;
+    ok = cudaStreamSynchronize(stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
   }
   if (ok && cudaMallocHost((void**)&h->stage, sizeof(Stage)) != cudaSuccess) { cudaGetLastError(); ok = false; }
   if (!ok) {
@@ -343,8 +351,7 @@ ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double*
     return PPCG_ERR_ARG;
   }
   if (h->n == 0) { write_trivial_info(info, PPCG_OK); return PPCG_OK; }
-  double* xs = nullptr;
-  ppcg_status s = stage_inputs(h, b, x0, x, false, st, &xs);
+  ppcg_status s = stage_inputs(h, b, x0, false, st);
   if (s != PPCG_OK) return s;
   prepare_control(h, tol, maxit, st);
   cudaMemcpyAsync(h->d_desc, &h->desc, sizeof(SysDesc), cudaMemcpyHostToDevice, st);
@@ -375,7 +382,7 @@ ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double*
     set_error("ppcg_solve: launch failed: %s", cudaGetErrorString(e));
     return PPCG_ERR_CUDA;
   }
-  stage_outputs(h, x, xs, st);
+  stage_outputs(h, x, st);
   std::vector<std::pair<ppcg_ctx*, ppcg_info*>> items{{h, info}};
   enqueue_info(items, st);
   return check_launch("ppcg_solve") ? PPCG_OK : PPCG_ERR_CUDA;
@@ -398,11 +405,11 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
       if (hs[j] == hs[i]) { set_error("ppcg_batch_solve: handle %d repeated", i); return PPCG_ERR_ARG; }
   }
   std::vector<int> cl, gr;
-  std::vector<double*> xsol(count, nullptr);
   for (int i = 0; i < count; i++) {
     ppcg_ctx* h = hs[i];
     if (h->n == 0) { if (infos) write_trivial_info(&infos[i], PPCG_OK); continue; }
-    ppcg_status s = stage_inputs(h, b[i], x0 ? x0[i] : nullptr, x[i], true, st, &xsol[i]);
+    if (!is_device_ptr(x[i])) { set_error("ppcg_batch_solve: x[%d] must be a device pointer", i); return PPCG_ERR_ARG; }
+    ppcg_status s = stage_inputs(h, b[i], x0 ? x0[i] : nullptr, true, st);
     if (s != PPCG_OK) return s;
     prepare_control(h, tol[i], maxit[i], st);
     (h->path == PPCG_PATH_CLUSTER ? cl : gr).push_back(i);
@@ -467,7 +474,7 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
   std::vector<std::pair<ppcg_ctx*, ppcg_info*>> items;
   for (int i = 0; i < count; i++) {
     if (hs[i]->n == 0) continue;
-    stage_outputs(hs[i], x[i], xsol[i], st);
+    stage_outputs(hs[i], x[i], st);
     items.push_back({hs[i], infos ? &infos[i] : nullptr});
   }
   if (!items.empty()) enqueue_info(items, st);

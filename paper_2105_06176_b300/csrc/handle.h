@@ -59,7 +59,8 @@ struct ppcg_ctx {
   int nparts = 0;      // partial slots per pass (CTAs in the group)
   double bytes_per_iter = 0.0;
   // workspace
-  double *b_ws = nullptr, *x_ws = nullptr, *tmp = nullptr;
+  double *b_ws = nullptr, *tmp = nullptr;
+  int ns64 = 0, xslot = 0;   // slots of the FP64 vector block and the slot holding x
   double* part = nullptr;
   ppcg::Ctl* ctl = nullptr;
   unsigned* bar = nullptr;
@@ -72,12 +73,11 @@ struct ppcg_ctx {
 
 namespace ppcg {
 
-// Enqueue b/x0 into solver-order device vectors (fills h->desc.b/x/x_zero); *x_solver is
-// the device x the kernel writes.
-ppcg_status stage_inputs(ppcg_ctx* h, const double* b, const double* x0, double* x, bool require_device,
-                         cudaStream_t st, double** x_solver);
-// Enqueue the copy (and un-permutation) of the solver's x into the caller's x.
-void stage_outputs(ppcg_ctx* h, double* x, double* xs, cudaStream_t st);
+// Enqueue b/x0 into solver-order device storage (fills h->desc.b and x_zero; x0 goes into
+// the x slot of the vector block).  require_device: b and x0 must be device pointers.
+ppcg_status stage_inputs(ppcg_ctx* h, const double* b, const double* x0, bool require_device, cudaStream_t st);
+// Enqueue the copy (and un-permutation) of the solver's x into the caller's x (host or device).
+void stage_outputs(ppcg_ctx* h, double* x, cudaStream_t st);
 // Enqueue a fresh control block and the barrier/err reset for a new solve.
 void prepare_control(ppcg_ctx* h, double tol, int32_t maxit, cudaStream_t st);
 // Device bytes a handle of this size will allocate (estimate used for admission).

@@ -9,6 +9,8 @@
 namespace ppcg {
 
 constexpr int kChunk = 32;           // SELL-C-sigma chunk height C: one warp lane per row
+constexpr int kSlots64 = 10, kSlots32 = 11, kSlotsIR = 2;   // slots of the vector blocks
+constexpr int kSlotX64 = 8, kSlotXIR = 1, kSlotInvd = 9;  // x and D^-1 slots
 constexpr int kClusterThreads = 256; // CTA size of the cluster path
 constexpr int kClusterSize = 8;      // CTAs per thread-block cluster (portable maximum)
 
@@ -69,14 +71,13 @@ struct SysDesc {
   int32_t inner_maxit, max_outer, nparts, x_zero;  // x_zero: x starts at 0 (skip the A x0 gather)
   double tol, inner_tol;
   int64_t spin_limit_ns;
-  const double* b;       // solver order
-  double* x;             // solver order (FP64 solution, holds x0 at start)
-  // Per-row vectors, each vs elements apart in one allocation:
+  const double* b;       // right-hand side, solver order (plain array)
+  // Per-row vectors in chunk-interleaved blocks (for each 32-row chunk, the block's slots
+  // of 32 values side by side):
   //   v64: r u wa wb z q s p x invd (FP64 path); in FP32_IR: r64 x (outer residual, solution)
-  //   v32: r u wa wb z q s p d invd rhs diag (FP32_IR inner solve; d is the inner solution)
+  //   v32: r u wa wb z q s p d invd rhs (FP32_IR inner solve; d is the inner solution)
   double* v64;
   float* v32;
-  int64_t vs;
   double* part;          // [2][nparts][4] block partials, double-buffered by pass parity
   Ctl* ctl;
   unsigned* bar;         // grid barrier arrival counter (grid path; zeroed before each launch)

@@ -50,7 +50,6 @@ struct Request {
 struct Slot {
   uint64_t ticket = 0;
   ppcg_handle h = nullptr;
-  double* xs = nullptr;       // device x the kernel writes
   size_t footprint = 0;
 };
 
@@ -117,8 +116,7 @@ void admit_loop(ppcg_srv* S) {
     slot.footprint = req->footprint;
     if (st == PPCG_OK && req->n > 0) {
       slot.h = h;
-      st = stage_inputs(h, req->b.data(), req->has_x0 ? req->x0.data() : nullptr, h->x_ws, false, S->s_admit,
-                        &slot.xs);
+      st = stage_inputs(h, req->b.data(), req->has_x0 ? req->x0.data() : nullptr, false, S->s_admit);
       if (st == PPCG_OK) {
         prepare_control(h, req->tol, req->maxit, S->s_admit);
         cudaMemcpyAsync(h->d_desc, &h->desc, sizeof(SysDesc), cudaMemcpyHostToDevice, S->s_admit);
@@ -227,7 +225,7 @@ void exec_loop(ppcg_srv* S) {
       if (sg.ctl.state != S_DONE && sg.err == 0) { keep.push_back(s); continue; }
       Result r;
       r.x.resize(s.h->n);
-      stage_outputs(s.h, r.x.data(), s.xs, S->s_exec);
+      stage_outputs(s.h, r.x.data(), S->s_exec);
       cudaStreamSynchronize(S->s_exec);
       InfoJob j{s.h->stage, &r.info, s.h->bytes_per_iter, s.h->opts.norm, s.h->opts.precision};
       fill_info(sg, j, &r.info);

@@ -147,13 +147,31 @@ __device__ __forceinline__ float ld_stream(const float* p) {
   return v;
 }
 
-// acc + sum_j val[slot_j] * x[col[slot_j]] (* dsc[col] when SCALE) over the row's
+// Chunk-interleaved vector block: for every 32-row chunk c, NS slots of 32 values each, so
+// slot k of row i lives at base + (i / 32) * NS * 32 + k * 32 + i % 32.  A warp reaches all
+// its rows' vectors from one chunk pointer with compile-time slot offsets, and every slot
+// access of a warp is 32 consecutive values.
+template <typename T, int NS> struct Blk {
+  T* b;
+  static constexpr int64_t kTile = (int64_t)NS * kChunk;
+  __device__ __forceinline__ T* chunk(int32_t c, int lane) const { return b + (int64_t)c * kTile + lane; }
+};
+
+// Gather of one slot of a block, through L2 (the slot was written by other CTAs in the
+// previous pass).
+template <typename T, int NS> struct GatherSlot {
+  const T* base;   // block base + slot * 32
+  __device__ __forceinline__ T operator()(int32_t j) const {
+    return ldcg(base + (int64_t)(j >> 5) * ((int64_t)NS * kChunk) + (j & 31));
+  }
+};
+
+// acc + sum_j val[slot_j] * x(col[slot_j]) (* dsc[col] when SCALE) over the row's
 // off-diagonal slots base + j*32, j < len, in CSR order; acc enters holding the diagonal
-// term.  Gathers use ld.global.cg: the gathered vector was written by other CTAs in the
-// previous pass.
-template <typename T, bool SCALE>
-__device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* __restrict__ val,
-                                     const T* x, const T* __restrict__ dsc, int64_t base, int len, T acc) {
+// term.
+template <typename T, bool SCALE, class G>
+__device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* __restrict__ val, const G& x,
+                                     const T* __restrict__ dsc, int64_t base, int len, T acc) {
   int j = 0;
   for (; j + 8 <= len; j += 8) {
     int32_t c[8];
@@ -165,7 +183,7 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* _
     }
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-      T xv = ldcg(x + c[k]);
+      T xv = x(c[k]);
       if (SCALE) xv = __ldg(dsc + c[k]) * xv;
       acc = fma(a[k], xv, acc);
     }
@@ -182,7 +200,7 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* _
 #pragma unroll
   for (int k = 0; k < 7; k++) {
     if (j + k < len) {
-      T xv = ldcg(x + c[k]);
+      T xv = x(c[k]);
       if (SCALE) xv = __ldg(dsc + c[k]) * xv;
       acc = fma(a[k], xv, acc);
     }
@@ -190,80 +208,65 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* _
   return acc;
 }
 
-// Per-precision view of the Krylov vectors and matrix arrays.  The recurrence vectors, the
-// solution and D^-1 live vs elements apart from one base pointer, so a pass addresses
-// every per-row array from (base + row) and a constant slot stride instead of holding a
-// pointer per vector in registers.
-//   FP64 block: r u wa wb z q s p x invd
-//   FP32 block: r u wa wb z q s p d invd rhs diag   (d: the inner solution)
-enum { V_R = 0, V_U, V_WA, V_WB, V_Z, V_Q, V_S, V_P, V_X, V_INVD, V_RHS, V_DIAG };
-template <typename T> struct Vec {
-  const T* val; const T* diag; const T* rhs;
-  T* vb; int64_t vs;
-  __device__ __forceinline__ T* at(int k) const { return vb + (int64_t)k * vs; }
-};
-
-__device__ __forceinline__ Vec<double> vec64(const SysDesc& S) {
-  return {S.A.val, S.A.diag, S.b, S.v64, S.vs};
-}
-__device__ __forceinline__ Vec<float> vec32(const SysDesc& S) {
-  return {S.A.val32, S.v32 + V_DIAG * S.vs, S.v32 + V_RHS * S.vs, S.v32, S.vs};
-}
+// Vector slots.  FP64 block (NS 10): r u wa wb z q s p x invd.  FP32 block (NS 11):
+// r u wa wb z q s p d invd rhs (d: inner solution).  FP32_IR keeps its FP64 outer residual
+// and solution in a 2-slot FP64 block: r64 x.
+enum { V_R = 0, V_U, V_WA, V_WB, V_Z, V_Q, V_S, V_P, V_X, V_INVD, V_RHS };
+constexpr int kNS64 = 10, kNS32 = 11, kNSIR = 2;
+constexpr int IR_R = 0, IR_X = 1;
 
 struct Lanes {
   int32_t gw, W;   // global warp id within the group, warps in the group (chunk indices < 2^26)
   int32_t lane;
 };
 
-// Walks the group's chunks (warp gw, gw + W, ...) with the next chunk's slot range loaded
-// one step ahead.
-struct ChunkIter {
-  const int64_t* cptr;
-  int32_t c, W, nchunks, len, nlen;
-  int64_t b0, nb0;
-  __device__ __forceinline__ ChunkIter(const DevMatrix& A, const Lanes& L)
-      : cptr(A.cptr), c(L.gw), W(L.W), nchunks((int32_t)A.nchunks), len(0), nlen(0), b0(0), nb0(0) {
-    if (c < nchunks) {
-      b0 = __ldg(cptr + c);
-      len = (int32_t)((__ldg(cptr + c + 1) - b0) / kChunk);
-    }
-    prefetch();
-  }
-  __device__ __forceinline__ void prefetch() {
-    if (c + W < nchunks) {
-      nb0 = __ldg(cptr + c + W);
-      nlen = (int32_t)((__ldg(cptr + c + W + 1) - nb0) / kChunk);
-    }
-  }
-  __device__ __forceinline__ bool ok() const { return c < nchunks; }
-  __device__ __forceinline__ void next() { c += W; b0 = nb0; len = nlen; prefetch(); }
+#define FOR_CHUNKS(A, L) for (int32_t c = (L).gw; c < (int32_t)(A).nchunks; c += (L).W)
+
+__device__ __forceinline__ void chunk_slots(const DevMatrix& A, int32_t c, int lane, int64_t& base, int& len) {
+  const int64_t b0 = __ldg(A.cptr + c);
+  len = (int)((__ldg(A.cptr + c + 1) - b0) / kChunk);
+  base = b0 + lane;
+}
+
+// Per-precision matrix/vector view used by the generic passes.
+template <typename T, int NS> struct View {
+  const T* val;     // SELL values (A D^-1, off-diagonal)
+  const T* dsc;     // a_ii per row, plain array (gathered as the column scale of A v)
+  const T* rhs;     // right-hand side, plain array (FP64 path) -- nullptr when it is a slot
+  Blk<T, NS> v;
 };
 
-#define FOR_CHUNKS(A, L) for (ChunkIter it(A, L); it.ok(); it.next())
-#define CHUNK_ROW(L) (it.c * kChunk + (L).lane)
-#define CHUNK_BASE(L) (it.b0 + (L).lane)
+__device__ __forceinline__ View<double, kNS64> view64(const SysDesc& S) {
+  return {S.A.val, S.A.diag, S.b, {S.v64}};
+}
+__device__ __forceinline__ View<float, kNS32> view32(const SysDesc& S) {
+  return {S.A.val32, S.A.diag32, nullptr, {S.v32}};
+}
 
 // -------------------------------------------------------------------------- passes --
 
 // P_SETUP1 (FP64), Alg. 2 line 1: r0 = b - A x0 ; u0 = M^-1 r0.  Partials (b,b), (r,r).
 __device__ __forceinline__ void pass_setup1(const SysDesc& S, const Lanes& L, Dots<double>& d, bool x_zero) {
   const DevMatrix& A = S.A;
+  const Blk<double, kNS64> v{S.v64};
+  const GatherSlot<double, kNS64> gx{S.v64 + V_X * kChunk};
   FOR_CHUNKS(A, L) {
-    const int64_t base = CHUNK_BASE(L);
-    const int len = it.len;
-    const int32_t row = CHUNK_ROW(L);
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
+    double* pc = v.chunk(c, L.lane);
     double ax = 0.0, bi = 0.0, id = 0.0;
     if (in) {
       bi = __ldg(S.b + row);
-      id = __ldg(S.v64 + V_INVD * S.vs + row);
-      if (!x_zero) ax = __ldg(A.diag + row) * ldcg(S.x + row);
+      id = ldcs(pc + V_INVD * kChunk);
+      if (!x_zero) ax = __ldg(A.diag + row) * ldcg(pc + V_X * kChunk);
     }
-    if (!x_zero) ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len, ax);
+    if (!x_zero) ax = row_dot<double, true>(A.col, A.val, gx, A.diag, base, len, ax);
     if (in) {
-      double ri = bi - ax;
-      stcs(S.v64 + V_R * S.vs + row, ri);
-      stcs(S.v64 + V_U * S.vs + row, id * ri);
+      const double ri = bi - ax;
+      stcs(pc + V_R * kChunk, ri);
+      stcs(pc + V_U * kChunk, id * ri);
       d.add(0, bi, bi);
       d.add(1, ri, ri);
     }
@@ -271,19 +274,21 @@ __device__ __forceinline__ void pass_setup1(const SysDesc& S, const Lanes& L, Do
 }
 
 // P_SETUP2, Alg. 2 lines 1-2: w0 = A u0 (= Ahat r0) ; partials (r,u), (w,u), norm.
-template <typename T>
-__device__ __forceinline__ void pass_setup2(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d,
-                                         bool paper_norm) {
+template <typename T, int NS>
+__device__ __forceinline__ void pass_setup2(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, Dots<T>& d,
+                                            bool paper_norm) {
+  const GatherSlot<T, NS> gr{V.v.b + V_R * kChunk};
   FOR_CHUNKS(A, L) {
-    const int64_t base = CHUNK_BASE(L);
-    const int len = it.len;
-    const int32_t row = CHUNK_ROW(L);
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
+    T* pc = V.v.chunk(c, L.lane);
     T ri = T(0), ui = T(0);
-    if (in) { ri = ldcg(v.at(V_R) + row); ui = ldcs(v.at(V_U) + row); }
-    T wi = row_dot<T, false>(A.col, v.val, v.at(V_R), nullptr, base, len, ri);
+    if (in) { ri = ldcg(pc + V_R * kChunk); ui = ldcs(pc + V_U * kChunk); }
+    const T wi = row_dot<T, false>(A.col, V.val, gr, nullptr, base, len, ri);
     if (in) {
-      stcs(v.at(V_WA) + row, wi);
+      stcs(pc + V_WA * kChunk, wi);
       d.add(0, ri, ui);
       d.add(1, wi, ui);
       if (paper_norm) d.add(2, ui, ui); else d.add(2, ri, ri);
@@ -292,44 +297,39 @@ __device__ __forceinline__ void pass_setup2(const DevMatrix& A, const Vec<T>& v,
 }
 
 // P_ITER: one full iteration of Alg. 2 for the group's rows (see the file comment).  The
-// row's own vector entries are loaded before the gather so their latency overlaps it;
-// every per-row array is addressed from one pointer (pr) plus a slot stride.
-template <typename T, bool FIRST>
-__device__ __forceinline__ void pass_iter(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d,
+// row's own vector entries are loaded before the gather so their latency overlaps it.
+template <typename T, int NS, bool FIRST>
+__device__ __forceinline__ void pass_iter(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, Dots<T>& d,
                                           T alpha, T beta, int k, bool paper_norm) {
-  const int64_t* __restrict__ cptr = A.cptr;
-  const int32_t* __restrict__ col = A.col;
-  const T* __restrict__ val = v.val;
-  T* const vb = v.vb;
-  const int64_t vs = v.vs;
-  const int32_t n = (int32_t)A.n;
   const int wcs = (k & 1) ? V_WB : V_WA;
   const int wns = (k & 1) ? V_WA : V_WB;
-  const T* wc = vb + wcs * vs;
-  const int32_t nchunks = (int32_t)A.nchunks;
-  for (int32_t c = L.gw; c < nchunks; c += L.W) {
-    const int64_t b0 = __ldg(cptr + c);
-    const int len = (int)((__ldg(cptr + c + 1) - b0) / kChunk);
+  const GatherSlot<T, NS> gw{V.v.b + wcs * kChunk};
+  const int32_t* __restrict__ col = A.col;
+  const T* __restrict__ val = V.val;
+  const int32_t n = (int32_t)A.n;
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < n;
-    T* pr = vb + row;
+    T* pc = V.v.chunk(c, L.lane);
     T wi = T(0), id = T(0), ui = T(0), xi = T(0), ri = T(0);
     T zo = T(0), qo = T(0), so = T(0), po = T(0);
     if (in) {
-      wi = ldcg(pr + wcs * vs);
-      id = ldcs(pr + V_INVD * vs);
-      ui = ldcs(pr + V_U * vs);
-      xi = ldcs(pr + V_X * vs);
-      ri = ldcs(pr + V_R * vs);
+      wi = ldcg(pc + wcs * kChunk);
+      id = ldcs(pc + V_INVD * kChunk);
+      ui = ldcs(pc + V_U * kChunk);
+      xi = ldcs(pc + V_X * kChunk);
+      ri = ldcs(pc + V_R * kChunk);
       if (!FIRST) {
-        zo = ldcs(pr + V_Z * vs);
-        qo = ldcs(pr + V_Q * vs);
-        so = ldcs(pr + V_S * vs);
-        po = ldcs(pr + V_P * vs);
+        zo = ldcs(pc + V_Z * kChunk);
+        qo = ldcs(pc + V_Q * kChunk);
+        so = ldcs(pc + V_S * kChunk);
+        po = ldcs(pc + V_P * kChunk);
       }
     }
     // n_i = (A M^-1 w)_i = w_i + sum_{j != i} ahat_ij w_j
-    const T ni = row_dot<T, false>(col, val, wc, nullptr, b0 + L.lane, len, wi);
+    const T ni = row_dot<T, false>(col, val, gw, nullptr, base, len, wi);
     if (in) {
       const T mi = id * wi;
       const T zi = FIRST ? ni : fma(beta, zo, ni);
@@ -340,14 +340,14 @@ __device__ __forceinline__ void pass_iter(const DevMatrix& A, const Vec<T>& v, c
       ri = fma(-alpha, si, ri);
       const T un = fma(-alpha, qi, ui);
       const T wnn = fma(-alpha, zi, wi);
-      stcs(pr + V_Z * vs, zi);
-      stcs(pr + V_Q * vs, qi);
-      stcs(pr + V_S * vs, si);
-      stcs(pr + V_P * vs, pi);
-      stcs(pr + V_X * vs, xi);
-      stcs(pr + V_R * vs, ri);
-      stcs(pr + V_U * vs, un);
-      stcs(pr + wns * vs, wnn);
+      stcs(pc + V_Z * kChunk, zi);
+      stcs(pc + V_Q * kChunk, qi);
+      stcs(pc + V_S * kChunk, si);
+      stcs(pc + V_P * kChunk, pi);
+      stcs(pc + V_X * kChunk, xi);
+      stcs(pc + V_R * kChunk, ri);
+      stcs(pc + V_U * kChunk, un);
+      stcs(pc + wns * kChunk, wnn);
       d.add(0, ri, un);
       d.add(1, wnn, un);
       if (paper_norm) d.add(2, un, un); else d.add(2, ri, ri);
@@ -355,70 +355,79 @@ __device__ __forceinline__ void pass_iter(const DevMatrix& A, const Vec<T>& v, c
   }
 }
 
-// P_TRUE (FP64): partial ||b - A x||^2.
+// P_TRUE (FP64): partial ||b - A x||^2, x in slot XS of an NS-slot FP64 block.
+template <int NS, int XS>
 __device__ __forceinline__ void pass_true(const SysDesc& S, const Lanes& L, Dots<double>& d) {
   const DevMatrix& A = S.A;
+  const Blk<double, NS> v{S.v64};
+  const GatherSlot<double, NS> gx{S.v64 + XS * kChunk};
   FOR_CHUNKS(A, L) {
-    const int64_t base = CHUNK_BASE(L);
-    const int len = it.len;
-    const int32_t row = CHUNK_ROW(L);
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     double ax = 0.0, bi = 0.0;
-    if (in) { bi = __ldg(S.b + row); ax = __ldg(A.diag + row) * ldcg(S.x + row); }
-    ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len, ax);
+    if (in) { bi = __ldg(S.b + row); ax = __ldg(A.diag + row) * ldcg(v.chunk(c, L.lane) + XS * kChunk); }
+    ax = row_dot<double, true>(A.col, A.val, gx, A.diag, base, len, ax);
     if (in) {
-      double t = bi - ax;
+      const double t = bi - ax;
       d.add(0, t, t);
     }
   }
 }
 
-// P_RR1: residual replacement, first half: r = rhs - A xs ; u = M^-1 r ; s = A p ; q = M^-1 s.
+// P_RR1: residual replacement, first half: r = rhs - A x ; u = M^-1 r ; s = A p ; q = M^-1 s.
 // (At iteration 0 p is zero, so s = q = 0.)
-template <typename T>
-__device__ __forceinline__ void pass_rr1(const DevMatrix& A, const Vec<T>& v, const Lanes& L, bool p_zero) {
+template <typename T, int NS>
+__device__ __forceinline__ void pass_rr1(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, bool p_zero) {
+  const GatherSlot<T, NS> gx{V.v.b + V_X * kChunk};
+  const GatherSlot<T, NS> gp{V.v.b + V_P * kChunk};
   FOR_CHUNKS(A, L) {
-    const int64_t base = CHUNK_BASE(L);
-    const int len = it.len;
-    const int32_t row = CHUNK_ROW(L);
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
+    T* pc = V.v.chunk(c, L.lane);
     T ax = T(0), ap = T(0), id = T(0), rh = T(0);
     if (in) {
-      const T di = __ldg(v.diag + row);
-      id = __ldg(v.at(V_INVD) + row);
-      rh = __ldg(v.rhs + row);
-      ax = di * ldcg(v.at(V_X) + row);
-      if (!p_zero) ap = di * ldcg(v.at(V_P) + row);
+      const T di = __ldg(V.dsc + row);
+      id = ldcs(pc + V_INVD * kChunk);
+      rh = V.rhs ? __ldg(V.rhs + row) : ldcs(pc + V_RHS * kChunk);
+      ax = di * ldcg(pc + V_X * kChunk);
+      if (!p_zero) ap = di * ldcg(pc + V_P * kChunk);
     }
-    ax = row_dot<T, true>(A.col, v.val, v.at(V_X), v.diag, base, len, ax);
-    if (!p_zero) ap = row_dot<T, true>(A.col, v.val, v.at(V_P), v.diag, base, len, ap);
+    ax = row_dot<T, true>(A.col, V.val, gx, V.dsc, base, len, ax);
+    if (!p_zero) ap = row_dot<T, true>(A.col, V.val, gp, V.dsc, base, len, ap);
     if (in) {
       const T ri = rh - ax;
-      stcs(v.at(V_R) + row, ri);
-      stcs(v.at(V_U) + row, id * ri);
-      stcs(v.at(V_S) + row, ap);
-      stcs(v.at(V_Q) + row, id * ap);
+      stcs(pc + V_R * kChunk, ri);
+      stcs(pc + V_U * kChunk, id * ri);
+      stcs(pc + V_S * kChunk, ap);
+      stcs(pc + V_Q * kChunk, id * ap);
     }
   }
 }
 
 // P_RR2: w = A u (= Ahat r) ; z = A q (= Ahat s) ; partials (r,u), (w,u), norm.
-template <typename T>
-__device__ __forceinline__ void pass_rr2(const DevMatrix& A, const Vec<T>& v, const Lanes& L, Dots<T>& d, int k,
-                                      bool paper_norm) {
-  T* wc = v.at((k & 1) ? V_WB : V_WA);
+template <typename T, int NS>
+__device__ __forceinline__ void pass_rr2(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, Dots<T>& d,
+                                         int k, bool paper_norm) {
+  const int wcs = (k & 1) ? V_WB : V_WA;
+  const GatherSlot<T, NS> gr{V.v.b + V_R * kChunk};
+  const GatherSlot<T, NS> gs{V.v.b + V_S * kChunk};
   FOR_CHUNKS(A, L) {
-    const int64_t base = CHUNK_BASE(L);
-    const int len = it.len;
-    const int32_t row = CHUNK_ROW(L);
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
+    T* pc = V.v.chunk(c, L.lane);
     T ri = T(0), ui = T(0), si = T(0);
-    if (in) { ri = ldcg(v.at(V_R) + row); ui = ldcs(v.at(V_U) + row); si = ldcg(v.at(V_S) + row); }
-    const T wi = row_dot<T, false>(A.col, v.val, v.at(V_R), nullptr, base, len, ri);
-    const T zi = row_dot<T, false>(A.col, v.val, v.at(V_S), nullptr, base, len, si);
+    if (in) { ri = ldcg(pc + V_R * kChunk); ui = ldcs(pc + V_U * kChunk); si = ldcg(pc + V_S * kChunk); }
+    const T wi = row_dot<T, false>(A.col, V.val, gr, nullptr, base, len, ri);
+    const T zi = row_dot<T, false>(A.col, V.val, gs, nullptr, base, len, si);
     if (in) {
-      stcs(wc + row, wi);
-      stcs(v.at(V_Z) + row, zi);
+      stcs(pc + wcs * kChunk, wi);
+      stcs(pc + V_Z * kChunk, zi);
       d.add(0, ri, ui);
       d.add(1, wi, ui);
       if (paper_norm) d.add(2, ui, ui); else d.add(2, ri, ri);
@@ -426,27 +435,33 @@ __device__ __forceinline__ void pass_rr2(const DevMatrix& A, const Vec<T>& v, co
   }
 }
 
+// P_ZERO_X: x = 0 (slot XS of an NS-slot FP64 block).
+template <int NS, int XS>
 __device__ __forceinline__ void pass_zero_x(const SysDesc& S, const Lanes& L) {
+  const Blk<double, NS> v{S.v64};
   FOR_CHUNKS(S.A, L) {
-    const int32_t row = CHUNK_ROW(L);
-    if (row < S.A.n) S.x[row] = 0.0;
+    const int32_t row = c * kChunk + L.lane;
+    if (row < S.A.n) v.chunk(c, L.lane)[XS * kChunk] = 0.0;
   }
 }
 
 // P_ORES (FP32_IR outer step): r64 = b - A x in FP64 ; partials (r64,r64), (b,b).
 __device__ __forceinline__ void pass_ores(const SysDesc& S, const Lanes& L, Dots<double>& d) {
   const DevMatrix& A = S.A;
+  const Blk<double, kNSIR> v{S.v64};
+  const GatherSlot<double, kNSIR> gx{S.v64 + IR_X * kChunk};
   FOR_CHUNKS(A, L) {
-    const int64_t base = CHUNK_BASE(L);
-    const int len = it.len;
-    const int32_t row = CHUNK_ROW(L);
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
+    double* pc = v.chunk(c, L.lane);
     double ax = 0.0, bi = 0.0;
-    if (in) { bi = __ldg(S.b + row); ax = __ldg(A.diag + row) * ldcg(S.x + row); }
-    ax = row_dot<double, true>(A.col, A.val, S.x, A.diag, base, len, ax);
+    if (in) { bi = __ldg(S.b + row); ax = __ldg(A.diag + row) * ldcg(pc + IR_X * kChunk); }
+    ax = row_dot<double, true>(A.col, A.val, gx, A.diag, base, len, ax);
     if (in) {
-      double t = bi - ax;
-      stcs(S.v64 + row, t);
+      const double t = bi - ax;
+      stcs(pc + IR_R * kChunk, t);
       d.add(0, t, t);
       d.add(1, bi, bi);
     }
@@ -455,23 +470,31 @@ __device__ __forceinline__ void pass_ores(const SysDesc& S, const Lanes& L, Dots
 
 // P_OINIT: rhs32 = r64 / ||r64|| ; r32 = rhs32 ; u32 = M^-1 r32 ; d32 = 0.
 __device__ __forceinline__ void pass_oinit(const SysDesc& S, const Lanes& L, double scale) {
+  const Blk<double, kNSIR> v64{S.v64};
+  const Blk<float, kNS32> v32{S.v32};
   FOR_CHUNKS(S.A, L) {
-    const int32_t row = CHUNK_ROW(L);
+    const int32_t row = c * kChunk + L.lane;
     if (row < S.A.n) {
-      float rh = (float)(ldcs(S.v64 + row) * scale);
-      stcs(S.v32 + V_RHS * S.vs + row, rh);
-      stcs(S.v32 + V_R * S.vs + row, rh);
-      stcs(S.v32 + V_U * S.vs + row, __ldg(S.v32 + V_INVD * S.vs + row) * rh);
-      stcs(S.v32 + V_X * S.vs + row, 0.0f);
+      float* pc = v32.chunk(c, L.lane);
+      const float rh = (float)(ldcs(v64.chunk(c, L.lane) + IR_R * kChunk) * scale);
+      stcs(pc + V_RHS * kChunk, rh);
+      stcs(pc + V_R * kChunk, rh);
+      stcs(pc + V_U * kChunk, ldcs(pc + V_INVD * kChunk) * rh);
+      stcs(pc + V_X * kChunk, 0.0f);
     }
   }
 }
 
 // P_OUPD: x += ||r64|| * d32 (FP64 solution accumulation).
 __device__ __forceinline__ void pass_oupd(const SysDesc& S, const Lanes& L, double rn) {
+  const Blk<double, kNSIR> v64{S.v64};
+  const Blk<float, kNS32> v32{S.v32};
   FOR_CHUNKS(S.A, L) {
-    const int32_t row = CHUNK_ROW(L);
-    if (row < S.A.n) S.x[row] = fma(rn, (double)ldcs(S.v32 + V_X * S.vs + row), S.x[row]);
+    const int32_t row = c * kChunk + L.lane;
+    if (row < S.A.n) {
+      double* px = v64.chunk(c, L.lane) + IR_X * kChunk;
+      *px = fma(rn, (double)ldcs(v32.chunk(c, L.lane) + V_X * kChunk), *px);
+    }
   }
 }
 
@@ -693,38 +716,44 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
     const bool fp32 = S.precision == PPCG_FP32_IR && (C.state >= S_O_START);
     double* slot = S.part + ((size_t)C.parity * P + g.rank()) * 4;
     bool partials = true;
-    if (!fp32 || pass == P_ORES) {
+    if (!fp32) {
       Dots<double> d;
-      Vec<double> v = vec64(S);
+      const View<double, kNS64> V = view64(S);
       switch (pass) {
         case P_SETUP1: pass_setup1(S, L, d, S.x_zero != 0); break;
-        case P_SETUP2: pass_setup2<double>(S.A, v, L, d, paper); break;
+        case P_SETUP2: pass_setup2(S.A, V, L, d, paper); break;
         case P_ITER:
-          if (C.first) pass_iter<double, true>(S.A, v, L, d, C.alpha, C.beta, C.iter, paper);
-          else pass_iter<double, false>(S.A, v, L, d, C.alpha, C.beta, C.iter, paper);
+          if (C.first) pass_iter<double, kNS64, true>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper);
+          else pass_iter<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper);
           break;
-        case P_TRUE: pass_true(S, L, d); break;
-        case P_RR1: pass_rr1<double>(S.A, v, L, C.iter == 0); partials = false; break;
-        case P_RR2: pass_rr2<double>(S.A, v, L, d, C.iter, paper); break;
-        case P_ZERO_X: pass_zero_x(S, L); partials = false; break;
+        case P_TRUE: pass_true<kNS64, V_X>(S, L, d); break;
+        case P_RR1: pass_rr1(S.A, V, L, C.iter == 0); partials = false; break;
+        case P_RR2: pass_rr2(S.A, V, L, d, C.iter, paper); break;
+        case P_ZERO_X: pass_zero_x<kNS64, V_X>(S, L); partials = false; break;
+        default: partials = false; break;
+      }
+      if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
+    } else if (pass == P_ORES || pass == P_ZERO_X || pass == P_OINIT || pass == P_OUPD) {
+      Dots<double> d;
+      switch (pass) {
         case P_ORES: pass_ores(S, L, d); break;
+        case P_ZERO_X: pass_zero_x<kNSIR, IR_X>(S, L); partials = false; break;
+        case P_OINIT: pass_oinit(S, L, 1.0 / C.rn); partials = false; break;
+        case P_OUPD: pass_oupd(S, L, C.rn); partials = false; break;
         default: partials = false; break;
       }
       if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
     } else {
       Dots<float> d;
-      Vec<float> v = vec32(S);
+      const View<float, kNS32> V = view32(S);
       switch (pass) {
-        case P_SETUP2: pass_setup2<float>(S.A, v, L, d, paper); break;
+        case P_SETUP2: pass_setup2(S.A, V, L, d, paper); break;
         case P_ITER:
-          if (C.first) pass_iter<float, true>(S.A, v, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
-          else pass_iter<float, false>(S.A, v, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
+          if (C.first) pass_iter<float, kNS32, true>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
+          else pass_iter<float, kNS32, false>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
           break;
-        case P_RR1: pass_rr1<float>(S.A, v, L, C.inner_iter == 0); partials = false; break;
-        case P_RR2: pass_rr2<float>(S.A, v, L, d, C.inner_iter, paper); break;
-        case P_ZERO_X: pass_zero_x(S, L); partials = false; break;
-        case P_OINIT: pass_oinit(S, L, 1.0 / C.rn); partials = false; break;
-        case P_OUPD: pass_oupd(S, L, C.rn); partials = false; break;
+        case P_RR1: pass_rr1(S.A, V, L, C.inner_iter == 0); partials = false; break;
+        case P_RR2: pass_rr2(S.A, V, L, d, C.inner_iter, paper); break;
         default: partials = false; break;
       }
       if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
