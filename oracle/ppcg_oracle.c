@@ -23,6 +23,12 @@
  *     formed; if it fails, the recurrence vectors are replaced by their true values
  *     (residual replacement, not in the paper) and the iteration continues.
  *   - rr_period > 0 additionally replaces residuals every rr_period iterations.
+ *   - Restart on breakdown (not in the paper): when the alpha denominator is not positive
+ *     after the first iteration -- which pipelined PCG meets near its attainable accuracy --
+ *     and fewer than max_restarts restarts were made, the residuals are replaced by their
+ *     true values, the direction recurrences p, s, q, z are reset to zero, and the next
+ *     step takes beta = 0, alpha = gamma / delta as at i = 0.  max_restarts = 0 reports the
+ *     breakdown instead.
  *   - b == 0 returns x = 0 with 0 iterations; a non-positive diagonal is "not SPD";
  *     gamma <= 0 or a non-positive alpha denominator is a breakdown.
  *   - The iteration count is the number of times the vector-update block runs.
@@ -115,7 +121,7 @@ static double true_residual(int64_t n, const int64_t* rp, const int32_t* ci, con
  */
 int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
                   const double* b, const double* x0, double* x, double tol, int32_t maxit,
-                  int32_t norm_mode, int32_t rr_period, int32_t sum_mode,
+                  int32_t norm_mode, int32_t rr_period, int32_t max_restarts, int32_t sum_mode,
                   double* alpha_hist, double* beta_hist, double* res_hist,
                   double* state_out, oracle_result* res) {
   memset(res, 0, sizeof(*res));
@@ -137,6 +143,9 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
   double gamma = 0.0, gamma_prev = 0.0, delta = 0.0, alpha = 0.0, alpha_prev = 0.0, beta = 0.0;
   double norm = 0.0;
   int32_t it = 0;
+  int restart = 0;        /* the next step starts the recurrences afresh (beta = 0) */
+  int32_t restarts = 0;
+  int32_t last_rr_it = -1; /* iteration of the latest residual replacement */
 
   for (int64_t i = 0; i < n; i++) x[i] = x0 ? x0[i] : 0.0;
   res->bnorm = sqrt(dot(sum_mode, n, b, b));
@@ -164,7 +173,7 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
   for (it = 0;; it++) {
     if (res_hist) res_hist[it] = norm;
     /* optional periodic residual replacement (not in the paper) */
-    int replace = (rr_period > 0 && it > 0 && it % rr_period == 0);
+    int replace = (rr_period > 0 && it > 0 && it % rr_period == 0 && last_rr_it != it);
     /* stop test at the top of iteration i on norm_i */
     if (!replace) {
       int passed = norm_mode ? (norm <= tol) : (norm <= tol * res->bnorm);
@@ -190,21 +199,42 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
       delta = dot(sum_mode, n, w, u);
       norm = norm_mode ? sqrt(dot(sum_mode, n, u, u)) : sqrt(dot(sum_mode, n, r, r));
       res->rr_count++;
+      last_rr_it = it;
       if (norm_mode ? (norm <= tol) : (norm <= tol * res->bnorm)) { status = OR_OK; break; }
     }
     if (it >= maxit) { status = OR_ERR_NOT_CONVERGED; break; }
     if (!isfinite(gamma) || !isfinite(delta)) { status = OR_ERR_NONFINITE; break; }
     /* lines 5-9: scalars */
-    if (it > 0) {
+    if (it > 0 && !restart) {
       beta = gamma / gamma_prev;
       double den = delta - beta * gamma / alpha_prev;
-      if (!(gamma > 0.0) || !(den > 0.0)) { status = OR_ERR_BREAKDOWN; break; }
+      if (!(gamma > 0.0) || !(den > 0.0)) {
+        if (restarts >= max_restarts) { status = OR_ERR_BREAKDOWN; break; }
+        /* restart: true residuals, direction recurrences reset, then beta = 0 */
+        restarts++;
+        for (int64_t i = 0; i < n; i++) { p[i] = 0.0; s[i] = 0.0; q[i] = 0.0; z[i] = 0.0; }
+        oracle_spmv(n, rp, ci, v, x, tmp);
+        for (int64_t i = 0; i < n; i++) r[i] = b[i] - tmp[i];
+        apply_jacobi(n, d, r, u);
+        oracle_spmv(n, rp, ci, v, u, w);
+        apply_jacobi(n, d, w, m);
+        oracle_spmv(n, rp, ci, v, m, nv);
+        gamma = dot(sum_mode, n, r, u);
+        delta = dot(sum_mode, n, w, u);
+        norm = norm_mode ? sqrt(dot(sum_mode, n, u, u)) : sqrt(dot(sum_mode, n, r, r));
+        res->rr_count++;
+        last_rr_it = it;
+        restart = 1;
+        it--;              /* re-enter the top of this iteration with the new values */
+        continue;
+      }
       alpha = gamma / den;
     } else {
       beta = 0.0;
       if (!(gamma > 0.0) || !(delta > 0.0)) { status = OR_ERR_BREAKDOWN; break; }
       alpha = gamma / delta;
     }
+    restart = 0;
     if (alpha_hist) alpha_hist[it] = alpha;
     if (beta_hist) beta_hist[it] = beta;
     /* lines 10-17: z, q, s, p, then x, r, u, w */

@@ -314,3 +314,31 @@ def test_residual_replacement():
     assert rel(st["r"], b - A @ st["x"]) < 1e-14
     assert rel(st["s"], A @ st["p"]) < 1e-14
     assert rel(st["z"], A @ st["q"]) < 1e-14
+
+
+def _breakdown_system():
+    """A 2-D log-normal variable-coefficient system (267^2 rows) on which plain pipelined
+    PCG breaks down (alpha denominator <= 0) just before reaching 1e-8."""
+    spec = [s for s in synth.batch_mix(128, 11) if s[0] == "varcoeff2d" and s[1] == 267][0]
+    return synth.build_spec(spec)
+
+
+def test_restart_on_breakdown():
+    """Without restarts Alg. 2 stops with a breakdown near its attainable accuracy while
+    Alg. 1 converges; with restarts (true residuals, reset directions, beta = 0) the
+    pipelined solve reaches the same true residual as Alg. 1."""
+    a, b = _breakdown_system()
+    plain = oracle.pipecg(a, b, tol=1e-8, maxit=20000, max_restarts=0)
+    assert plain["result"]["status"] == oracle.ERR_BREAKDOWN
+    classic = oracle.pcg(a, b, tol=1e-8, maxit=20000)
+    assert classic["result"]["status"] == oracle.OK
+    out = oracle.pipecg(a, b, tol=1e-8, maxit=20000)
+    r = out["result"]
+    assert r["status"] == oracle.OK and 1 <= r["rr_count"] <= 8
+    A = a.to_scipy()
+    assert np.linalg.norm(b - A @ out["x"]) <= 1e-8 * np.linalg.norm(b)
+    assert rel(out["x"], classic["x"]) < 1e-6
+    # before the first breakdown the two runs are the same computation
+    k = plain["result"]["iters"] - 5
+    assert np.array_equal(oracle.pipecg(a, b, tol=0.0, maxit=k, max_restarts=0)["x"],
+                          oracle.pipecg(a, b, tol=0.0, maxit=k)["x"])
