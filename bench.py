@@ -159,6 +159,178 @@ def cpu_oracle_rate(a, b, k_lo=2, k_hi=8):
             "seconds": t2 - t0}
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def measure_latency_2d(pp, torch):
+    """64x64 2-D Poisson (N = 4,096), b = A x_true: solve latency and time per iteration
+    on the default (cluster) path and the whole-GPU path."""
+    a = synth.poisson2d(64)
+    b = torch.from_numpy(a.to_scipy() @ synth.xtrue_uniform(a.n, 1)).cuda()
+    out = {"workload": "2D 5-point Poisson 64x64, FP64, rel tol 1e-8"}
+    for name, path in (("cluster", pp.PATH_CLUSTER), ("grid", pp.PATH_GRID)):
+        s = pp.Solver.from_csr(a, path=path)
+        x = torch.empty_like(b)
+        for _ in range(3):
+            s.solve(b, None, x, tol=TOL, maxit=MAXIT)
+        ts = []
+        for _ in range(20):
+            e0, e1 = _events()
+            e0.record()
+            _, info = s.solve(b, None, x, tol=TOL, maxit=MAXIT, sync=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        out[name] = {"solve_us_p50": float(np.median(ts)), "iters": info.iters,
+                     "us_per_iter": float(np.median(ts)) / max(info.iters, 1),
+                     "rel_res_true": info.rel_res_true}
+        s.close()
+    return out
+
+
+def measure_batch(pp, torch, count, seed=11, precision=0):
+    """Ragged batch (sizes log-uniform 1e3-2e5, half 2-D / half 3-D log-normal stencils):
+    one ppcg_batch_solve of CLUSTER-path handles against sequential ppcg_solve calls of
+    default-plan handles, both to rel 1e-8."""
+    specs = synth.batch_mix(count, seed)
+    systems = [synth.build_spec(sp) for sp in specs]
+    rows = sum(a.n for a, _ in systems)
+    bs = [torch.from_numpy(b).cuda() for _, b in systems]
+    xs = [torch.empty_like(b) for b in bs]
+    seq = [pp.Solver.from_csr(a, precision=precision) for a, _ in systems]
+    bat = [pp.Solver.from_csr(a, precision=precision, path=pp.PATH_CLUSTER) for a, _ in systems]
+    # warm-up (first launches of each kernel shape)
+    seq[0].solve(bs[0], None, xs[0], tol=TOL, maxit=MAXIT)
+    pp.batch_solve(bat[:2], bs[:2], xs[:2], tol=TOL, maxit=MAXIT)
+    e0, e1 = _events()
+    e0.record()
+    infos_seq = [s.solve(b, None, x, tol=TOL, maxit=MAXIT, sync=False)[1] for s, b, x in zip(seq, bs, xs)]
+    e1.record()
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) * 1e-3
+    e0, e1 = _events()
+    e0.record()
+    infos_bat = pp.batch_solve(bat, bs, xs, tol=TOL, maxit=MAXIT, sync=False)
+    e1.record()
+    torch.cuda.synchronize()
+    t_bat = e0.elapsed_time(e1) * 1e-3
+    ok = all(i.status == pp.OK for i in infos_bat) and all(i.status == pp.OK for i in infos_seq)
+    bad = [{"n": a.n, "seq": pp.status_name(i.status), "seq_iters": i.iters, "batch": pp.status_name(j.status),
+            "batch_iters": j.iters} for (a, _), i, j in zip(systems, infos_seq, infos_bat)
+           if i.status != pp.OK or j.status != pp.OK][:8]
+    iters = sum(i.iters for i in infos_bat)
+    for s in seq + bat:
+        s.close()
+    return {"systems": count, "rows": rows, "precision": "fp64" if precision == 0 else "fp32_ir",
+            "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat, "all_ok": ok, "not_ok": bad,
+            "iters_total": iters, "row_iters_per_s": sum(i.iters * a.n for i, (a, _) in zip(infos_bat, systems)) / t_bat}
+
+
+def _serving_pool(seed, count, hi, buckets=24):
+    """Request stream: sizes log-uniform [1e3, hi] over {2-D, 3-D var-coeff, RGG}.  Sizes are
+    snapped to `buckets` log-spaced values so each (family, size) matrix is built once;
+    every request gets its own right-hand side."""
+    specs = synth.serving_mix(count, seed, hi=hi)
+    grid = np.exp(np.linspace(np.log(1e3), np.log(hi), buckets))
+    built = {}
+    reqs = []
+    for k, (fam, size, _, _) in enumerate(specs):
+        rows = size * size if fam == "varcoeff2d" else size ** 3 if fam == "varcoeff3d" else size
+        rb = grid[np.argmin(np.abs(np.log(grid) - np.log(rows)))]
+        if fam == "varcoeff2d":
+            size = max(2, int(round(np.sqrt(rb))))
+        elif fam == "varcoeff3d":
+            size = max(2, int(round(np.cbrt(rb))))
+        else:
+            size = int(round(rb))
+        key = (fam, size)
+        if key not in built:
+            built[key] = synth.build_spec((fam, size, 7919 * len(built) + seed, 0))[0]
+        a = built[key]
+        reqs.append((a, synth.rhs_uniform(a.n, 100000 + k)))
+    return reqs
+
+
+def run_server(pp, reqs, arrivals, precision=1, epoch_iters=128):
+    """Submit reqs at the given arrival offsets (s); poll until all finish.  Returns
+    (latencies, wall seconds, statuses)."""
+    srv = pp.Server(precision=precision, epoch_iters=epoch_iters)
+    t0 = time.perf_counter()
+    pending = {}
+    lat = [None] * len(reqs)
+    status = [None] * len(reqs)
+    k = 0
+    while k < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while k < len(reqs) and arrivals[k] <= now:
+            a, b = reqs[k]
+            pending[srv.submit(a, b, tol=TOL, maxit=MAXIT)] = (k, a.n, t0 + arrivals[k])
+            k += 1
+        for t in list(pending):
+            st, _, info = srv.poll(t, pending[t][1])
+            if st != pp.PENDING:
+                i, _, ta = pending.pop(t)
+                lat[i] = time.perf_counter() - ta
+                status[i] = st
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    srv.close()
+    return lat, wall, status
+
+
+def measure_serving(pp, nreq=160, hi=2e5, seed=5, rate_factors=(0.5,)):
+    """Continuous batching: saturation throughput (all requests at t = 0), then Poisson
+    arrivals at rate_factor x saturation; p50/p99 latency = poll-visible completion - arrival."""
+    reqs = _serving_pool(seed, nreq, hi)
+    run_server(pp, reqs[:8], [0.0] * 8)                       # warm-up
+    lat, wall, st = run_server(pp, reqs, [0.0] * len(reqs))
+    sat = len(reqs) / wall
+    out = {"requests": nreq, "size_range": [1e3, hi], "precision": "fp32_ir", "saturation_solves_per_s": sat,
+           "all_ok": all(s == pp.OK for s in st), "rates": []}
+    rng = np.random.default_rng(seed)
+    for f in rate_factors:
+        rate = f * sat
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+        arr -= arr[0]
+        lat, wall, st = run_server(pp, reqs, arr)
+        out["rates"].append({"rate_factor": f, "offered_per_s": rate, "solves_per_s": len(reqs) / wall,
+                             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                             "all_ok": all(s == pp.OK for s in st)})
+    return out
+
+
+def measure_rgg(pp, torch, npts=4_000_000, seed=3):
+    """Random geometric graph Laplacian (expected degree 14) + 1e-3 I: FP32+IR to 1e-8 and
+    FP64 to 1e-8 and 1e-10, time to solution and the FP32+IR error against the FP64 1e-10
+    solution."""
+    radius = (3 * 14.0 / (4 * np.pi * npts)) ** (1 / 3)
+    a = synth.rgg_laplacian(npts, radius, 1e-3, seed)
+    b = torch.from_numpy(synth.rhs_uniform(a.n, seed)).cuda()
+    out = {"workload": f"RGG Laplacian {npts} points, radius {radius:.6f}, shift 1e-3", "N": a.n, "nnz": a.nnz}
+    runs = {}
+    for name, prec, tol in (("fp64_1e-10", pp.FP64, 1e-10), ("fp64_1e-8", pp.FP64, 1e-8),
+                            ("fp32_ir_1e-8", pp.FP32_IR, 1e-8)):
+        s = pp.Solver.from_csr(a, precision=prec)
+        x = torch.empty_like(b)
+        s.solve(b, None, x, tol=tol, maxit=MAXIT)
+        e0, e1 = _events()
+        e0.record()
+        _, info = s.solve(b, None, x, tol=tol, maxit=MAXIT, sync=False)
+        e1.record()
+        torch.cuda.synchronize()
+        runs[name] = (x.clone(), info, e0.elapsed_time(e1) * 1e-3)
+        s.close()
+    ref = runs["fp64_1e-10"][0]
+    for name, (x, info, t) in runs.items():
+        out[name] = {"s": t, "iters": info.iters, "outer": info.outer_iters, "status": pp.status_name(info.status),
+                     "rel_res_true": info.rel_res_true,
+                     "err_vs_fp64_1e-10": (torch.linalg.norm(x - ref) / torch.linalg.norm(ref)).item()}
+    out["fp32_ir_speedup_vs_fp64_1e-8"] = runs["fp64_1e-8"][2] / runs["fp32_ir_1e-8"][2]
+    return out
+
+
 def run_reference(args, ws, rank):
     """Reference arm: the oracle, as it stands, on the host cores (rank 0 only)."""
     if rank != 0:
@@ -198,10 +370,30 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID_N, help="grid side (256 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the latency, batch and serving figures")
+    ap.add_argument("--mode", default="main", choices=["main", "batch", "serve", "rgg"],
+                    help="batch: the 1024-system ragged batch; serve: the serving rate sweep; "
+                         "rgg: FP32+IR vs FP64 on the 4M-point random geometric graph")
+    ap.add_argument("--batch-count", type=int, default=1024)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.mode != "main":
+        import torch
+        import paper_2105_06176_b300 as pp
+        torch.cuda.set_device(local)
+        if args.mode == "rgg":
+            res = {"mode": "rgg", "rgg": measure_rgg(pp, torch)}
+        elif args.mode == "batch":
+            res = {"mode": "batch", "fp64": measure_batch(pp, torch, args.batch_count),
+                   "fp32_ir": measure_batch(pp, torch, args.batch_count, precision=1)}
+        else:
+            res = {"mode": "serve", "serving": measure_serving(pp, nreq=2000, hi=4e6,
+                                                               rate_factors=(0.25, 0.5, 1.0, 2.0, 4.0))}
+        if rank == 0:
+            print(json.dumps(res), flush=True)
         return
 
     import torch
@@ -324,6 +516,11 @@ def main():
                                  "rel_res_true": im.rel_res_true, "err_vs_fp64_solution": err,
                                  "fp32_bytes_per_iter": b_alg(n, nnz, 4)}
         sm.close()
+
+    if not args.no_extras:
+        line["latency_2d64"] = measure_latency_2d(pp, torch)
+        line["batch"] = measure_batch(pp, torch, 128)
+        line["serving"] = measure_serving(pp)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(a, b)

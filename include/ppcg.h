@@ -80,7 +80,10 @@ typedef struct {
   int64_t spin_limit_ns;    /* time limit of one device-side barrier wait (ns); exceeded -> TIMEOUT */
   int32_t cluster_max_rows; /* PATH_AUTO: systems with at most this many rows take the CLUSTER path */
   int32_t epoch_iters;      /* server: iterations each resident solve advances per epoch */
-  int32_t reserved[6];
+  int32_t max_restarts;     /* restarts after a breakdown (alpha denominator <= 0 past the first
+                               iteration): true residuals, direction recurrences reset, beta = 0.
+                               0 = report PPCG_ERR_BREAKDOWN instead */
+  int32_t reserved[5];
 } ppcg_opts;
 
 /* Per-solve results.  Filled asynchronously; valid after the solve's stream is synchronised. */
@@ -89,7 +92,7 @@ typedef struct {
   int32_t iters;             /* iterations of Alg. 2 (executions of the vector-update block); FP32_IR:
                                 summed over inner solves */
   int32_t outer_iters;       /* FP32_IR refinement steps (0 for FP64) */
-  int32_t rr_count;          /* residual replacements performed */
+  int32_t rr_count;          /* residual replacements performed (restarts included) */
   double rel_res_recursive;  /* stopping norm at exit, divided by ||b|| (REL_R) or absolute (PAPER_U_ABS) */
   double rel_res_true;       /* ||b - A x||_2 / ||b||_2 at exit, FP64 (0 when b = 0) */
   double seconds;            /* device time of the solve (globaltimer), setup and final residual included */
@@ -99,7 +102,7 @@ typedef struct {
 
 /* Fill *opts with defaults: FP64, AUTO format/path, REL_R, sigma autotune, rr_period 0,
  * inner_tol 1e-2, inner_maxit 100000, max_outer 30, spin_limit 10 s, cluster_max_rows 16384,
- * epoch_iters 256. */
+ * epoch_iters 256, max_restarts 8. */
 void ppcg_opts_default(ppcg_opts* opts);
 
 /*

@@ -50,7 +50,7 @@ class Opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64),
                 ("cluster_max_rows", ctypes.c_int32), ("epoch_iters", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("max_restarts", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class Info(ctypes.Structure):

@@ -218,6 +218,7 @@ void ppcg_opts_default(ppcg_opts* o) {
   o->spin_limit_ns = 10000000000LL;
   o->cluster_max_rows = 16384;
   o->epoch_iters = 256;
+  o->max_restarts = 8;
 }
 
 const char* ppcg_last_error(void) { return g_err; }
@@ -331,6 +332,7 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   d.rr_period = fp32 && h->opts.rr_period == 0 ? 25 : h->opts.rr_period;
   d.inner_maxit = h->opts.inner_maxit;
   d.max_outer = h->opts.max_outer;
+  d.max_restarts = h->opts.max_restarts < 0 ? 0 : h->opts.max_restarts;
   d.inner_tol = h->opts.inner_tol;
   d.spin_limit_ns = h->opts.spin_limit_ns;
   d.nparts = h->nparts;

@@ -58,7 +58,8 @@ enum State : int32_t {
 struct Ctl {
   int32_t state, pass, status, iter;      // iter: Alg. 2 iterations (inner ones for FP32_IR)
   int32_t inner_iter, outer, rr_count, last_rr_iter;
-  int32_t parity, first, exit_now, pad;
+  int32_t parity, first, exit_now, restart;  // restart: next step starts afresh (beta = 0)
+  int32_t restarts, pad2;
   double gamma, gamma_prev, delta, alpha, alpha_prev, beta, norm;
   double bnorm, rn, rn_prev, res_true, inner_norm0, inner_target;
   unsigned long long t_start, t_end;
@@ -69,6 +70,7 @@ struct SysDesc {
   DevMatrix A;
   int32_t precision, norm, rr_period, maxit;
   int32_t inner_maxit, max_outer, nparts, x_zero;  // x_zero: x starts at 0 (skip the A x0 gather)
+  int32_t max_restarts, pad;
   double tol, inner_tol;
   int64_t spin_limit_ns;
   const double* b;       // right-hand side, solver order (plain array)

@@ -585,7 +585,7 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
       case S_AFTER_SETUP2:
         take_dots(c); c.state = S_TOP; break;
       case S_AFTER_ITER:
-        c.gamma_prev = c.gamma; c.alpha_prev = c.alpha; c.iter++;
+        c.gamma_prev = c.gamma; c.alpha_prev = c.alpha; c.iter++; c.restart = 0;
         take_dots(c); c.state = S_TOP; break;
       case S_AFTER_RR2:
         take_dots(c); c.rr_count++; c.last_rr_iter = c.iter;
@@ -602,8 +602,15 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
         }
         if (c.iter >= S.maxit) { c.status = PPCG_ERR_NOT_CONVERGED; c.state = S_FINAL; break; }
         if (!isfinite(c.gamma) || !isfinite(c.delta)) { c.status = PPCG_ERR_NONFINITE; c.state = S_FINAL; break; }
-        if (!scalars(c, c.iter)) { c.status = PPCG_ERR_BREAKDOWN; c.state = S_FINAL; break; }
-        c.first = (c.iter == 0);
+        if (!scalars(c, c.restart ? 0 : c.iter)) {
+          if (c.iter > 0 && !c.restart && c.restarts < S.max_restarts) {
+            // restart: replace the residuals, reset the direction recurrences, beta = 0 next
+            c.restarts++; c.restart = 1;
+            c.pass = P_RR1; c.state = S_AFTER_RR1; return;
+          }
+          c.status = PPCG_ERR_BREAKDOWN; c.state = S_FINAL; break;
+        }
+        c.first = (c.iter == 0 || c.restart);
         c.pass = P_ITER; c.state = S_AFTER_ITER; return;
       }
       case S_AFTER_TRUE:
@@ -727,7 +734,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
           else pass_iter<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper);
           break;
         case P_TRUE: pass_true<kNS64, V_X>(S, L, d); break;
-        case P_RR1: pass_rr1(S.A, V, L, C.iter == 0); partials = false; break;
+        case P_RR1: pass_rr1(S.A, V, L, C.iter == 0 || C.restart); partials = false; break;
         case P_RR2: pass_rr2(S.A, V, L, d, C.iter, paper); break;
         case P_ZERO_X: pass_zero_x<kNS64, V_X>(S, L); partials = false; break;
         default: partials = false; break;

@@ -192,3 +192,25 @@ def test_barrier_timeout_is_reported_not_hung():
     a, b = problem("poisson2d_64")
     x, info = gpu(a, b)             # the context still works
     assert info.status == m.OK
+
+
+def test_restart_on_breakdown_parity():
+    """The system on which plain Alg. 2 breaks down near 1e-8.  Up to the breakdown the
+    iterates follow the oracle's, so with restarts disabled both report the breakdown at
+    the same iteration (+-2).  After a restart the path depends on rounding (the breakdown
+    is itself a rounding effect), so the bar there is the outcome: both converge with the
+    same number of restarts to a true residual <= 1e-8, within 10% of the oracle's count."""
+    m = pp()
+    spec = [s for s in synth.batch_mix(128, 11) if s[0] == "varcoeff2d" and s[1] == 267][0]
+    a, b = synth.build_spec(spec)
+    ref = oracle.pipecg(a, b, tol=1e-8, maxit=20000)
+    ref0 = oracle.pipecg(a, b, tol=1e-8, maxit=20000, max_restarts=0)
+    for path in (1, 2):
+        x0, info0 = gpu(a, b, tol=1e-8, maxit=20000, path=path, max_restarts=0)
+        assert info0.status == m.ERR_BREAKDOWN
+        assert abs(info0.iters - ref0["result"]["iters"]) <= 2
+        x, info = gpu(a, b, tol=1e-8, maxit=20000, path=path)
+        assert info.status == m.OK
+        assert info.rr_count >= 1 and ref["result"]["rr_count"] >= 1
+        assert abs(info.iters - ref["result"]["iters"]) <= 0.1 * ref["result"]["iters"]
+        assert np.linalg.norm(b - a.to_scipy() @ x) <= 1e-8 * np.linalg.norm(b)
