@@ -286,7 +286,14 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
     h->shape = 0;
     if (const char* e = getenv("PPCG_GRID_SHAPE")) h->shape = atoi(e);   // launch-shape tuning knob
     if (h->shape < 0 || h->shape >= grid_shape_count()) h->shape = 0;
-    h->grid = grid_blocks_for_device(h->device, h->shape);
+    // One CTA per SM at most for small systems: enough warps for one 32-row chunk each,
+    // so the grid barrier spans only the CTAs that have rows to work on.
+    const int full = grid_blocks_for_device(h->device, h->shape);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int warps = grid_threads(h->shape) / 32;
+    const int64_t need = (h->A.nchunks + warps - 1) / warps;
+    h->grid = need >= sms ? full : (int)std::max<int64_t>(1, need);
     h->nparts = h->grid;
   } else {
     h->grid = kClusterSize;
@@ -377,7 +384,7 @@ ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double*
         }
       }
     }
-    e = launch_clusters(h->d_desc, d_list, d_list + 1, 1, 0, st);
+    e = launch_clusters(h->d_desc, d_list, d_list + 1, 1, 0, st, /*spread=*/true);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -89,8 +89,9 @@ struct SysDesc {
 // Launchers (solver.cu)
 cudaError_t launch_grid(const SysDesc* d_desc, int shape, int grid, int budget, cudaStream_t st);
 cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
-                            int nclusters, int budget, cudaStream_t st);
+                            int nclusters, int budget, cudaStream_t st, bool spread = false);
 int grid_shape_count();
+int grid_threads(int shape);
 int grid_blocks_for_device(int device, int shape);
 int max_active_clusters(int device);
 cudaError_t launch_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, int grid,

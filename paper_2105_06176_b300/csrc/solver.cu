@@ -147,6 +147,50 @@ __device__ __forceinline__ float ld_stream(const float* p) {
   return v;
 }
 
+// ---------------------------------------------------------- bulk-copy staging (TMA) --
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bulk asynchronous copy global -> shared, completing bytes on the mbarrier.  Both
+// addresses 16-byte aligned, size a multiple of 16 (every caller copies whole 32-row slots).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+  return ok != 0;
+}
+// Orders this thread's earlier generic-proxy accesses before its later bulk copies.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+// Bounded wait for a stage's bulk copies; on expiry records a timeout in *err and returns.
+__device__ __forceinline__ void stage_wait(uint64_t* bar, unsigned phase, int32_t* err) {
+  for (uint32_t spin = 0; !mbar_try_wait(bar, phase); spin++) {
+    if (spin > (1u << 22)) {
+      atomicCAS(err, 0, (int32_t)PPCG_ERR_TIMEOUT);
+      return;
+    }
+  }
+}
+
+constexpr int kStageLen = 8;                 // SELL slots per row staged in shared memory
+constexpr int kStageVecBytes = 10 * kChunk * 8;                        // one FP64 tile
+constexpr int kStageBytes = kStageVecBytes + kStageLen * kChunk * (4 + 8);
+constexpr int kWarpStageBytes = 2 * kStageBytes;                       // double-buffered
+
 // Chunk-interleaved vector block: for every 32-row chunk c, NS slots of 32 values each, so
 // slot k of row i lives at base + (i / 32) * NS * 32 + k * 32 + i % 32.  A warp reaches all
 // its rows' vectors from one chunk pointer with compile-time slot offsets, and every slot
@@ -352,6 +396,110 @@ __device__ __forceinline__ void pass_iter(const DevMatrix& A, const View<T, NS>&
       d.add(1, wnn, un);
       if (paper_norm) d.add(2, un, un); else d.add(2, ri, ri);
     }
+  }
+}
+
+// P_ITER with bulk-copy staging (whole-GPU path).  Each warp double-buffers its chunks in
+// shared memory: while it computes chunk c, the bulk copies of chunk c + W (the row tile of
+// every vector it reads, and the chunk's SELL columns and values when the rows have at most
+// kStageLen slots) are in flight.  Only the gathers of w from other chunks and the results
+// go through registers to and from global memory.
+template <typename T, int NS, bool FIRST>
+__device__ __forceinline__ void pass_iter_staged(const DevMatrix& A, const View<T, NS>& V, const Lanes& L,
+                                                 Dots<T>& d, T alpha, T beta, int k, bool paper_norm,
+                                                 unsigned char* wst, uint64_t* bars, unsigned& phases,
+                                                 int32_t* err) {
+  constexpr int NV = (NS == 11) ? 10 : NS;     // slots read by the pass (FP32 block: not rhs)
+  const int wcs = (k & 1) ? V_WB : V_WA;
+  const int wns = (k & 1) ? V_WA : V_WB;
+  const GatherSlot<T, NS> gw{V.v.b + wcs * kChunk};
+  const int32_t* __restrict__ col = A.col;
+  const T* __restrict__ val = V.val;
+  const int64_t* __restrict__ cptr = A.cptr;
+  const int32_t n = (int32_t)A.n;
+  const int32_t nchunks = (int32_t)A.nchunks;
+  const int lane = L.lane;
+
+  auto vec_s = [&](int st) { return reinterpret_cast<T*>(wst + st * kStageBytes); };
+  auto col_s = [&](int st) { return reinterpret_cast<int32_t*>(wst + st * kStageBytes + kStageVecBytes); };
+  auto val_s = [&](int st) {
+    return reinterpret_cast<T*>(wst + st * kStageBytes + kStageVecBytes + kStageLen * kChunk * 4);
+  };
+  auto issue = [&](int st, int32_t c) {            // one lane
+    const int64_t b0 = __ldg(cptr + c);
+    const int len = (int)((__ldg(cptr + c + 1) - b0) / kChunk);
+    const T* tile = V.v.b + (int64_t)c * NS * kChunk;
+    const unsigned lo = (unsigned)(wns * kChunk * sizeof(T));
+    const unsigned hi = (unsigned)((NV - wns - 1) * kChunk * sizeof(T));
+    unsigned bytes = lo + hi;
+    const bool mat = len > 0 && len <= kStageLen;
+    if (mat) bytes += (unsigned)(len * kChunk * (4 + sizeof(T)));
+    fence_proxy_async();
+    mbar_expect_tx(bars + st, bytes);
+    bulk_g2s(vec_s(st), tile, lo, bars + st);
+    bulk_g2s(vec_s(st) + (wns + 1) * kChunk, tile + (wns + 1) * kChunk, hi, bars + st);
+    if (mat) {
+      bulk_g2s(col_s(st), col + b0, (unsigned)(len * kChunk * 4), bars + st);
+      bulk_g2s(val_s(st), val + b0, (unsigned)(len * kChunk * sizeof(T)), bars + st);
+    }
+  };
+
+  int st = 0;
+  int32_t c = L.gw;
+  if (c < nchunks && lane == 0) issue(0, c);
+  for (; c < nchunks; c += L.W, st ^= 1) {
+    const int32_t cn = c + L.W;
+    if (cn < nchunks && lane == 0) issue(st ^ 1, cn);
+    const int64_t b0 = __ldg(cptr + c);
+    const int len = (int)((__ldg(cptr + c + 1) - b0) / kChunk);
+    stage_wait(bars + st, (phases >> st) & 1u, err);
+    phases ^= 1u << st;
+    const int32_t row = c * kChunk + lane;
+    const bool in = row < n;
+    const T* vsm = vec_s(st) + lane;
+    T acc = vsm[wcs * kChunk];
+    const T wi = acc;
+    if (len <= kStageLen) {
+      const int32_t* cs = col_s(st) + lane;
+      const T* as = val_s(st) + lane;
+      int32_t cc[kStageLen];
+      T aa[kStageLen];
+#pragma unroll
+      for (int j = 0; j < kStageLen; j++)
+        if (j < len) { cc[j] = cs[j * kChunk]; aa[j] = as[j * kChunk]; }
+#pragma unroll
+      for (int j = 0; j < kStageLen; j++)
+        if (j < len) acc = fma(aa[j], gw(cc[j]), acc);
+    } else {
+      acc = row_dot<T, false>(col, val, gw, nullptr, b0 + lane, len, acc);
+    }
+    if (in) {
+      const T ni = acc;
+      const T id = vsm[V_INVD * kChunk];
+      const T ui = vsm[V_U * kChunk];
+      const T mi = id * wi;
+      const T zi = FIRST ? ni : fma(beta, vsm[V_Z * kChunk], ni);
+      const T qi = FIRST ? mi : fma(beta, vsm[V_Q * kChunk], mi);
+      const T si = FIRST ? wi : fma(beta, vsm[V_S * kChunk], wi);
+      const T pi = FIRST ? ui : fma(beta, vsm[V_P * kChunk], ui);
+      const T xi = fma(alpha, pi, vsm[V_X * kChunk]);
+      const T ri = fma(-alpha, si, vsm[V_R * kChunk]);
+      const T un = fma(-alpha, qi, ui);
+      const T wnn = fma(-alpha, zi, wi);
+      T* pc = V.v.chunk(c, lane);
+      stcs(pc + V_Z * kChunk, zi);
+      stcs(pc + V_Q * kChunk, qi);
+      stcs(pc + V_S * kChunk, si);
+      stcs(pc + V_P * kChunk, pi);
+      stcs(pc + V_X * kChunk, xi);
+      stcs(pc + V_R * kChunk, ri);
+      stcs(pc + V_U * kChunk, un);
+      stcs(pc + wns * kChunk, wnn);
+      d.add(0, ri, un);
+      d.add(1, wnn, un);
+      if (paper_norm) d.add(2, un, un); else d.add(2, ri, ri);
+    }
+    __syncwarp();
   }
 }
 
@@ -691,8 +839,9 @@ struct Shared {
   double sm[3 * 32];
 };
 
-template <class G>
-__device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
+template <bool STAGED, class G>
+__device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsigned char* stage_mem,
+                           uint64_t* stage_bars, unsigned& phases) {
   __syncthreads();   // previous system's readers of sh are done
   if (threadIdx.x == 0) {
     sh.S = *Sg;
@@ -730,8 +879,15 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
         case P_SETUP1: pass_setup1(S, L, d, S.x_zero != 0); break;
         case P_SETUP2: pass_setup2(S.A, V, L, d, paper); break;
         case P_ITER:
-          if (C.first) pass_iter<double, kNS64, true>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper);
-          else pass_iter<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper);
+          if (STAGED) {
+            unsigned char* wst = stage_mem + (threadIdx.x >> 5) * kWarpStageBytes;
+            uint64_t* bars = stage_bars + 2 * (threadIdx.x >> 5);
+            if (C.first) pass_iter_staged<double, kNS64, true>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, wst, bars, phases, S.err);
+            else pass_iter_staged<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, wst, bars, phases, S.err);
+          } else {
+            if (C.first) pass_iter<double, kNS64, true>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper);
+            else pass_iter<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper);
+          }
           break;
         case P_TRUE: pass_true<kNS64, V_X>(S, L, d); break;
         case P_RR1: pass_rr1(S.A, V, L, C.iter == 0 || C.restart); partials = false; break;
@@ -756,8 +912,15 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
       switch (pass) {
         case P_SETUP2: pass_setup2(S.A, V, L, d, paper); break;
         case P_ITER:
-          if (C.first) pass_iter<float, kNS32, true>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
-          else pass_iter<float, kNS32, false>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
+          if (STAGED) {
+            unsigned char* wst = stage_mem + (threadIdx.x >> 5) * kWarpStageBytes;
+            uint64_t* bars = stage_bars + 2 * (threadIdx.x >> 5);
+            if (C.first) pass_iter_staged<float, kNS32, true>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper, wst, bars, phases, S.err);
+            else pass_iter_staged<float, kNS32, false>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper, wst, bars, phases, S.err);
+          } else {
+            if (C.first) pass_iter<float, kNS32, true>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
+            else pass_iter<float, kNS32, false>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
+          }
           break;
         case P_RR1: pass_rr1(S.A, V, L, C.inner_iter == 0); partials = false; break;
         case P_RR2: pass_rr2(S.A, V, L, d, C.inner_iter, paper); break;
@@ -765,6 +928,8 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
       }
       if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
     }
+    // The next pass may read this pass's stores with bulk copies (async proxy).
+    if (STAGED) fence_proxy_async();
     if (!g.sync()) {
       if (threadIdx.x == 0) { C.status = PPCG_ERR_TIMEOUT; C.state = S_DONE; }
       break;
@@ -781,23 +946,37 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh) {
   }
 }
 
-template <int THREADS, int MINB>
+template <int THREADS, int MINB, bool STAGED>
 __global__ void __launch_bounds__(THREADS, MINB) k_grid(const SysDesc* d, int budget) {
   __shared__ Shared sh;
+  __shared__ uint64_t bars[2 * (THREADS / 32)];
+  extern __shared__ __align__(128) unsigned char stage_mem[];
+  unsigned phases = 0;
+  if (STAGED) {
+    if ((threadIdx.x & 31) == 0) {
+      mbar_init(bars + 2 * (threadIdx.x >> 5), 1);
+      mbar_init(bars + 2 * (threadIdx.x >> 5) + 1, 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+  }
   GridGroup g{d->bar, d->err, (long long)d->spin_limit_ns, 0u};
-  run_system(g, d, budget, sh);
+  run_system<STAGED>(g, d, budget, sh, stage_mem, bars, phases);
 }
 
 // Launch shapes of the grid path: (threads per CTA, minimum CTAs per SM for the register
-// budget).  Index 0 is the default (fastest measured on the 256^3 stencil); the others trade
-// registers against resident warps.
+// budget, bulk-copy staging).  Index 0 is the default (fastest measured on the 256^3
+// stencil); the others trade registers, resident warps and staging.
 struct GridShape {
   void (*fn)(const SysDesc*, int);
   int threads;
+  int smem;     // dynamic shared memory (staging buffers)
 };
 const GridShape kGridShapes[] = {
-    {k_grid<512, 2>, 512}, {k_grid<256, 4>, 256}, {k_grid<256, 3>, 256}, {k_grid<512, 1>, 512},
-    {k_grid<384, 2>, 384}, {k_grid<128, 6>, 128},
+    {k_grid<512, 2, false>, 512, 0}, {k_grid<256, 4, false>, 256, 0}, {k_grid<256, 3, false>, 256, 0},
+    {k_grid<512, 1, false>, 512, 0}, {k_grid<384, 2, false>, 384, 0}, {k_grid<128, 6, false>, 128, 0},
+    {k_grid<512, 1, true>, 512, 16 * kWarpStageBytes}, {k_grid<256, 2, true>, 256, 8 * kWarpStageBytes},
+    {k_grid<384, 1, true>, 384, 12 * kWarpStageBytes},
 };
 constexpr int kNumGridShapes = (int)(sizeof(kGridShapes) / sizeof(kGridShapes[0]));
 
@@ -806,8 +985,10 @@ __global__ void __launch_bounds__(kClusterThreads, 4) k_cluster(const SysDesc* d
   __shared__ Shared sh;
   ClusterGroup g;
   unsigned cid;
+  unsigned phases = 0;
   asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
-  for (int k = list_ptr[cid]; k < list_ptr[cid + 1]; k++) run_system(g, descs + list[k], budget, sh);
+  for (int k = list_ptr[cid]; k < list_ptr[cid + 1]; k++)
+    run_system<false>(g, descs + list[k], budget, sh, nullptr, nullptr, phases);
 }
 
 // Failure-detection self test: the grid barrier with one rank that never arrives.  Every
@@ -823,12 +1004,20 @@ __global__ void k_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, in
 }  // namespace
 
 int grid_shape_count() { return kNumGridShapes; }
+int grid_threads(int shape) { return kGridShapes[shape].threads; }
+
+static void set_smem_attr(const GridShape& gs) {
+  if (gs.smem > 0 && cudaFuncSetAttribute((const void*)gs.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, gs.smem) !=
+                         cudaSuccess)
+    cudaGetLastError();
+}
 
 int grid_blocks_for_device(int device, int shape) {
   int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   const GridShape& gs = kGridShapes[shape];
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gs.fn, gs.threads, 0);
+  set_smem_attr(gs);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gs.fn, gs.threads, gs.smem);
   if (per < 1) per = 1;
   return sms * per;
 }
@@ -856,14 +1045,24 @@ int max_active_clusters(int device) {
 cudaError_t launch_grid(const SysDesc* d_desc, int shape, int grid, int budget, cudaStream_t st) {
   void* args[] = {(void*)&d_desc, (void*)&budget};
   const GridShape& gs = kGridShapes[shape];
-  return cudaLaunchCooperativeKernel((void*)gs.fn, dim3(grid), dim3(gs.threads), args, 0, st);
+  return cudaLaunchCooperativeKernel((void*)gs.fn, dim3(grid), dim3(gs.threads), args, gs.smem, st);
 }
 
 cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
-                            int nclusters, int budget, cudaStream_t st) {
+                            int nclusters, int budget, cudaStream_t st, bool spread) {
+  // spread: request enough dynamic shared memory that no two CTAs share an SM, so a lone
+  // cluster gets the FP64 pipes of 8 SMs instead of being packed onto two.
+  static bool attr_set = false;
+  const int spread_smem = 120 * 1024;
+  if (spread && !attr_set) {
+    if (cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, spread_smem) != cudaSuccess)
+      cudaGetLastError();
+    attr_set = true;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kClusterSize * nclusters);
   cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = spread ? spread_smem : 0;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
