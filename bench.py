@@ -37,6 +37,7 @@ GRID_N = 256
 SEED = 1
 TOL = 1e-8
 MAXIT = 20000
+SERVE_MAXIT = 200000       # served requests include 2-D stencils of up to 4e6 rows (kappa ~1e7)
 WORKLOAD = ("3D 7-point variable-coefficient diffusion 256^3 (N=16,777,216, nnz=117,047,296), "
             "log-normal(0,1) face coefficients, Jacobi, b~U[-1,1], x0=0, rel tol 1e-8, FP64 pipelined PCG")
 
@@ -261,12 +262,13 @@ def run_server(pp, reqs, arrivals, precision=1, epoch_iters=128):
     pending = {}
     lat = [None] * len(reqs)
     status = [None] * len(reqs)
+    infos = [None] * len(reqs)
     k = 0
     while k < len(reqs) or pending:
         now = time.perf_counter() - t0
         while k < len(reqs) and arrivals[k] <= now:
             a, b = reqs[k]
-            pending[srv.submit(a, b, tol=TOL, maxit=MAXIT)] = (k, a.n, t0 + arrivals[k])
+            pending[srv.submit(a, b, tol=TOL, maxit=SERVE_MAXIT)] = (k, a.n, t0 + arrivals[k])
             k += 1
         for t in list(pending):
             st, _, info = srv.poll(t, pending[t][1])
@@ -274,9 +276,11 @@ def run_server(pp, reqs, arrivals, precision=1, epoch_iters=128):
                 i, _, ta = pending.pop(t)
                 lat[i] = time.perf_counter() - ta
                 status[i] = st
+                infos[i] = info
         time.sleep(0.0005)
     wall = time.perf_counter() - t0
     srv.close()
+    run_server.last_infos = infos
     return lat, wall, status
 
 
@@ -390,7 +394,7 @@ def main():
             res = {"mode": "batch", "fp64": measure_batch(pp, torch, args.batch_count),
                    "fp32_ir": measure_batch(pp, torch, args.batch_count, precision=1)}
         else:
-            res = {"mode": "serve", "serving": measure_serving(pp, nreq=2000, hi=4e6,
+            res = {"mode": "serve", "serving": measure_serving(pp, nreq=400, hi=4e6,
                                                                rate_factors=(0.25, 0.5, 1.0, 2.0, 4.0))}
         if rank == 0:
             print(json.dumps(res), flush=True)

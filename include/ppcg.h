@@ -64,7 +64,9 @@ typedef enum { PPCG_PATH_AUTO = 0, PPCG_PATH_GRID = 1, PPCG_PATH_CLUSTER = 2 } p
 /* Solver options.  Obtain defaults with ppcg_opts_default and override fields. */
 typedef struct {
   int32_t precision;        /* ppcg_precision.  FP32_IR: FP32 matrix values and vectors inside an
-                               FP64 iterative-refinement loop (FP64 outer residual and solution). */
+                               FP64 iterative-refinement loop (FP64 outer residual and solution);
+                               a refinement step that does not halve the FP64 residual is undone
+                               and the solve continues with the FP64 iteration. */
   int32_t format;           /* ppcg_format.  The matrix is always converted to SELL-C-sigma (C = 32)
                                on the device; FMT_CSR forces sigma = 1 (CSR row order kept). */
   int32_t norm;             /* ppcg_norm */
@@ -79,10 +81,12 @@ typedef struct {
   int32_t max_outer;        /* FP32_IR: cap on refinement steps */
   int64_t spin_limit_ns;    /* time limit of one device-side barrier wait (ns); exceeded -> TIMEOUT */
   int32_t cluster_max_rows; /* PATH_AUTO: systems with at most this many rows take the CLUSTER path */
-  int32_t epoch_iters;      /* server: iterations each resident solve advances per epoch */
+  int32_t epoch_iters;      /* server: iterations per epoch of a 131072-row solve; a solve of n rows
+                               advances epoch_iters * 131072 / n (clamped to [2, 64 epoch_iters]) */
   int32_t max_restarts;     /* restarts after a breakdown (alpha denominator <= 0 past the first
                                iteration): true residuals, direction recurrences reset, beta = 0.
-                               0 = report PPCG_ERR_BREAKDOWN instead */
+                               0 = report PPCG_ERR_BREAKDOWN instead.  FP32_IR: per inner solve
+                               (an inner breakdown past the restarts ends that inner solve) */
   int32_t reserved[5];
 } ppcg_opts;
 
@@ -98,10 +102,13 @@ typedef struct {
   double seconds;            /* device time of the solve (globaltimer), setup and final residual included */
   double bytes_per_iter;     /* algorithmic bytes of one iteration: (v+4) nnz + 4 (N+1) + 17 v N */
   double bnorm;              /* ||b||_2 */
+  int32_t fp64_fallback;     /* FP32_IR: 1 when a refinement step failed to halve the FP64 residual and
+                                the solve finished with the FP64 iteration from the previous x */
+  int32_t reserved;
 } ppcg_info;
 
 /* Fill *opts with defaults: FP64, AUTO format/path, REL_R, sigma autotune, rr_period 0,
- * inner_tol 1e-2, inner_maxit 100000, max_outer 30, spin_limit 10 s, cluster_max_rows 16384,
+ * inner_tol 1e-2, inner_maxit 2000, max_outer 100, spin_limit 10 s, cluster_max_rows 16384,
  * epoch_iters 256, max_restarts 8. */
 void ppcg_opts_default(ppcg_opts* opts);
 
@@ -157,7 +164,11 @@ void ppcg_destroy(ppcg_handle handle);
  * device footprint fits in hbm_budget bytes (0 = 90% of free HBM at creation), keeps each
  * admitted request's vectors and scalars resident on the device, and advances all
  * resident requests together in epochs of a bounded number of iterations, so requests
- * that arrive while others run join at the next epoch.  opts may be NULL.
+ * that arrive while others run join at the next epoch.  opts may be NULL.  With
+ * opts->path == PPCG_PATH_AUTO and the default cluster_max_rows, requests of up to 131,072
+ * rows run on the CLUSTER path (all of them share one launch per epoch) and larger ones on
+ * the GRID path (the two oldest advance each epoch by a slice of about 20 ms).  A solve's
+ * result equals ppcg_solve on a handle created with the same options and cluster_max_rows.
  */
 ppcg_status ppcg_server_create(ppcg_server* server, size_t hbm_budget, const ppcg_opts* opts);
 

@@ -57,7 +57,8 @@ class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("outer_iters", ctypes.c_int32),
                 ("rr_count", ctypes.c_int32), ("rel_res_recursive", ctypes.c_double),
                 ("rel_res_true", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("bytes_per_iter", ctypes.c_double), ("bnorm", ctypes.c_double)]
+                ("bytes_per_iter", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("fp64_fallback", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

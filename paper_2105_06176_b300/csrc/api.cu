@@ -22,6 +22,61 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {nullptr};
+std::vector<Stage*> g_stage_free;     // pinned info stages, reused across handles
+}  // namespace
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev >= 0 && dev < 64 && !g_pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      if (cudaMemPoolCreate(&g_pools[dev], &props) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+      } else {
+        cudaGetLastError();
+        g_pools[dev] = nullptr;
+      }
+    }
+    if (dev >= 0 && dev < 64) pool = g_pools[dev];
+  }
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
+}
+
+void pool_free(void* p, cudaStream_t st) {
+  if (p && cudaFreeAsync(p, st) != cudaSuccess) cudaGetLastError();
+}
+
+static Stage* stage_get() {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_stage_free.empty()) {
+    Stage* blk = nullptr;
+    if (cudaMallocHost((void**)&blk, 64 * sizeof(Stage)) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    for (int i = 0; i < 64; i++) g_stage_free.push_back(blk + i);
+  }
+  Stage* s = g_stage_free.back();
+  g_stage_free.pop_back();
+  memset(s, 0, sizeof(Stage));
+  return s;
+}
+
+static void stage_put(Stage* s) {
+  if (!s) return;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  g_stage_free.push_back(s);
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -88,18 +143,16 @@ void CUDART_CB info_callback(void* p) {
 
 template <typename T>
 static bool walloc(ppcg_ctx* h, T** p, size_t count) {
-  if (cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
+  if (pool_alloc((void**)p, std::max<size_t>(count, 1) * sizeof(T), h->stream) != cudaSuccess) return false;
   h->allocs.push_back(*p);
   return true;
 }
 
+// Releases a handle's memory in the order of its last stream (after its last solve).
 static void free_all(ppcg_ctx* h) {
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->allocs) pool_free(p, h->stream);
   h->allocs.clear();
-  if (h->stage) cudaFreeHost(h->stage);
+  stage_put(h->stage);
   h->stage = nullptr;
 }
 
@@ -161,7 +214,7 @@ size_t footprint_bytes(int64_t n, int64_t nnz, int32_t precision) {
   const bool fp32 = precision == PPCG_FP32_IR;
   const double slots = 1.05 * (double)nnz + 32.0 * ((double)n / 32.0 + 1.0);
   double bytes = slots * (fp32 ? 16.0 : 12.0) + (double)n * 8.0 * 6.0;   // matrix + cptr/diag/invd/b/tmp/perm
-  bytes += fp32 ? (double)n * (8.0 * 2 + 4.0 * 12 + 8.0) : (double)n * 8.0 * 10.0;
+  bytes += (double)n * 8.0 * 10.0 + (fp32 ? (double)n * 4.0 * 11.0 : 0.0);
   return (size_t)bytes + (1u << 20);
 }
 
@@ -213,8 +266,8 @@ void ppcg_opts_default(ppcg_opts* o) {
   o->sigma = 0;
   o->rr_period = 0;
   o->inner_tol = 1e-2;
-  o->inner_maxit = 100000;
-  o->max_outer = 30;
+  o->inner_maxit = 2000;
+  o->max_outer = 100;
   o->spin_limit_ns = 10000000000LL;
   o->cluster_max_rows = 16384;
   o->epoch_iters = 256;
@@ -239,8 +292,8 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   if (h->opts.precision != PPCG_FP64 && h->opts.precision != PPCG_FP32_IR) { delete h; set_error("ppcg_create: bad precision"); return PPCG_ERR_ARG; }
   if (h->opts.norm != PPCG_NORM_REL_R && h->opts.norm != PPCG_NORM_PAPER_U_ABS) { delete h; set_error("ppcg_create: bad norm"); return PPCG_ERR_ARG; }
   if (h->opts.spin_limit_ns <= 0) h->opts.spin_limit_ns = 10000000000LL;
-  if (h->opts.inner_maxit <= 0) h->opts.inner_maxit = 100000;
-  if (h->opts.max_outer <= 0) h->opts.max_outer = 30;
+  if (h->opts.inner_maxit <= 0) h->opts.inner_maxit = 2000;
+  if (h->opts.max_outer <= 0) h->opts.max_outer = 100;
   if (!(h->opts.inner_tol > 0.0 && h->opts.inner_tol < 1.0)) h->opts.inner_tol = 1e-2;
   cudaGetDevice(&h->device);
   h->n = n;
@@ -251,14 +304,15 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
 
   // Bring the CSR to the device (temporary copies when it lives on the host).
   std::vector<void*> tmp;
-  auto free_tmp = [&]() { for (void* p : tmp) cudaFree(p); tmp.clear(); };
+  h->stream = stream;
+  auto free_tmp = [&]() { for (void* p : tmp) pool_free(p, stream); tmp.clear(); };
   const int64_t* d_rp = row_ptr;
   const int32_t* d_col = col;
   const double* d_val = val;
   auto upload = [&](const void* src, size_t bytes, const void** dst) -> bool {
     if (is_device_ptr(src)) { *dst = src; return true; }
     void* p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(bytes, 1)) != cudaSuccess) { cudaGetLastError(); return false; }
+    if (pool_alloc(&p, std::max<size_t>(bytes, 1), stream) != cudaSuccess) return false;
     tmp.push_back(p);
     if (cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) { cudaGetLastError(); return false; }
     *dst = p;
@@ -305,32 +359,30 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
 
   // Workspace.
   SysDesc& d = h->desc;
-  // Chunk-interleaved vector blocks.  FP64: r u wa wb z q s p x invd.  FP32_IR: FP64 block
-  // r64 x and FP32 block r u wa wb z q s p d invd rhs.
-  h->ns64 = fp32 ? kSlotsIR : kSlots64;
-  h->xslot = fp32 ? kSlotXIR : kSlotX64;
+  // Chunk-interleaved vector blocks.  FP64: r u wa wb z q s p x invd (also held by FP32_IR:
+  // its outer residual, its solution, and the FP64 iteration it falls back to).  FP32_IR
+  // adds the FP32 block r u wa wb z q s p d invd rhs.
+  h->ns64 = kSlots64;
+  h->xslot = kSlotX64;
   const size_t rows_padded = (size_t)h->A.nchunks * kChunk;
   bool ok = walloc(h, &h->b_ws, n) && walloc(h, &h->tmp, n) &&
             walloc(h, &h->part, 2 * (size_t)h->nparts * 4) && walloc(h, &h->ctl, 1) &&
             walloc(h, &h->bar, 1) && walloc(h, &h->err, 1) && walloc(h, &h->d_desc, 1) &&
-            walloc(h, &d.v64, rows_padded * h->ns64);
+            walloc(h, &d.v64, rows_padded * kSlots64);
   if (ok && fp32) ok = walloc(h, &d.v32, rows_padded * kSlots32);
   if (ok) {
-    if (fp32) {
+    k_to_slot<double><<<blocks_for(n, 256), 256, 0, stream>>>(n, nullptr, h->A.invd, d.v64, kSlots64, kSlotInvd);
+    if (fp32)
       k_to_slot<float><<<blocks_for(n, 256), 256, 0, stream>>>(n, nullptr, h->A.invd32, d.v32, kSlots32, kSlotInvd);
-    } else {
-      k_to_slot<double><<<blocks_for(n, 256), 256, 0, stream>>>(n, nullptr, h->A.invd, d.v64, kSlots64, kSlotInvd);
-    }
     ok = cudaStreamSynchronize(stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
   }
-  if (ok && cudaMallocHost((void**)&h->stage, sizeof(Stage)) != cudaSuccess) { cudaGetLastError(); ok = false; }
+  if (ok && !(h->stage = stage_get())) ok = false;
   if (!ok) {
     free_all(h);
     delete h;
     set_error("ppcg_create: out of device memory for the workspace");
     return PPCG_ERR_OOM;
   }
-  memset(h->stage, 0, sizeof(Stage));
   d.A = h->A;
   d.precision = h->opts.precision;
   d.norm = h->opts.norm;
@@ -360,6 +412,7 @@ ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double*
     return PPCG_ERR_ARG;
   }
   if (h->n == 0) { write_trivial_info(info, PPCG_OK); return PPCG_OK; }
+  h->stream = st;
   ppcg_status s = stage_inputs(h, b, x0, false, st);
   if (s != PPCG_OK) return s;
   prepare_control(h, tol, maxit, st);
@@ -418,6 +471,7 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
     ppcg_ctx* h = hs[i];
     if (h->n == 0) { if (infos) write_trivial_info(&infos[i], PPCG_OK); continue; }
     if (!is_device_ptr(x[i])) { set_error("ppcg_batch_solve: x[%d] must be a device pointer", i); return PPCG_ERR_ARG; }
+    h->stream = st;
     ppcg_status s = stage_inputs(h, b[i], x0 ? x0[i] : nullptr, true, st);
     if (s != PPCG_OK) return s;
     prepare_control(h, tol[i], maxit[i], st);
@@ -533,8 +587,10 @@ ppcg_status ppcg_selftest_barrier_timeout(int32_t grid, int32_t drop_rank, int64
 
 void ppcg_destroy(ppcg_handle h) {
   if (!h) return;
-  cudaDeviceSynchronize();
+  // the handle's work is ordered on its last stream: wait for that stream only
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) cudaGetLastError();
   free_all(h);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) cudaGetLastError();
   delete h;
 }
 

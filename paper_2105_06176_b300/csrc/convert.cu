@@ -101,28 +101,42 @@ __global__ void k_permute_diag(int64_t n, const int32_t* __restrict__ perm,
 }
 
 template <typename T>
-cudaError_t dalloc(T** p, size_t count, std::vector<void*>& allocs) {
-  cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+cudaError_t dalloc(T** p, size_t count, std::vector<void*>& allocs, cudaStream_t st) {
+  cudaError_t e = pool_alloc((void**)p, std::max<size_t>(count, 1) * sizeof(T), st);
   if (e == cudaSuccess) allocs.push_back(*p);
   return e;
 }
 
+// Stable order of the rows of one window by decreasing length: a counting sort over the
+// window's length histogram (row lengths are small for sparse matrices), with a comparison
+// sort as the fallback for windows holding very long rows.
+void sort_window(const std::vector<int32_t>& len, int64_t w0, int64_t w1, int32_t* out,
+                 std::vector<int64_t>& hist) {
+  int32_t mx = 0;
+  for (int64_t i = w0; i < w1; i++) mx = std::max(mx, len[i]);
+  if (mx > 4096) {
+    std::iota(out, out + (w1 - w0), (int32_t)w0);
+    std::stable_sort(out, out + (w1 - w0), [&](int32_t a, int32_t b) { return len[a] > len[b]; });
+    return;
+  }
+  hist.assign(mx + 2, 0);
+  for (int64_t i = w0; i < w1; i++) hist[mx - len[i] + 1]++;          // bucket 0 = longest
+  for (int32_t k = 1; k <= mx + 1; k++) hist[k] += hist[k - 1];        // start offsets
+  for (int64_t i = w0; i < w1; i++) out[hist[mx - len[i]]++] = (int32_t)i;
+}
+
 // Slots of SELL-C-sigma for the given row lengths: rows sorted by decreasing length inside
 // windows of sigma rows (stable), chunks of 32 consecutive sorted rows padded to their
-// longest row.  Returns the slot count; fills perm when asked.
+// longest row.  Returns the slot count; fills perm and cptr when asked.
 int64_t sell_slots(const std::vector<int32_t>& len, int64_t sigma, std::vector<int32_t>* perm,
                    std::vector<int64_t>* cptr) {
   const int64_t n = (int64_t)len.size();
   const int64_t nchunks = (n + kChunk - 1) / kChunk;
   std::vector<int32_t> p;
+  std::vector<int64_t> hist;
   if (sigma > 1) {
     p.resize(n);
-    std::iota(p.begin(), p.end(), 0);
-    for (int64_t w0 = 0; w0 < n; w0 += sigma) {
-      int64_t w1 = std::min(n, w0 + sigma);
-      std::stable_sort(p.begin() + w0, p.begin() + w1,
-                       [&](int32_t a, int32_t b) { return len[a] > len[b]; });
-    }
+    for (int64_t w0 = 0; w0 < n; w0 += sigma) sort_window(len, w0, std::min(n, w0 + sigma), p.data() + w0, hist);
   }
   if (cptr) cptr->assign(nchunks + 1, 0);
   int64_t slots = 0;
@@ -145,12 +159,12 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
                                 DevMatrix* A, int32_t** d_perm_out) {
   auto t0 = std::chrono::steady_clock::now();
   std::vector<void*> tmp;
-  auto free_tmp = [&]() { for (void* p : tmp) cudaFree(p); tmp.clear(); };
+  auto free_tmp = [&]() { for (void* p : tmp) pool_free(p, st); tmp.clear(); };
   double *d_diag0 = nullptr, *d_invd0 = nullptr;
   int32_t *d_len = nullptr, *d_flags = nullptr;
   cudaError_t e = cudaSuccess;
-  if ((e = dalloc(&d_diag0, n, tmp)) || (e = dalloc(&d_invd0, n, tmp)) ||
-      (e = dalloc(&d_len, n, tmp)) || (e = dalloc(&d_flags, 1, tmp))) {
+  if ((e = dalloc(&d_diag0, n, tmp, st)) || (e = dalloc(&d_invd0, n, tmp, st)) ||
+      (e = dalloc(&d_len, n, tmp, st)) || (e = dalloc(&d_flags, 1, tmp, st))) {
     free_tmp();
     set_error("ppcg_create: device allocation failed: %s", cudaGetErrorString(e));
     return PPCG_ERR_OOM;
@@ -189,11 +203,11 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   int64_t* d_cptr = nullptr; int32_t* d_scol = nullptr; double* d_sval = nullptr; float* d_sval32 = nullptr;
   double *d_sdiag = nullptr, *d_sinvd = nullptr; float *d_sdiag32 = nullptr, *d_sinvd32 = nullptr;
   int32_t *d_perm = nullptr, *d_iperm = nullptr;
-  if ((e = dalloc(&d_cptr, nchunks + 1, allocs)) || (e = dalloc(&d_scol, nslots, allocs)) ||
-      (e = dalloc(&d_sval, nslots, allocs)) || (e = dalloc(&d_sdiag, n, allocs)) ||
-      (e = dalloc(&d_sinvd, n, allocs)) ||
-      (want_fp32 && ((e = dalloc(&d_sval32, nslots, allocs)) || (e = dalloc(&d_sdiag32, n, allocs)) ||
-                     (e = dalloc(&d_sinvd32, n, allocs))))) {
+  if ((e = dalloc(&d_cptr, nchunks + 1, allocs, st)) || (e = dalloc(&d_scol, nslots, allocs, st)) ||
+      (e = dalloc(&d_sval, nslots, allocs, st)) || (e = dalloc(&d_sdiag, n, allocs, st)) ||
+      (e = dalloc(&d_sinvd, n, allocs, st)) ||
+      (want_fp32 && ((e = dalloc(&d_sval32, nslots, allocs, st)) || (e = dalloc(&d_sdiag32, n, allocs, st)) ||
+                     (e = dalloc(&d_sinvd32, n, allocs, st))))) {
     free_tmp();
     set_error("ppcg_create: device allocation failed: %s", cudaGetErrorString(e));
     return PPCG_ERR_OOM;
@@ -201,7 +215,7 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   if (!perm.empty()) {
     std::vector<int32_t> iperm(n);
     for (int64_t i = 0; i < n; i++) iperm[perm[i]] = (int32_t)i;
-    if ((e = dalloc(&d_perm, n, allocs)) || (e = dalloc(&d_iperm, n, tmp))) {
+    if ((e = dalloc(&d_perm, n, allocs, st)) || (e = dalloc(&d_iperm, n, tmp, st))) {
       free_tmp();
       set_error("ppcg_create: device allocation failed: %s", cudaGetErrorString(e));
       return PPCG_ERR_OOM;

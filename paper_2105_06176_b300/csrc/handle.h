@@ -40,6 +40,7 @@ inline void fill_info(const Stage& s, const InfoJob& j, ppcg_info* out) {
   r.rel_res_true = c.bnorm > 0 ? c.res_true / c.bnorm : 0.0;
   r.seconds = c.t_end > c.t_start ? (double)(c.t_end - c.t_start) * 1e-9 : 0.0;
   r.bytes_per_iter = j.bytes_per_iter;
+  r.fp64_fallback = c.fallback;
   *out = r;
 }
 
@@ -67,7 +68,8 @@ struct ppcg_ctx {
   int32_t* err = nullptr;
   ppcg::SysDesc* d_desc = nullptr;
   ppcg::SysDesc desc;        // host copy, refreshed per solve
-  ppcg::Stage* stage = nullptr;   // pinned
+  ppcg::Stage* stage = nullptr;   // pinned, from the library's stage pool
+  cudaStream_t stream = nullptr;  // stream of the handle's latest work (creation or solve)
 };
 
 

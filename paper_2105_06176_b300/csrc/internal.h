@@ -9,8 +9,8 @@
 namespace ppcg {
 
 constexpr int kChunk = 32;           // SELL-C-sigma chunk height C: one warp lane per row
-constexpr int kSlots64 = 10, kSlots32 = 11, kSlotsIR = 2;   // slots of the vector blocks
-constexpr int kSlotX64 = 8, kSlotXIR = 1, kSlotInvd = 9;  // x and D^-1 slots
+constexpr int kSlots64 = 10, kSlots32 = 11;   // slots of the vector blocks
+constexpr int kSlotX64 = 8, kSlotInvd = 9;    // x and D^-1 slots
 constexpr int kClusterThreads = 256; // CTA size of the cluster path
 constexpr int kClusterSize = 8;      // CTAs per thread-block cluster (portable maximum)
 
@@ -43,6 +43,7 @@ enum Pass : int32_t {
   P_ORES,      // FP32_IR: r64 = b - A x (FP64) ; partials (r64,r64) (b,b)
   P_OINIT,     // FP32_IR: rhs32 = r64 / ||r64|| ; r32 = rhs32 ; u32 = M^-1 r32 ; d32 = 0
   P_OUPD,      // FP32_IR: x += ||r64|| * d32
+  P_OUNDO,     // FP32_IR: x -= ||r64_prev|| * d32 (undo a refinement step that did not help)
 };
 
 // Control states (see solver.cuh: control()).
@@ -50,7 +51,7 @@ enum State : int32_t {
   S_START = 0, S_AFTER_SETUP1, S_AFTER_SETUP2, S_TOP, S_AFTER_ITER, S_AFTER_TRUE, S_AFTER_RR1,
   S_AFTER_RR2, S_FINAL, S_AFTER_FINAL, S_DONE,
   S_O_START, S_O_AFTER_ORES, S_O_AFTER_ZERO, S_O_AFTER_OINIT, S_I_AFTER_SETUP2, S_I_TOP,
-  S_I_AFTER_ITER, S_I_AFTER_RR1, S_I_AFTER_RR2, S_O_AFTER_OUPD,
+  S_I_AFTER_ITER, S_I_AFTER_RR1, S_I_AFTER_RR2, S_O_AFTER_OUPD, S_O_AFTER_UNDO,
 };
 
 // Device-resident control block of one solve.  Read by every CTA at launch start, written
@@ -59,9 +60,9 @@ struct Ctl {
   int32_t state, pass, status, iter;      // iter: Alg. 2 iterations (inner ones for FP32_IR)
   int32_t inner_iter, outer, rr_count, last_rr_iter;
   int32_t parity, first, exit_now, restart;  // restart: next step starts afresh (beta = 0)
-  int32_t restarts, pad2;
+  int32_t restarts, fallback;   // fallback: FP32_IR switched to the FP64 iteration
   double gamma, gamma_prev, delta, alpha, alpha_prev, beta, norm;
-  double bnorm, rn, rn_prev, res_true, inner_norm0, inner_target;
+  double bnorm, rn, rn_prev, res_true, inner_norm0, inner_target, rr_norm_prev;
   unsigned long long t_start, t_end;
   double red[4];                           // reduced partials of the last pass
 };
@@ -70,13 +71,14 @@ struct SysDesc {
   DevMatrix A;
   int32_t precision, norm, rr_period, maxit;
   int32_t inner_maxit, max_outer, nparts, x_zero;  // x_zero: x starts at 0 (skip the A x0 gather)
-  int32_t max_restarts, pad;
+  int32_t max_restarts, budget;   // budget: iterations this launch may advance (0 = launch's)
   double tol, inner_tol;
   int64_t spin_limit_ns;
   const double* b;       // right-hand side, solver order (plain array)
   // Per-row vectors in chunk-interleaved blocks (for each 32-row chunk, the block's slots
   // of 32 values side by side):
-  //   v64: r u wa wb z q s p x invd (FP64 path); in FP32_IR: r64 x (outer residual, solution)
+  //   v64: r u wa wb z q s p x invd (FP64 path; FP32_IR keeps its FP64 outer residual in r and
+  //        its solution in x, and falls back to the FP64 iteration in this block if needed)
   //   v32: r u wa wb z q s p d invd rhs (FP32_IR inner solve; d is the inner solution)
   double* v64;
   float* v32;
@@ -110,5 +112,10 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
                                 DevMatrix* A, int32_t** d_perm_out);
 
 void set_error(const char* fmt, ...);
+
+// Device memory of handles comes from a library-owned stream-ordered pool per device (no
+// device-wide synchronisation on allocation or release; freed blocks stay in the pool).
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);
+void pool_free(void* p, cudaStream_t st);
 
 }  // namespace ppcg

@@ -153,7 +153,12 @@ bool run_cluster_epoch(ppcg_srv* S, const std::vector<Slot*>& slots) {
   std::vector<double> cost(m);
   for (int k = 0; k < m; k++) {
     descs[k] = slots[k]->h->desc;
-    cost[k] = (double)slots[k]->h->sell.nslots;
+    // Same work per solve and epoch: epoch_iters iterations for a 2^17-row system, more for
+    // smaller ones (at most 64x), fewer for larger ones (at least 2).
+    const double n = (double)std::max<int64_t>(slots[k]->h->n, 1);
+    const double it = std::min(64.0 * S->epoch_iters, std::max(2.0, S->epoch_iters * 131072.0 / n));
+    descs[k].budget = (int32_t)it;
+    cost[k] = (double)slots[k]->h->sell.nslots * it;
   }
   int nclusters = std::min(m, max_active_clusters(S->device));
   std::vector<int> order(m);
@@ -206,9 +211,14 @@ void exec_loop(ppcg_srv* S) {
     std::vector<Slot*> cl, gr;
     for (Slot& s : active) (s.h->path == PPCG_PATH_CLUSTER ? cl : gr).push_back(&s);
     bool ok = run_cluster_epoch(S, cl);
-    for (Slot* s : gr) {
+    // Whole-GPU solves in arrival order: the two oldest each get a slice of about 20 ms of
+    // streaming work (iterations inversely proportional to their size); later ones wait.
+    for (size_t k = 0; k < gr.size() && k < 2; k++) {
+      Slot* s = gr[k];
+      const double n = (double)std::max<int64_t>(s->h->n, 1);
+      const int slice = (int)std::min(4000.0, std::max(32.0, 2.5e8 / n));
       cudaMemsetAsync(s->h->bar, 0, sizeof(unsigned), S->s_exec);
-      ok = ok && launch_grid(s->h->d_desc, s->h->shape, s->h->grid, S->epoch_iters, S->s_exec) == cudaSuccess;
+      ok = ok && launch_grid(s->h->d_desc, s->h->shape, s->h->grid, slice, S->s_exec) == cudaSuccess;
     }
     for (Slot& s : active) {
       cudaMemcpyAsync(&s.h->stage->ctl, s.h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, S->s_exec);
@@ -225,6 +235,7 @@ void exec_loop(ppcg_srv* S) {
       if (sg.ctl.state != S_DONE && sg.err == 0) { keep.push_back(s); continue; }
       Result r;
       r.x.resize(s.h->n);
+      s.h->stream = S->s_exec;
       stage_outputs(s.h, r.x.data(), S->s_exec);
       cudaStreamSynchronize(S->s_exec);
       InfoJob j{s.h->stage, &r.info, s.h->bytes_per_iter, s.h->opts.norm, s.h->opts.precision};
@@ -254,6 +265,9 @@ ppcg_status ppcg_server_create(ppcg_server* server, size_t hbm_budget, const ppc
   ppcg_srv* S = new ppcg_srv();
   ppcg_opts_default(&S->opts);
   if (opts) S->opts = *opts;
+  // Default plan: requests up to 131,072 rows run on thread-block clusters (all of them
+  // advance together inside one launch per epoch); larger ones use the whole GPU.
+  if (S->opts.path == PPCG_PATH_AUTO && (!opts || opts->cluster_max_rows == 16384)) S->opts.cluster_max_rows = 131072;
   if (S->opts.epoch_iters > 0) S->epoch_iters = S->opts.epoch_iters;
   cudaGetDevice(&S->device);
   size_t fr = 0, tot = 0;

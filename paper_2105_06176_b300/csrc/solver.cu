@@ -254,10 +254,10 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* _
 
 // Vector slots.  FP64 block (NS 10): r u wa wb z q s p x invd.  FP32 block (NS 11):
 // r u wa wb z q s p d invd rhs (d: inner solution).  FP32_IR keeps its FP64 outer residual
-// and solution in a 2-slot FP64 block: r64 x.
+// and solution in slots r and x of the FP64 block.
 enum { V_R = 0, V_U, V_WA, V_WB, V_Z, V_Q, V_S, V_P, V_X, V_INVD, V_RHS };
-constexpr int kNS64 = 10, kNS32 = 11, kNSIR = 2;
-constexpr int IR_R = 0, IR_X = 1;
+constexpr int kNS64 = 10, kNS32 = 11;
+constexpr int IR_R = V_R, IR_X = V_X;
 
 struct Lanes {
   int32_t gw, W;   // global warp id within the group, warps in the group (chunk indices < 2^26)
@@ -596,8 +596,8 @@ __device__ __forceinline__ void pass_zero_x(const SysDesc& S, const Lanes& L) {
 // P_ORES (FP32_IR outer step): r64 = b - A x in FP64 ; partials (r64,r64), (b,b).
 __device__ __forceinline__ void pass_ores(const SysDesc& S, const Lanes& L, Dots<double>& d) {
   const DevMatrix& A = S.A;
-  const Blk<double, kNSIR> v{S.v64};
-  const GatherSlot<double, kNSIR> gx{S.v64 + IR_X * kChunk};
+  const Blk<double, kNS64> v{S.v64};
+  const GatherSlot<double, kNS64> gx{S.v64 + IR_X * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
     chunk_slots(A, c, L.lane, base, len);
@@ -618,7 +618,7 @@ __device__ __forceinline__ void pass_ores(const SysDesc& S, const Lanes& L, Dots
 
 // P_OINIT: rhs32 = r64 / ||r64|| ; r32 = rhs32 ; u32 = M^-1 r32 ; d32 = 0.
 __device__ __forceinline__ void pass_oinit(const SysDesc& S, const Lanes& L, double scale) {
-  const Blk<double, kNSIR> v64{S.v64};
+  const Blk<double, kNS64> v64{S.v64};
   const Blk<float, kNS32> v32{S.v32};
   FOR_CHUNKS(S.A, L) {
     const int32_t row = c * kChunk + L.lane;
@@ -633,9 +633,22 @@ __device__ __forceinline__ void pass_oinit(const SysDesc& S, const Lanes& L, dou
   }
 }
 
+// P_OUNDO: x -= ||r64_prev|| * d32, taking back the last refinement step.
+__device__ __forceinline__ void pass_oundo(const SysDesc& S, const Lanes& L, double rn_prev) {
+  const Blk<double, kNS64> v64{S.v64};
+  const Blk<float, kNS32> v32{S.v32};
+  FOR_CHUNKS(S.A, L) {
+    const int32_t row = c * kChunk + L.lane;
+    if (row < S.A.n) {
+      double* px = v64.chunk(c, L.lane) + IR_X * kChunk;
+      *px = fma(-rn_prev, (double)ldcs(v32.chunk(c, L.lane) + V_X * kChunk), *px);
+    }
+  }
+}
+
 // P_OUPD: x += ||r64|| * d32 (FP64 solution accumulation).
 __device__ __forceinline__ void pass_oupd(const SysDesc& S, const Lanes& L, double rn) {
-  const Blk<double, kNSIR> v64{S.v64};
+  const Blk<double, kNS64> v64{S.v64};
   const Blk<float, kNS32> v32{S.v32};
   FOR_CHUNKS(S.A, L) {
     const int32_t row = c * kChunk + L.lane;
@@ -784,6 +797,12 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
         if (c.bnorm == 0.0) { c.status = PPCG_OK; c.pass = P_ZERO_X; c.state = S_O_AFTER_ZERO; return; }
         if (c.rn <= S.tol * c.bnorm) { c.status = PPCG_OK; c.state = S_DONE; c.pass = P_NONE; return; }
         if (!isfinite(c.rn)) { c.status = PPCG_ERR_NONFINITE; c.state = S_DONE; c.pass = P_NONE; return; }
+        if (c.outer > 0 && !(c.rn <= 0.5 * c.rn_prev)) {
+          // The FP32 inner solve did not halve the FP64 residual (kappa * eps32 near 1, or
+          // recurrences that drifted): take the step back and finish with the FP64
+          // iteration from the previous x.
+          c.pass = P_OUNDO; c.state = S_O_AFTER_UNDO; return;
+        }
         if (c.outer >= S.max_outer || c.iter >= S.maxit) {
           c.status = PPCG_ERR_NOT_CONVERGED; c.state = S_DONE; c.pass = P_NONE; return;
         }
@@ -792,36 +811,54 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
       case S_O_AFTER_ZERO:
         c.res_true = 0.0; c.state = S_DONE; c.pass = P_NONE; return;
       case S_O_AFTER_OINIT:
-        c.inner_iter = 0; c.last_rr_iter = -1;
+        c.inner_iter = 0; c.last_rr_iter = -1; c.restart = 0; c.restarts = 0; c.rr_norm_prev = 0.0;
         c.pass = P_SETUP2; c.state = S_I_AFTER_SETUP2; return;
       case S_I_AFTER_SETUP2:
         take_dots(c); c.inner_norm0 = c.norm; c.state = S_I_TOP; break;
       case S_I_AFTER_ITER:
-        c.gamma_prev = c.gamma; c.alpha_prev = c.alpha; c.iter++; c.inner_iter++;
+        c.gamma_prev = c.gamma; c.alpha_prev = c.alpha; c.iter++; c.inner_iter++; c.restart = 0;
         take_dots(c); c.state = S_I_TOP; break;
       case S_I_AFTER_RR2:
-        take_dots(c); c.rr_count++; c.last_rr_iter = c.inner_iter; c.state = S_I_TOP; break;
+        take_dots(c); c.rr_count++; c.last_rr_iter = c.inner_iter;
+        if (!c.restart && !(c.norm <= 4.0 * c.rr_norm_prev)) {
+          // periodic replacement: the true inner residual came out more than 4x the recursive
+          // one it replaced -- the FP32 recurrences have drifted; end this inner solve.
+          c.pass = P_OUPD; c.state = S_O_AFTER_OUPD; return;
+        }
+        c.state = S_I_TOP; break;
       case S_I_AFTER_RR1:
         c.pass = P_RR2; c.state = S_I_AFTER_RR2; return;
       case S_I_TOP: {
         if (c.iter >= iter_end) { c.pass = P_NONE; c.exit_now = 1; return; }
         if (!isfinite(c.gamma) || !isfinite(c.delta) || !isfinite(c.norm)) {
-          c.status = PPCG_ERR_NONFINITE; c.state = S_DONE; c.pass = P_NONE; return;
+          // the FP32 inner solve overflowed: x still holds the last good refinement
+          c.state = S_O_AFTER_UNDO; break;
         }
         if (c.norm <= c.inner_target * c.inner_norm0 || c.inner_iter >= S.inner_maxit || c.iter >= S.maxit) {
           c.pass = P_OUPD; c.state = S_O_AFTER_OUPD; return;
         }
         if (S.rr_period > 0 && c.inner_iter > 0 && c.inner_iter % S.rr_period == 0 &&
             c.last_rr_iter != c.inner_iter) {
+          c.rr_norm_prev = c.norm;   // recursive residual being replaced
           c.pass = P_RR1; c.state = S_I_AFTER_RR1; return;
         }
-        if (!scalars(c, c.inner_iter)) {
+        if (!scalars(c, c.restart ? 0 : c.inner_iter)) {
           if (c.inner_iter == 0) { c.status = PPCG_ERR_BREAKDOWN; c.state = S_DONE; c.pass = P_NONE; return; }
+          if (!c.restart && c.restarts < S.max_restarts) {
+            // restart the inner recurrences from the current correction (as in FP64)
+            c.restarts++; c.restart = 1;
+            c.pass = P_RR1; c.state = S_I_AFTER_RR1; return;
+          }
           c.pass = P_OUPD; c.state = S_O_AFTER_OUPD; return;   // keep the correction so far
         }
-        c.first = (c.inner_iter == 0);
+        c.first = (c.inner_iter == 0 || c.restart);
         c.pass = P_ITER; c.state = S_I_AFTER_ITER; return;
       }
+      case S_O_AFTER_UNDO:
+        // FP64 iteration from x: its first step starts the recurrences afresh (beta = 0)
+        c.fallback = 1; c.restart = 1; c.restarts = 0; c.last_rr_iter = -1;
+        c.status = PPCG_ERR_NOT_CONVERGED;
+        c.state = S_START; break;
       case S_O_AFTER_OUPD:
         c.outer++; c.rn_prev = c.rn;
         c.pass = P_ORES; c.state = S_O_AFTER_ORES; return;
@@ -855,6 +892,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
   __syncthreads();
   const SysDesc& S = sh.S;
   Ctl& C = sh.C;
+  if (S.budget > 0) budget = S.budget;     // per-system epoch budget (server)
   const int iter_end = budget > 0 && C.iter < 0x7fffffff - budget ? C.iter + budget : 0x7fffffff;
   const int nw = blockDim.x >> 5;
   Lanes L;
@@ -876,7 +914,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
       Dots<double> d;
       const View<double, kNS64> V = view64(S);
       switch (pass) {
-        case P_SETUP1: pass_setup1(S, L, d, S.x_zero != 0); break;
+        case P_SETUP1: pass_setup1(S, L, d, S.x_zero != 0 && !C.fallback); break;
         case P_SETUP2: pass_setup2(S.A, V, L, d, paper); break;
         case P_ITER:
           if (STAGED) {
@@ -896,13 +934,14 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
         default: partials = false; break;
       }
       if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
-    } else if (pass == P_ORES || pass == P_ZERO_X || pass == P_OINIT || pass == P_OUPD) {
+    } else if (pass == P_ORES || pass == P_ZERO_X || pass == P_OINIT || pass == P_OUPD || pass == P_OUNDO) {
       Dots<double> d;
       switch (pass) {
         case P_ORES: pass_ores(S, L, d); break;
-        case P_ZERO_X: pass_zero_x<kNSIR, IR_X>(S, L); partials = false; break;
+        case P_ZERO_X: pass_zero_x<kNS64, IR_X>(S, L); partials = false; break;
         case P_OINIT: pass_oinit(S, L, 1.0 / C.rn); partials = false; break;
         case P_OUPD: pass_oupd(S, L, C.rn); partials = false; break;
+        case P_OUNDO: pass_oundo(S, L, C.rn_prev); partials = false; break;
         default: partials = false; break;
       }
       if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
@@ -922,7 +961,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
             else pass_iter<float, kNS32, false>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
           }
           break;
-        case P_RR1: pass_rr1(S.A, V, L, C.inner_iter == 0); partials = false; break;
+        case P_RR1: pass_rr1(S.A, V, L, C.inner_iter == 0 || C.restart); partials = false; break;
         case P_RR2: pass_rr2(S.A, V, L, d, C.inner_iter, paper); break;
         default: partials = false; break;
       }

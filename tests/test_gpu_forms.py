@@ -60,10 +60,25 @@ def test_fp32_ir_reaches_fp64_accuracy(name, path):
     assert info.status == m.OK, info
     t = np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)
     assert t <= 1e-8 and info.rel_res_true <= 1e-8
-    assert info.outer_iters >= 2
+    assert info.outer_iters >= 2 and info.fp64_fallback == 0
     err = rel(x, ref["x"])
     # x error is bounded by cond(A) times the residual gap; both solves sit at <= 1e-8
     assert err <= 1e-4, err
+
+
+def test_fp32_ir_falls_back_to_fp64_when_refinement_stalls():
+    """A 2-D log-normal system with kappa near 1/eps32 (1164^2 rows): FP32 inner solves cannot
+    reduce the FP64 residual, so the refinement step is undone and the solve finishes with
+    the FP64 iteration -- to the same true residual as the plain FP64 solve."""
+    m = pp()
+    a = synth.varcoeff2d(1164, 77)
+    b = dev(synth.rhs_uniform(a.n, 78))
+    s = m.Solver.from_csr(a, precision=m.FP32_IR)
+    x, info = s.solve(b, tol=1e-8, maxit=200000)
+    assert info.status == m.OK, info
+    assert info.fp64_fallback == 1
+    bn = b.cpu().numpy()
+    assert np.linalg.norm(bn - a.to_scipy() @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(bn)
 
 
 # ------------------------------------------------------------------ batched ------------
@@ -158,9 +173,10 @@ def test_server_results_same_alone_and_in_mix(precision):
         assert np.array_equal(x0, x1)
         r = np.linalg.norm(b - a.to_scipy() @ x1) / np.linalg.norm(b)
         assert r <= 1e-8
-    # and the served result equals a solo ppcg_solve with the same settings
+    # and the served result equals a solo ppcg_solve with the same settings (the server's
+    # plan: cluster up to 131,072 rows)
     a, b = systems[0]
-    s = m.Solver.from_csr(a, precision=precision)
+    s = m.Solver.from_csr(a, precision=precision, cluster_max_rows=131072)
     xs, info = s.solve(dev(b), tol=1e-8, maxit=20000)
     assert np.array_equal(xs.cpu().numpy(), alone[0][1])
 
