@@ -60,7 +60,7 @@ def lib():
         _lib.oracle_spmv.restype = None
         _lib.oracle_pipecg.argtypes = [ctypes.c_int64, P, P, P, P, P, P, ctypes.c_double,
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                       ctypes.c_int32, P, P, P, P, ctypes.POINTER(Result)]
+                                       ctypes.c_int32, ctypes.c_int32, P, P, P, P, ctypes.POINTER(Result)]
         _lib.oracle_pipecg.restype = ctypes.c_int
         _lib.oracle_pcg.argtypes = [ctypes.c_int64, P, P, P, P, P, P, ctypes.c_double,
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -90,8 +90,9 @@ def spmv(a, x):
 
 
 def pipecg(a, b, x0=None, tol=1e-8, maxit=10000, norm=NORM_REL_R, rr_period=0, max_restarts=8,
-           sum_mode=0, history=False, state=False):
-    """Algorithm 2 (with restart on breakdown, up to max_restarts times).
+           jacobi_elim=False, sum_mode=0, history=False, state=False):
+    """Algorithm 2 (with restart on breakdown, up to max_restarts times).  jacobi_elim: the
+    variant with q = M^-1 s and u = M^-1 r in place of their recurrences.
     Returns dict(x, result, [alpha, beta, res], [state])."""
     rp, ci, v = _csr_args(a)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -103,7 +104,8 @@ def pipecg(a, b, x0=None, tol=1e-8, maxit=10000, norm=NORM_REL_R, rr_period=0, m
     st = np.empty(10 * a.n) if state else None
     res = Result()
     lib().oracle_pipecg(a.n, _ptr(rp), _ptr(ci), _ptr(v), _ptr(b), _ptr(x0), _ptr(x), tol,
-                        maxit, norm, rr_period, max_restarts, sum_mode, _ptr(ah), _ptr(bh), _ptr(rh),
+                        maxit, norm, rr_period, max_restarts, int(bool(jacobi_elim)), sum_mode, _ptr(ah),
+                        _ptr(bh), _ptr(rh),
                         _ptr(st), ctypes.byref(res))
     out = {"x": x, "result": res.as_dict()}
     if history:

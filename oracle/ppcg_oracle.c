@@ -23,6 +23,9 @@
  *     formed; if it fails, the recurrence vectors are replaced by their true values
  *     (residual replacement, not in the paper) and the iteration continues.
  *   - rr_period > 0 additionally replaces residuals every rr_period iterations.
+ *   - jacobi_elim (a variant, not the paper's literal algorithm): with a diagonal M the
+ *     recurrences of lines 11 and 16 reproduce q = M^-1 s and u = M^-1 r exactly in exact
+ *     arithmetic, so the variant computes q and u from s and r after their updates instead.
  *   - Restart on breakdown (not in the paper): when the alpha denominator is not positive
  *     after the first iteration -- which pipelined PCG meets near its attainable accuracy --
  *     and fewer than max_restarts restarts were made, the residuals are replaced by their
@@ -121,8 +124,8 @@ static double true_residual(int64_t n, const int64_t* rp, const int32_t* ci, con
  */
 int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
                   const double* b, const double* x0, double* x, double tol, int32_t maxit,
-                  int32_t norm_mode, int32_t rr_period, int32_t max_restarts, int32_t sum_mode,
-                  double* alpha_hist, double* beta_hist, double* res_hist,
+                  int32_t norm_mode, int32_t rr_period, int32_t max_restarts, int32_t jacobi_elim,
+                  int32_t sum_mode, double* alpha_hist, double* beta_hist, double* res_hist,
                   double* state_out, oracle_result* res) {
   memset(res, 0, sizeof(*res));
   if (n < 0 || maxit < 0 || !(tol >= 0.0)) { res->status = OR_ERR_ARG; return res->status; }
@@ -240,12 +243,12 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
     /* lines 10-17: z, q, s, p, then x, r, u, w */
     for (int64_t i = 0; i < n; i++) {
       z[i] = nv[i] + beta * z[i];
-      q[i] = m[i] + beta * q[i];
       s[i] = w[i] + beta * s[i];
+      q[i] = jacobi_elim ? s[i] / d[i] : m[i] + beta * q[i];
       p[i] = u[i] + beta * p[i];
       x[i] = x[i] + alpha * p[i];
       r[i] = r[i] - alpha * s[i];
-      u[i] = u[i] - alpha * q[i];
+      u[i] = jacobi_elim ? r[i] / d[i] : u[i] - alpha * q[i];
       w[i] = w[i] - alpha * z[i];
     }
     /* lines 18-20: gamma_{i+1}, delta, norm_{i+1} */

@@ -342,3 +342,32 @@ def test_restart_on_breakdown():
     k = plain["result"]["iters"] - 5
     assert np.array_equal(oracle.pipecg(a, b, tol=0.0, maxit=k, max_restarts=0)["x"],
                           oracle.pipecg(a, b, tol=0.0, maxit=k)["x"])
+
+
+# ---------------------------------------------------------------- Jacobi elimination -----
+
+def test_jacobi_elimination_variant():
+    """The variant that computes q = M^-1 s and u = M^-1 r instead of carrying them: exact
+    termination on k distinct eigenvalues like Alg. 2, the same iterates as Alg. 2 to
+    rounding in early iterations, the invariants u = M^-1 r, q = M^-1 s hold to the last
+    bit, and the full solve converges in the same number of iterations (+-2)."""
+    n = 64
+    eigs = np.repeat(np.array([1.0, 3.0, 7.0, 20.0, 50.0, 100.0]), [11, 11, 11, 11, 10, 10])
+    a, dense = synth.hadamard_spd(n, eigs, seed=11)
+    b = synth.rhs_uniform(n, 12)
+    xs = np.linalg.solve(dense, b)
+    assert rel(oracle.pipecg(a, b, tol=0.0, maxit=5, jacobi_elim=True)["x"], xs) > 1e-2
+    assert rel(oracle.pipecg(a, b, tol=0.0, maxit=6, jacobi_elim=True)["x"], xs) < 1e-11
+    a = synth.varcoeff3d(24, seed=2)
+    b = synth.rhs_uniform(a.n, 3)
+    for k in (5, 20):
+        x1 = oracle.pipecg(a, b, tol=0.0, maxit=k)["x"]
+        x2 = oracle.pipecg(a, b, tol=0.0, maxit=k, jacobi_elim=True)["x"]
+        assert rel(x2, x1) < 1e-11
+    st = oracle.pipecg(a, b, tol=0.0, maxit=20, jacobi_elim=True, state=True)["state"]
+    dinv = 1.0 / a.to_scipy().diagonal()
+    assert np.array_equal(st["u"], st["r"] / (1.0 / dinv)) or rel(st["u"], dinv * st["r"]) < 1e-15
+    f1 = oracle.pipecg(a, b, tol=1e-8, maxit=5000)
+    f2 = oracle.pipecg(a, b, tol=1e-8, maxit=5000, jacobi_elim=True)
+    assert f2["result"]["status"] == oracle.OK
+    assert abs(f1["result"]["iters"] - f2["result"]["iters"]) <= 2
