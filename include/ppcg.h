@@ -60,6 +60,14 @@ typedef enum {
   PPCG_NORM_PAPER_U_ABS = 1 /* sqrt((u, u)) <= tol, the absolute preconditioned norm of Alg. 2 / Sec. VI */
 } ppcg_norm;
 typedef enum { PPCG_PATH_AUTO = 0, PPCG_PATH_GRID = 1, PPCG_PATH_CLUSTER = 2 } ppcg_path;
+typedef enum {
+  PPCG_VARIANT_ALG2 = 0,          /* Alg. 2 as printed: u and q carried by their recurrences */
+  PPCG_VARIANT_JACOBI_SCALED = 1  /* Jacobi elimination: with M = diag(A), u = M^-1 r and q = M^-1 s hold
+                                     exactly, so the solver runs the same iteration on D^-1/2 A D^-1/2
+                                     (u = r, q = s, m = w there): six vectors per row instead of eight,
+                                     no M^-1 stream, fewer FP64 operations; alpha, beta and x are those
+                                     of Alg. 2 up to rounding.  FP64 precision only. */
+} ppcg_variant;
 
 /* Solver options.  Obtain defaults with ppcg_opts_default and override fields. */
 typedef struct {
@@ -87,7 +95,8 @@ typedef struct {
                                iteration): true residuals, direction recurrences reset, beta = 0.
                                0 = report PPCG_ERR_BREAKDOWN instead.  FP32_IR: per inner solve
                                (an inner breakdown past the restarts ends that inner solve) */
-  int32_t reserved[5];
+  int32_t variant;          /* ppcg_variant */
+  int32_t reserved[4];
 } ppcg_opts;
 
 /* Per-solve results.  Filled asynchronously; valid after the solve's stream is synchronised. */

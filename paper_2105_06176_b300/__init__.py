@@ -17,7 +17,7 @@ __all__ = [
     "OK", "PENDING", "ERR_ARG", "ERR_NOT_SPD", "ERR_BREAKDOWN", "ERR_NOT_CONVERGED",
     "ERR_NONFINITE", "ERR_OOM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_BUSY", "ERR_UNKNOWN_TICKET",
     "FP64", "FP32_IR", "NORM_REL_R", "NORM_PAPER_U_ABS", "PATH_AUTO", "PATH_GRID", "PATH_CLUSTER",
-    "FMT_AUTO", "FMT_CSR", "FMT_SELL", "EXPORTED_SYMBOLS",
+    "FMT_AUTO", "FMT_CSR", "FMT_SELL", "VARIANT_ALG2", "VARIANT_JACOBI_SCALED", "EXPORTED_SYMBOLS",
 ]
 
 OK, PENDING, ERR_ARG, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_NOT_CONVERGED = 0, 1, -1, -2, -3, -4
@@ -26,6 +26,7 @@ FP64, FP32_IR = 0, 1
 FMT_AUTO, FMT_CSR, FMT_SELL = 0, 1, 2
 NORM_REL_R, NORM_PAPER_U_ABS = 0, 1
 PATH_AUTO, PATH_GRID, PATH_CLUSTER = 0, 1, 2
+VARIANT_ALG2, VARIANT_JACOBI_SCALED = 0, 1
 
 _NAMES = {OK: "OK", PENDING: "PENDING", ERR_ARG: "ERR_ARG", ERR_NOT_SPD: "ERR_NOT_SPD",
           ERR_BREAKDOWN: "ERR_BREAKDOWN", ERR_NOT_CONVERGED: "ERR_NOT_CONVERGED",
@@ -50,7 +51,8 @@ class Opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64),
                 ("cluster_max_rows", ctypes.c_int32), ("epoch_iters", ctypes.c_int32),
-                ("max_restarts", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("max_restarts", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Info(ctypes.Structure):

@@ -109,6 +109,31 @@ __global__ void k_to_slot(int64_t n, const int32_t* __restrict__ perm, const T* 
   if (i < n) blk[slot_index(i, ns, slot)] = src[perm ? perm[i] : i];
 }
 
+// plain -> block slot divided by the scale slot (x~ = x / sig), optional row permutation
+__global__ void k_to_slot_unscale(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
+                                  double* __restrict__ blk, int ns, int slot, int sig_slot) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) blk[slot_index(i, ns, slot)] = src[perm ? perm[i] : i] / blk[slot_index(i, ns, sig_slot)];
+}
+
+// block slot times the scale slot -> plain (x = sig * x~), optional row permutation
+__global__ void k_from_slot_scale(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ blk,
+                                  int ns, int slot, int sig_slot, double* __restrict__ dst) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[perm ? perm[i] : i] = blk[slot_index(i, ns, slot)] * blk[slot_index(i, ns, sig_slot)];
+}
+
+// d and sig = d^-1/2 slots of the Jacobi-scaled block
+__global__ void k_fill_scale_slots(int64_t n, const double* __restrict__ diag, double* __restrict__ blk, int ns,
+                                   int dslot, int sslot) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double d = diag[i];
+    blk[slot_index(i, ns, dslot)] = d;
+    blk[slot_index(i, ns, sslot)] = 1.0 / sqrt(d);
+  }
+}
+
 __global__ void k_fill_slot(int64_t n, double* __restrict__ blk, int ns, int slot, double v) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) blk[slot_index(i, ns, slot)] = v;
@@ -188,7 +213,10 @@ ppcg_status stage_inputs(ppcg_ctx* h, const double* b, const double* x0, bool re
   } else {
     const double* src = x0;
     if (!x0d) { cudaMemcpyAsync(h->tmp, x0, bytes, cudaMemcpyHostToDevice, st); src = h->tmp; }
-    k_to_slot<double><<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, src, h->desc.v64, h->ns64, h->xslot);
+    if (h->opts.variant == PPCG_VARIANT_JACOBI_SCALED)
+      k_to_slot_unscale<<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, src, h->desc.v64, h->ns64, h->xslot, kSlotSigS);
+    else
+      k_to_slot<double><<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, src, h->desc.v64, h->ns64, h->xslot);
   }
   h->desc.b = bsol;
   h->desc.x_zero = x_zero;
@@ -198,7 +226,11 @@ ppcg_status stage_inputs(ppcg_ctx* h, const double* b, const double* x0, bool re
 void stage_outputs(ppcg_ctx* h, double* x, cudaStream_t st) {
   const int64_t n = h->n;
   const bool xd = is_device_ptr(x);
-  k_from_slot<<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, h->desc.v64, h->ns64, h->xslot, xd ? x : h->tmp);
+  if (h->opts.variant == PPCG_VARIANT_JACOBI_SCALED)
+    k_from_slot_scale<<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, h->desc.v64, h->ns64, h->xslot, kSlotSigS,
+                                                          xd ? x : h->tmp);
+  else
+    k_from_slot<<<blocks_for(n, 256), 256, 0, st>>>(n, h->perm, h->desc.v64, h->ns64, h->xslot, xd ? x : h->tmp);
   if (!xd) cudaMemcpyAsync(x, h->tmp, n * sizeof(double), cudaMemcpyDeviceToHost, st);
 }
 
@@ -291,6 +323,12 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   if (opts) h->opts = *opts;
   if (h->opts.precision != PPCG_FP64 && h->opts.precision != PPCG_FP32_IR) { delete h; set_error("ppcg_create: bad precision"); return PPCG_ERR_ARG; }
   if (h->opts.norm != PPCG_NORM_REL_R && h->opts.norm != PPCG_NORM_PAPER_U_ABS) { delete h; set_error("ppcg_create: bad norm"); return PPCG_ERR_ARG; }
+  if (h->opts.variant != PPCG_VARIANT_ALG2 && h->opts.variant != PPCG_VARIANT_JACOBI_SCALED) {
+    delete h; set_error("ppcg_create: bad variant"); return PPCG_ERR_ARG;
+  }
+  if (h->opts.variant == PPCG_VARIANT_JACOBI_SCALED && h->opts.precision != PPCG_FP64) {
+    delete h; set_error("ppcg_create: the Jacobi-scaled variant is FP64 only"); return PPCG_ERR_ARG;
+  }
   if (h->opts.spin_limit_ns <= 0) h->opts.spin_limit_ns = 10000000000LL;
   if (h->opts.inner_maxit <= 0) h->opts.inner_maxit = 2000;
   if (h->opts.max_outer <= 0) h->opts.max_outer = 100;
@@ -328,7 +366,8 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   }
   int32_t sigma = h->opts.format == PPCG_FMT_CSR ? 1 : h->opts.sigma;
   ppcg_status s = convert_csr_to_sell(n, nnz, d_rp, d_col, d_val, sigma, h->opts.precision == PPCG_FP32_IR,
-                                      stream, h->allocs, &h->sell, &h->A, &h->perm);
+                                      h->opts.variant == PPCG_VARIANT_JACOBI_SCALED, stream, h->allocs, &h->sell,
+                                      &h->A, &h->perm);
   free_tmp();
   if (s != PPCG_OK) { free_all(h); delete h; return s; }
 
@@ -356,22 +395,28 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   const bool fp32 = h->opts.precision == PPCG_FP32_IR;
   const double v = fp32 ? 4.0 : 8.0;
   h->bytes_per_iter = (v + 4.0) * (double)nnz + 4.0 * (double)(n + 1) + 17.0 * v * (double)n;
+  if (h->opts.variant == PPCG_VARIANT_JACOBI_SCALED)   // off-diagonals, 13 vector streams
+    h->bytes_per_iter = (v + 4.0) * (double)(nnz - n) + 4.0 * (double)(n + 1) + 13.0 * v * (double)n;
 
   // Workspace.
   SysDesc& d = h->desc;
   // Chunk-interleaved vector blocks.  FP64: r u wa wb z q s p x invd (also held by FP32_IR:
   // its outer residual, its solution, and the FP64 iteration it falls back to).  FP32_IR
   // adds the FP32 block r u wa wb z q s p d invd rhs.
-  h->ns64 = kSlots64;
-  h->xslot = kSlotX64;
+  const bool scaled = h->opts.variant == PPCG_VARIANT_JACOBI_SCALED;
+  h->ns64 = scaled ? kSlotsS : kSlots64;
+  h->xslot = scaled ? kSlotXS : kSlotX64;
   const size_t rows_padded = (size_t)h->A.nchunks * kChunk;
   bool ok = walloc(h, &h->b_ws, n) && walloc(h, &h->tmp, n) &&
             walloc(h, &h->part, 2 * (size_t)h->nparts * 4) && walloc(h, &h->ctl, 1) &&
             walloc(h, &h->bar, 1) && walloc(h, &h->err, 1) && walloc(h, &h->d_desc, 1) &&
-            walloc(h, &d.v64, rows_padded * kSlots64);
+            walloc(h, &d.v64, rows_padded * h->ns64);
   if (ok && fp32) ok = walloc(h, &d.v32, rows_padded * kSlots32);
   if (ok) {
-    k_to_slot<double><<<blocks_for(n, 256), 256, 0, stream>>>(n, nullptr, h->A.invd, d.v64, kSlots64, kSlotInvd);
+    if (scaled)
+      k_fill_scale_slots<<<blocks_for(n, 256), 256, 0, stream>>>(n, h->A.diag, d.v64, kSlotsS, kSlotDS, kSlotSigS);
+    else
+      k_to_slot<double><<<blocks_for(n, 256), 256, 0, stream>>>(n, nullptr, h->A.invd, d.v64, kSlots64, kSlotInvd);
     if (fp32)
       k_to_slot<float><<<blocks_for(n, 256), 256, 0, stream>>>(n, nullptr, h->A.invd32, d.v32, kSlots32, kSlotInvd);
     ok = cudaStreamSynchronize(stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
@@ -392,6 +437,7 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   d.inner_maxit = h->opts.inner_maxit;
   d.max_outer = h->opts.max_outer;
   d.max_restarts = h->opts.max_restarts < 0 ? 0 : h->opts.max_restarts;
+  d.variant = h->opts.variant;
   d.inner_tol = h->opts.inner_tol;
   d.spin_limit_ns = h->opts.spin_limit_ns;
   d.nparts = h->nparts;

@@ -1,7 +1,8 @@
 // CSR -> SELL-C-sigma conversion with the Jacobi diagonal (Sec. V-A: CSR input, Jacobi
 // preconditioner M = diag(A)).  Runs once per handle inside ppcg_create.
 //
-// The solver keeps the matrix column-scaled, Ahat = A D^-1, so that the preconditioner
+// The solver keeps the matrix column-scaled, Ahat = A D^-1 (or, for the Jacobi-scaled
+// variant, symmetrically scaled, D^-1/2 A D^-1/2, with the same unit diagonal), so that the preconditioner
 // apply and the SpMV of Alg. 2 lines 21-22 (m = M^-1 w; n = A m) become one product
 // n = Ahat w with no per-iteration multiply by D^-1 inside the gather.  The scaling divides
 // (a_ij / a_jj), so every diagonal entry of Ahat is exactly 1.0: the SELL arrays hold the
@@ -56,7 +57,7 @@ __global__ void k_fill(int64_t n, int64_t nchunks, const int64_t* __restrict__ r
                        const double* __restrict__ diag, const int32_t* __restrict__ rowlen,
                        const int32_t* __restrict__ perm, const int32_t* __restrict__ iperm,
                        const int64_t* __restrict__ cptr, int32_t* __restrict__ scol,
-                       double* __restrict__ sval, float* __restrict__ sval32) {
+                       double* __restrict__ sval, float* __restrict__ sval32, int sym) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t c = t / kChunk;
   int lane = (int)(t % kChunk);
@@ -72,7 +73,8 @@ __global__ void k_fill(int64_t n, int64_t nchunks, const int64_t* __restrict__ r
     int32_t oc = col[k];
     if (oc == o) continue;                       // diagonal: implicit, exactly 1 after scaling
     int64_t slot = base + (int64_t)j * kChunk + lane;
-    double v = val[k] / diag[oc];
+    // A D^-1 (column scaling), or D^-1/2 A D^-1/2 for the symmetrically scaled variant
+    double v = sym ? val[k] / (sqrt(diag[o]) * sqrt(diag[oc])) : val[k] / diag[oc];
     scol[slot] = iperm ? iperm[oc] : oc;
     sval[slot] = v;
     if (sval32) sval32[slot] = (float)v;
@@ -154,7 +156,7 @@ int64_t sell_slots(const std::vector<int32_t>& len, int64_t sigma, std::vector<i
 }  // namespace
 
 ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col,
-                                const double* d_val, int32_t sigma_req, bool want_fp32,
+                                const double* d_val, int32_t sigma_req, bool want_fp32, bool sym_scale,
                                 cudaStream_t st, std::vector<void*>& allocs, SellBuild* out,
                                 DevMatrix* A, int32_t** d_perm_out) {
   auto t0 = std::chrono::steady_clock::now();
@@ -227,7 +229,7 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
     int64_t threads = nchunks * kChunk;
     k_fill<<<(unsigned)((threads + tb - 1) / tb), tb, 0, st>>>(n, nchunks, d_rp, d_col, d_val, d_diag0,
                                                                d_len, d_perm, d_iperm, d_cptr, d_scol,
-                                                               d_sval, d_sval32);
+                                                               d_sval, d_sval32, sym_scale ? 1 : 0);
     k_permute_diag<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(n, d_perm, d_diag0, d_invd0, d_sdiag,
                                                                  d_sinvd, d_sdiag32, d_sinvd32);
     e = cudaStreamSynchronize(st);
@@ -236,7 +238,7 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
     int64_t threads = nchunks * kChunk;
     k_fill<<<(unsigned)((threads + tb - 1) / tb), tb, 0, st>>>(n, nchunks, d_rp, d_col, d_val, d_diag0,
                                                                d_len, nullptr, nullptr, d_cptr, d_scol,
-                                                               d_sval, d_sval32);
+                                                               d_sval, d_sval32, sym_scale ? 1 : 0);
     k_permute_diag<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(n, nullptr, d_diag0, d_invd0, d_sdiag,
                                                                  d_sinvd, d_sdiag32, d_sinvd32);
     e = cudaStreamSynchronize(st);

@@ -11,6 +11,8 @@ namespace ppcg {
 constexpr int kChunk = 32;           // SELL-C-sigma chunk height C: one warp lane per row
 constexpr int kSlots64 = 10, kSlots32 = 11;   // slots of the vector blocks
 constexpr int kSlotX64 = 8, kSlotInvd = 9;    // x and D^-1 slots
+// Jacobi-scaled variant, FP64 block: r wa wb z s p x d sig (sig = a_ii^-1/2)
+constexpr int kSlotsS = 9, kSlotXS = 6, kSlotDS = 7, kSlotSigS = 8;
 constexpr int kClusterThreads = 256; // CTA size of the cluster path
 constexpr int kClusterSize = 8;      // CTAs per thread-block cluster (portable maximum)
 
@@ -72,6 +74,7 @@ struct SysDesc {
   int32_t precision, norm, rr_period, maxit;
   int32_t inner_maxit, max_outer, nparts, x_zero;  // x_zero: x starts at 0 (skip the A x0 gather)
   int32_t max_restarts, budget;   // budget: iterations this launch may advance (0 = launch's)
+  int32_t variant, pad3;          // ppcg_variant
   double tol, inner_tol;
   int64_t spin_limit_ns;
   const double* b;       // right-hand side, solver order (plain array)
@@ -107,7 +110,7 @@ struct SellBuild {
   double seconds = 0.0;   // conversion wall time
 };
 ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col,
-                                const double* d_val, int32_t sigma_req, bool want_fp32,
+                                const double* d_val, int32_t sigma_req, bool want_fp32, bool sym_scale,
                                 cudaStream_t st, std::vector<void*>& allocs, SellBuild* out,
                                 DevMatrix* A, int32_t** d_perm_out);
 

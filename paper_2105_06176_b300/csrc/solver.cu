@@ -583,6 +583,207 @@ __device__ __forceinline__ void pass_rr2(const DevMatrix& A, const View<T, NS>& 
   }
 }
 
+// ------------------------------------------ Jacobi-scaled variant (Jacobi elimination) --
+// With M = D = diag(A), u = D^-1 r and q = D^-1 s hold exactly, and Alg. 2 is the
+// unpreconditioned pipelined iteration on A~ = D^-1/2 A D^-1/2 in the variables
+// x~ = D^1/2 x, r~ = D^-1/2 r (= D^1/2 u), w~ = D^-1/2 w, ... where u = r, q = s, m = w:
+// gamma = (r~, r~), delta = (w~, r~) are Alg. 2's gamma and delta, and the stopping norm
+// ||r||^2 = sum d_i r~_i^2.  FP64 block: r wa wb z s p x d sig (sig = d^-1/2).
+enum { VS_R = 0, VS_WA, VS_WB, VS_Z, VS_S, VS_P, VS_X, VS_D, VS_SIG };
+constexpr int kNSS = 9;
+
+__device__ __forceinline__ double scaled_norm_term(bool paper, double ri, double di, double sg) {
+  return paper ? (sg * ri) * (sg * ri) : (di * ri) * ri;
+}
+
+// P_SETUP1: r~ = sig b - A~ x~ ; partial (b, b).
+__device__ __forceinline__ void spass_setup1(const SysDesc& S, const Lanes& L, Dots<double>& d, bool x_zero) {
+  const DevMatrix& A = S.A;
+  const Blk<double, kNSS> v{S.v64};
+  const GatherSlot<double, kNSS> gx{S.v64 + VS_X * kChunk};
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
+    const bool in = row < A.n;
+    double* pc = v.chunk(c, L.lane);
+    double ax = 0.0, bi = 0.0, sg = 0.0;
+    if (in) {
+      bi = __ldg(S.b + row);
+      sg = ldcs(pc + VS_SIG * kChunk);
+      if (!x_zero) ax = ldcg(pc + VS_X * kChunk);
+    }
+    if (!x_zero) ax = row_dot<double, false>(A.col, A.val, gx, nullptr, base, len, ax);
+    if (in) {
+      stcs(pc + VS_R * kChunk, fma(sg, bi, -ax));
+      d.add(0, bi, bi);
+    }
+  }
+}
+
+// P_SETUP2: w~ = A~ r~ ; partials gamma = (r~, r~), delta = (w~, r~), stopping norm.
+__device__ __forceinline__ void spass_setup2(const SysDesc& S, const Lanes& L, Dots<double>& d, bool paper) {
+  const DevMatrix& A = S.A;
+  const Blk<double, kNSS> v{S.v64};
+  const GatherSlot<double, kNSS> gr{S.v64 + VS_R * kChunk};
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
+    const bool in = row < A.n;
+    double* pc = v.chunk(c, L.lane);
+    double ri = 0.0, di = 0.0, sg = 0.0;
+    if (in) {
+      ri = ldcg(pc + VS_R * kChunk);
+      if (paper) sg = ldcs(pc + VS_SIG * kChunk); else di = ldcs(pc + VS_D * kChunk);
+    }
+    const double wi = row_dot<double, false>(A.col, A.val, gr, nullptr, base, len, ri);
+    if (in) {
+      stcs(pc + VS_WA * kChunk, wi);
+      d.add(0, ri, ri);
+      d.add(1, wi, ri);
+      d.a[2] += scaled_norm_term(paper, ri, di, sg);
+    }
+  }
+}
+
+// P_ITER (scaled): n~ = A~ w~ ; z = n + beta z ; s = w + beta s ; p = r + beta p ;
+// x += alpha p ; r -= alpha s ; w -= alpha z ; partials.
+template <bool FIRST>
+__device__ __forceinline__ void spass_iter(const SysDesc& S, const Lanes& L, Dots<double>& d, double alpha,
+                                           double beta, int k, bool paper) {
+  const DevMatrix& A = S.A;
+  const Blk<double, kNSS> v{S.v64};
+  const int wcs = (k & 1) ? VS_WB : VS_WA;
+  const int wns = (k & 1) ? VS_WA : VS_WB;
+  const GatherSlot<double, kNSS> gw{S.v64 + wcs * kChunk};
+  const int32_t* __restrict__ col = A.col;
+  const double* __restrict__ val = A.val;
+  const int32_t n = (int32_t)A.n;
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
+    const bool in = row < n;
+    double* pc = v.chunk(c, L.lane);
+    double wi = 0.0, ri = 0.0, xi = 0.0, zo = 0.0, so = 0.0, po = 0.0, di = 0.0, sg = 0.0;
+    if (in) {
+      wi = ldcg(pc + wcs * kChunk);
+      ri = ldcs(pc + VS_R * kChunk);
+      xi = ldcs(pc + VS_X * kChunk);
+      if (paper) sg = ldcs(pc + VS_SIG * kChunk); else di = ldcs(pc + VS_D * kChunk);
+      if (!FIRST) {
+        zo = ldcs(pc + VS_Z * kChunk);
+        so = ldcs(pc + VS_S * kChunk);
+        po = ldcs(pc + VS_P * kChunk);
+      }
+    }
+    const double ni = row_dot<double, false>(col, val, gw, nullptr, base, len, wi);
+    if (in) {
+      const double zi = FIRST ? ni : fma(beta, zo, ni);
+      const double si = FIRST ? wi : fma(beta, so, wi);
+      const double pi = FIRST ? ri : fma(beta, po, ri);
+      xi = fma(alpha, pi, xi);
+      const double rn = fma(-alpha, si, ri);
+      const double wn = fma(-alpha, zi, wi);
+      stcs(pc + VS_Z * kChunk, zi);
+      stcs(pc + VS_S * kChunk, si);
+      stcs(pc + VS_P * kChunk, pi);
+      stcs(pc + VS_X * kChunk, xi);
+      stcs(pc + VS_R * kChunk, rn);
+      stcs(pc + wns * kChunk, wn);
+      d.add(0, rn, rn);
+      d.add(1, wn, rn);
+      d.a[2] += scaled_norm_term(paper, rn, di, sg);
+    }
+  }
+}
+
+// P_TRUE (scaled): ||b - A x||^2 = sum d (sig b - A~ x~)^2.
+__device__ __forceinline__ void spass_true(const SysDesc& S, const Lanes& L, Dots<double>& d) {
+  const DevMatrix& A = S.A;
+  const Blk<double, kNSS> v{S.v64};
+  const GatherSlot<double, kNSS> gx{S.v64 + VS_X * kChunk};
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
+    const bool in = row < A.n;
+    double* pc = v.chunk(c, L.lane);
+    double ax = 0.0, bi = 0.0, sg = 0.0, di = 0.0;
+    if (in) {
+      bi = __ldg(S.b + row);
+      sg = ldcs(pc + VS_SIG * kChunk);
+      di = ldcs(pc + VS_D * kChunk);
+      ax = ldcg(pc + VS_X * kChunk);
+    }
+    ax = row_dot<double, false>(A.col, A.val, gx, nullptr, base, len, ax);
+    if (in) {
+      const double t = fma(sg, bi, -ax);
+      d.add(0, di * t, t);
+    }
+  }
+}
+
+// P_RR1 (scaled): r~ = sig b - A~ x~ ; s~ = A~ p~ (0 at a restart or at iteration 0).
+__device__ __forceinline__ void spass_rr1(const SysDesc& S, const Lanes& L, bool p_zero) {
+  const DevMatrix& A = S.A;
+  const Blk<double, kNSS> v{S.v64};
+  const GatherSlot<double, kNSS> gx{S.v64 + VS_X * kChunk};
+  const GatherSlot<double, kNSS> gp{S.v64 + VS_P * kChunk};
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
+    const bool in = row < A.n;
+    double* pc = v.chunk(c, L.lane);
+    double ax = 0.0, ap = 0.0, bi = 0.0, sg = 0.0;
+    if (in) {
+      bi = __ldg(S.b + row);
+      sg = ldcs(pc + VS_SIG * kChunk);
+      ax = ldcg(pc + VS_X * kChunk);
+      if (!p_zero) ap = ldcg(pc + VS_P * kChunk);
+    }
+    ax = row_dot<double, false>(A.col, A.val, gx, nullptr, base, len, ax);
+    if (!p_zero) ap = row_dot<double, false>(A.col, A.val, gp, nullptr, base, len, ap);
+    if (in) {
+      stcs(pc + VS_R * kChunk, fma(sg, bi, -ax));
+      stcs(pc + VS_S * kChunk, ap);
+    }
+  }
+}
+
+// P_RR2 (scaled): w~ = A~ r~ ; z~ = A~ s~ ; partials.
+__device__ __forceinline__ void spass_rr2(const SysDesc& S, const Lanes& L, Dots<double>& d, int k, bool paper) {
+  const DevMatrix& A = S.A;
+  const Blk<double, kNSS> v{S.v64};
+  const int wcs = (k & 1) ? VS_WB : VS_WA;
+  const GatherSlot<double, kNSS> gr{S.v64 + VS_R * kChunk};
+  const GatherSlot<double, kNSS> gs{S.v64 + VS_S * kChunk};
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
+    const bool in = row < A.n;
+    double* pc = v.chunk(c, L.lane);
+    double ri = 0.0, si = 0.0, di = 0.0, sg = 0.0;
+    if (in) {
+      ri = ldcg(pc + VS_R * kChunk);
+      si = ldcg(pc + VS_S * kChunk);
+      if (paper) sg = ldcs(pc + VS_SIG * kChunk); else di = ldcs(pc + VS_D * kChunk);
+    }
+    const double wi = row_dot<double, false>(A.col, A.val, gr, nullptr, base, len, ri);
+    const double zi = row_dot<double, false>(A.col, A.val, gs, nullptr, base, len, si);
+    if (in) {
+      stcs(pc + wcs * kChunk, wi);
+      stcs(pc + VS_Z * kChunk, zi);
+      d.add(0, ri, ri);
+      d.add(1, wi, ri);
+      d.a[2] += scaled_norm_term(paper, ri, di, sg);
+    }
+  }
+}
+
 // P_ZERO_X: x = 0 (slot XS of an NS-slot FP64 block).
 template <int NS, int XS>
 __device__ __forceinline__ void pass_zero_x(const SysDesc& S, const Lanes& L) {
@@ -910,7 +1111,23 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
     const bool fp32 = S.precision == PPCG_FP32_IR && (C.state >= S_O_START);
     double* slot = S.part + ((size_t)C.parity * P + g.rank()) * 4;
     bool partials = true;
-    if (!fp32) {
+    if (!fp32 && S.variant == PPCG_VARIANT_JACOBI_SCALED) {
+      Dots<double> d;
+      switch (pass) {
+        case P_SETUP1: spass_setup1(S, L, d, S.x_zero != 0); break;
+        case P_SETUP2: spass_setup2(S, L, d, paper); break;
+        case P_ITER:
+          if (C.first) spass_iter<true>(S, L, d, C.alpha, C.beta, C.iter, paper);
+          else spass_iter<false>(S, L, d, C.alpha, C.beta, C.iter, paper);
+          break;
+        case P_TRUE: spass_true(S, L, d); break;
+        case P_RR1: spass_rr1(S, L, C.iter == 0 || C.restart); partials = false; break;
+        case P_RR2: spass_rr2(S, L, d, C.iter, paper); break;
+        case P_ZERO_X: pass_zero_x<kNSS, VS_X>(S, L); partials = false; break;
+        default: partials = false; break;
+      }
+      if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
+    } else if (!fp32) {
       Dots<double> d;
       const View<double, kNS64> V = view64(S);
       switch (pass) {

@@ -214,3 +214,49 @@ def test_restart_on_breakdown_parity():
         assert info.rr_count >= 1 and ref["result"]["rr_count"] >= 1
         assert abs(info.iters - ref["result"]["iters"]) <= 0.1 * ref["result"]["iters"]
         assert np.linalg.norm(b - a.to_scipy() @ x) <= 1e-8 * np.linalg.norm(b)
+
+
+# ----------------------------------------------------- Jacobi-scaled variant (next row f1) --
+
+SCALED = dict(variant=1)
+
+
+@pytest.mark.parametrize("name,k", [("poisson2d_64", 50), ("varcoeff3d_31", 20), ("rgg_20k", 20)])
+@pytest.mark.parametrize("path", [1, 2], ids=["grid", "cluster"])
+def test_scaled_variant_fixed_k_parity(name, k, path):
+    """The Jacobi-scaled variant against the oracle's Jacobi-elimination mode (its own
+    definition) and against Alg. 2 itself, both to 1e-10 at the calibrated k."""
+    a, b = problem(name)
+    x, info = gpu(a, b, tol=0.0, maxit=k, path=path, **SCALED)
+    assert info.iters == k
+    assert rel(x, oracle.pipecg(a, b, tol=0.0, maxit=k, jacobi_elim=True)["x"]) <= 1e-10
+    assert rel(x, oracle.pipecg(a, b, tol=0.0, maxit=k)["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["poisson2d_64", "varcoeff3d_31", "rgg_20k"])
+def test_scaled_variant_full_solve(name):
+    a, b = problem(name)
+    ref = oracle.pipecg(a, b, tol=1e-8, maxit=20000, jacobi_elim=True)
+    for path in (1, 2):
+        x, info = gpu(a, b, tol=1e-8, maxit=20000, path=path, **SCALED)
+        assert info.status == pp().OK
+        assert abs(info.iters - ref["result"]["iters"]) <= 2
+        t = np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)
+        assert t <= 1e-8 and info.rel_res_true == pytest.approx(t, rel=1e-6, abs=1e-14)
+
+
+def test_scaled_variant_modes():
+    """Non-zero x0, periodic residual replacement and the paper's norm in the variant."""
+    a, b = problem("varcoeff2d_150")
+    x0 = synth.xtrue_uniform(a.n, 9)
+    ref = oracle.pipecg(a, b, x0=x0, tol=0.0, maxit=40, rr_period=15, jacobi_elim=True)
+    x, info = gpu(a, b, x0=x0, tol=0.0, maxit=40, rr_period=15, path=1, **SCALED)
+    assert info.rr_count == ref["result"]["rr_count"]
+    assert rel(x, ref["x"]) <= 1e-10
+    a2 = synth.varcoeff2d(64, seed=3)
+    b2 = a2.to_scipy() @ np.full(a2.n, 1.0 / np.sqrt(a2.n))
+    r2 = oracle.pipecg(a2, b2, tol=1e-5, maxit=10000, norm=oracle.NORM_PAPER_U_ABS, jacobi_elim=True)
+    x2, i2 = gpu(a2, b2, tol=1e-5, maxit=10000, norm=pp().NORM_PAPER_U_ABS, **SCALED)
+    assert i2.status == pp().OK and abs(i2.iters - r2["result"]["iters"]) <= 2
+    with pytest.raises(pp().PPCGError):
+        pp().Solver.from_csr(a, precision=pp().FP32_IR, **SCALED)
