@@ -521,6 +521,26 @@ def main():
                                  "fp32_bytes_per_iter": b_alg(n, nnz, 4)}
         sm.close()
 
+    if not args.no_mixed:
+        # the Jacobi-scaled form of the same iteration (u = r, q = s; 13 streams per row)
+        sv = pp.Solver.from_csr(a, variant=pp.VARIANT_JACOBI_SCALED)
+        xv = torch.empty(n, dtype=torch.float64, device="cuda")
+        sv.solve(b_d, None, xv, tol=TOL, maxit=MAXIT)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, iv = sv.solve(b_d, None, xv, tol=TOL, maxit=MAXIT, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_var = e0.elapsed_time(e1) * 1e-3
+        err = (torch.linalg.norm(xv - x_d) / torch.linalg.norm(x_d)).item()
+        line["jacobi_scaled_vs_alg2"] = {"alg2_s": per_launch_s, "scaled_s": t_var,
+                                         "speedup": per_launch_s / t_var, "iters": iv.iters,
+                                         "alg2_iters": iters_per_solve,
+                                         "status": pp.status_name(iv.status),
+                                         "rel_res_true": iv.rel_res_true, "err_vs_alg2_solution": err,
+                                         "scaled_bytes_per_iter": iv.bytes_per_iter}
+        sv.close()
+
     if not args.no_extras:
         line["latency_2d64"] = measure_latency_2d(pp, torch)
         line["batch"] = measure_batch(pp, torch, 128)

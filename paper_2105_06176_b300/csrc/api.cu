@@ -439,6 +439,8 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   d.max_restarts = h->opts.max_restarts < 0 ? 0 : h->opts.max_restarts;
   d.variant = h->opts.variant;
   d.inner_tol = h->opts.inner_tol;
+  d.dmin = h->sell.dmin;
+  d.dmax = h->sell.dmax;
   d.spin_limit_ns = h->opts.spin_limit_ns;
   d.nparts = h->nparts;
   d.part = h->part;

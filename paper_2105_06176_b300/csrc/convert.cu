@@ -10,6 +10,7 @@
 // A v) exactly, as the first term of each row sum.
 #include <algorithm>
 #include <chrono>
+#include <cstring>
 #include <numeric>
 #include <vector>
 
@@ -21,33 +22,43 @@ namespace {
 
 enum : int32_t { F_ARG = 1, F_NOT_SPD = 2 };
 
-// One thread per row: validate the row, extract the diagonal, record the row length.
+// One thread per row: validate the row, extract the diagonal, record the row length; also
+// the extreme diagonal entries (for positive doubles the order of the bit patterns is the
+// numeric order, so integer min / max serve; one atomic pair per warp).
 __global__ void k_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                        const int32_t* __restrict__ col, const double* __restrict__ val,
                        double* __restrict__ diag, double* __restrict__ invd,
-                       int32_t* __restrict__ rowlen, int32_t* flags) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int64_t a = rp[i], e = rp[i + 1];
-  int32_t f = 0;
-  if (a < 0 || e < a || e > nnz || (i == 0 && a != 0) || (i == n - 1 && e != nnz)) {
-    f |= F_ARG;
-    e = a;
+                       int32_t* __restrict__ rowlen, int32_t* flags, unsigned long long* dminmax) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned long long lo = ~0ull, hi = 0ull;
+  if (i < n) {
+    int64_t a = rp[i], e = rp[i + 1];
+    int32_t f = 0;
+    if (a < 0 || e < a || e > nnz || (i == 0 && a != 0) || (i == n - 1 && e != nnz)) {
+      f |= F_ARG;
+      e = a;
+    }
+    if (e - a > INT32_MAX) { f |= F_ARG; e = a; }
+    double d = 0.0;
+    bool found = false;
+    int32_t off = 0;
+    for (int64_t k = a; k < e; k++) {
+      int32_t c = col[k];
+      if (c < 0 || c >= n) f |= F_ARG;
+      if (c == i) { d += val[k]; found = true; } else { off++; }
+    }
+    if (!found || !(d > 0.0)) f |= F_NOT_SPD;
+    rowlen[i] = off;          // off-diagonal entries of the row
+    diag[i] = d;
+    invd[i] = found && d > 0.0 ? 1.0 / d : 0.0;
+    if (f) atomicOr(flags, f);
+    if (found && d > 0.0) lo = hi = (unsigned long long)__double_as_longlong(d);
   }
-  if (e - a > INT32_MAX) { f |= F_ARG; e = a; }
-  double d = 0.0;
-  bool found = false;
-  int32_t off = 0;
-  for (int64_t k = a; k < e; k++) {
-    int32_t c = col[k];
-    if (c < 0 || c >= n) f |= F_ARG;
-    if (c == i) { d += val[k]; found = true; } else { off++; }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
-  if (!found || !(d > 0.0)) f |= F_NOT_SPD;
-  rowlen[i] = off;          // off-diagonal entries of the row
-  diag[i] = d;
-  invd[i] = found && d > 0.0 ? 1.0 / d : 0.0;
-  if (f) atomicOr(flags, f);
+  if ((threadIdx.x & 31) == 0) { atomicMin(dminmax, lo); atomicMax(dminmax + 1, hi); }
 }
 
 // One thread per (chunk row): write the row's off-diagonal slots, column-major inside its
@@ -164,20 +175,26 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   auto free_tmp = [&]() { for (void* p : tmp) pool_free(p, st); tmp.clear(); };
   double *d_diag0 = nullptr, *d_invd0 = nullptr;
   int32_t *d_len = nullptr, *d_flags = nullptr;
+  unsigned long long* d_mm = nullptr;
   cudaError_t e = cudaSuccess;
   if ((e = dalloc(&d_diag0, n, tmp, st)) || (e = dalloc(&d_invd0, n, tmp, st)) ||
-      (e = dalloc(&d_len, n, tmp, st)) || (e = dalloc(&d_flags, 1, tmp, st))) {
+      (e = dalloc(&d_len, n, tmp, st)) || (e = dalloc(&d_flags, 1, tmp, st)) ||
+      (e = dalloc(&d_mm, 2, tmp, st))) {
     free_tmp();
     set_error("ppcg_create: device allocation failed: %s", cudaGetErrorString(e));
     return PPCG_ERR_OOM;
   }
   cudaMemsetAsync(d_flags, 0, sizeof(int32_t), st);
+  cudaMemsetAsync(d_mm, 0xff, sizeof(unsigned long long), st);        // min: all ones
+  cudaMemsetAsync(d_mm + 1, 0, sizeof(unsigned long long), st);       // max: 0
   const int tb = 256;
   k_rows<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(n, nnz, d_rp, d_col, d_val, d_diag0, d_invd0,
-                                                       d_len, d_flags);
+                                                       d_len, d_flags, d_mm);
   int32_t flags = 0;
+  unsigned long long mm[2] = {0, 0};
   std::vector<int32_t> len(n);
   cudaMemcpyAsync(&flags, d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(mm, d_mm, sizeof(mm), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(len.data(), d_len, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
     free_tmp();
@@ -265,6 +282,8 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   out->nslots = nslots;
   out->sigma = (int32_t)sigma;
   out->padding = nnz > n ? (double)(nslots - (nnz - n)) / (double)(nnz - n) : 0.0;
+  std::memcpy(&out->dmin, &mm[0], sizeof(double));
+  std::memcpy(&out->dmax, &mm[1], sizeof(double));
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return PPCG_OK;
 }

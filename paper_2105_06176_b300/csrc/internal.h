@@ -46,6 +46,7 @@ enum Pass : int32_t {
   P_OINIT,     // FP32_IR: rhs32 = r64 / ||r64|| ; r32 = rhs32 ; u32 = M^-1 r32 ; d32 = 0
   P_OUPD,      // FP32_IR: x += ||r64|| * d32
   P_OUNDO,     // FP32_IR: x -= ||r64_prev|| * d32 (undo a refinement step that did not help)
+  P_NORM,      // stopping norm only (after an iteration pass that skipped it)
 };
 
 // Control states (see solver.cuh: control()).
@@ -53,7 +54,7 @@ enum State : int32_t {
   S_START = 0, S_AFTER_SETUP1, S_AFTER_SETUP2, S_TOP, S_AFTER_ITER, S_AFTER_TRUE, S_AFTER_RR1,
   S_AFTER_RR2, S_FINAL, S_AFTER_FINAL, S_DONE,
   S_O_START, S_O_AFTER_ORES, S_O_AFTER_ZERO, S_O_AFTER_OINIT, S_I_AFTER_SETUP2, S_I_TOP,
-  S_I_AFTER_ITER, S_I_AFTER_RR1, S_I_AFTER_RR2, S_O_AFTER_OUPD, S_O_AFTER_UNDO,
+  S_I_AFTER_ITER, S_I_AFTER_RR1, S_I_AFTER_RR2, S_O_AFTER_OUPD, S_O_AFTER_UNDO, S_AFTER_NORM,
 };
 
 // Device-resident control block of one solve.  Read by every CTA at launch start, written
@@ -63,6 +64,8 @@ struct Ctl {
   int32_t inner_iter, outer, rr_count, last_rr_iter;
   int32_t parity, first, exit_now, restart;  // restart: next step starts afresh (beta = 0)
   int32_t restarts, fallback;   // fallback: FP32_IR switched to the FP64 iteration
+  int32_t want_rr, rr_valid;    // the next iteration pass accumulates the norm; norm is current
+  int32_t norm_return, pad4;    // state to resume after a P_NORM pass
   double gamma, gamma_prev, delta, alpha, alpha_prev, beta, norm;
   double bnorm, rn, rn_prev, res_true, inner_norm0, inner_target, rr_norm_prev;
   unsigned long long t_start, t_end;
@@ -76,6 +79,7 @@ struct SysDesc {
   int32_t max_restarts, budget;   // budget: iterations this launch may advance (0 = launch's)
   int32_t variant, pad3;          // ppcg_variant
   double tol, inner_tol;
+  double dmin, dmax;     // extreme diagonal entries (bounds of ||r||^2 / gamma)
   int64_t spin_limit_ns;
   const double* b;       // right-hand side, solver order (plain array)
   // Per-row vectors in chunk-interleaved blocks (for each 32-row chunk, the block's slots
@@ -108,6 +112,7 @@ struct SellBuild {
   int32_t sigma = 1;
   double padding = 0.0;   // padded slots / off-diagonal nonzeros
   double seconds = 0.0;   // conversion wall time
+  double dmin = 0.0, dmax = 0.0;   // extreme diagonal entries
 };
 ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col,
                                 const double* d_val, int32_t sigma_req, bool want_fp32, bool sym_scale,

@@ -344,7 +344,7 @@ __device__ __forceinline__ void pass_setup2(const DevMatrix& A, const View<T, NS
 // row's own vector entries are loaded before the gather so their latency overlaps it.
 template <typename T, int NS, bool FIRST>
 __device__ __forceinline__ void pass_iter(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, Dots<T>& d,
-                                          T alpha, T beta, int k, bool paper_norm) {
+                                          T alpha, T beta, int k, bool paper_norm, bool with_rr = true) {
   const int wcs = (k & 1) ? V_WB : V_WA;
   const int wns = (k & 1) ? V_WA : V_WB;
   const GatherSlot<T, NS> gw{V.v.b + wcs * kChunk};
@@ -394,7 +394,20 @@ __device__ __forceinline__ void pass_iter(const DevMatrix& A, const View<T, NS>&
       stcs(pc + wns * kChunk, wnn);
       d.add(0, ri, un);
       d.add(1, wnn, un);
-      if (paper_norm) d.add(2, un, un); else d.add(2, ri, ri);
+      if (with_rr) { if (paper_norm) d.add(2, un, un); else d.add(2, ri, ri); }
+    }
+  }
+}
+
+// P_NORM (Alg. 2 form): partial ||r||^2 or (u, u).
+template <typename T, int NS>
+__device__ __forceinline__ void pass_norm(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, Dots<T>& d,
+                                          bool paper_norm) {
+  FOR_CHUNKS(A, L) {
+    const int32_t row = c * kChunk + L.lane;
+    if (row < A.n) {
+      const T v = ldcs(V.v.chunk(c, L.lane) + (paper_norm ? V_U : V_R) * kChunk);
+      d.add(2, v, v);
     }
   }
 }
@@ -651,7 +664,7 @@ __device__ __forceinline__ void spass_setup2(const SysDesc& S, const Lanes& L, D
 // x += alpha p ; r -= alpha s ; w -= alpha z ; partials.
 template <bool FIRST>
 __device__ __forceinline__ void spass_iter(const SysDesc& S, const Lanes& L, Dots<double>& d, double alpha,
-                                           double beta, int k, bool paper) {
+                                           double beta, int k, bool paper, bool with_rr) {
   const DevMatrix& A = S.A;
   const Blk<double, kNSS> v{S.v64};
   const int wcs = (k & 1) ? VS_WB : VS_WA;
@@ -671,7 +684,7 @@ __device__ __forceinline__ void spass_iter(const SysDesc& S, const Lanes& L, Dot
       wi = ldcg(pc + wcs * kChunk);
       ri = ldcs(pc + VS_R * kChunk);
       xi = ldcs(pc + VS_X * kChunk);
-      if (paper) sg = ldcs(pc + VS_SIG * kChunk); else di = ldcs(pc + VS_D * kChunk);
+      if (with_rr) { if (paper) sg = ldcs(pc + VS_SIG * kChunk); else di = ldcs(pc + VS_D * kChunk); }
       if (!FIRST) {
         zo = ldcs(pc + VS_Z * kChunk);
         so = ldcs(pc + VS_S * kChunk);
@@ -694,7 +707,22 @@ __device__ __forceinline__ void spass_iter(const SysDesc& S, const Lanes& L, Dot
       stcs(pc + wns * kChunk, wn);
       d.add(0, rn, rn);
       d.add(1, wn, rn);
-      d.a[2] += scaled_norm_term(paper, rn, di, sg);
+      if (with_rr) d.a[2] += scaled_norm_term(paper, rn, di, sg);
+    }
+  }
+}
+
+// P_NORM (scaled): partial sum d r~^2 (= ||r||^2) or sig^2 r~^2 (= (u, u)).
+__device__ __forceinline__ void spass_norm(const SysDesc& S, const Lanes& L, Dots<double>& d, bool paper) {
+  const Blk<double, kNSS> v{S.v64};
+  FOR_CHUNKS(S.A, L) {
+    const int32_t row = c * kChunk + L.lane;
+    if (row < S.A.n) {
+      const double* pc = v.chunk(c, L.lane);
+      const double ri = ldcs(pc + VS_R * kChunk);
+      const double di = paper ? 0.0 : ldcs(pc + VS_D * kChunk);
+      const double sg = paper ? ldcs(pc + VS_SIG * kChunk) : 0.0;
+      d.a[2] += scaled_norm_term(paper, ri, di, sg);
     }
   }
 }
@@ -916,6 +944,16 @@ __device__ __forceinline__ bool passed(const Ctl& c, const SysDesc& S) {
   return S.norm == PPCG_NORM_PAPER_U_ABS ? (c.norm <= S.tol) : (c.norm <= S.tol * c.bnorm);
 }
 
+// Could the stopping test pass, given only gamma?  ||r||^2 <= dmax gamma is not needed: the
+// lower bound dmin gamma <= ||r||^2 (REL_R) or gamma / dmax <= (u,u) (paper norm) decides
+// "certainly not yet"; slack widens the window (used to predict the next iteration).
+__device__ __forceinline__ bool may_pass(const Ctl& c, const SysDesc& S, double slack) {
+  if (!(c.gamma >= 0.0)) return true;
+  if (S.norm == PPCG_NORM_PAPER_U_ABS) return c.gamma / S.dmax <= slack * S.tol * S.tol;
+  const double t = S.tol * c.bnorm;
+  return c.gamma * S.dmin <= slack * t * t;
+}
+
 // Alg. 2 lines 5-9.  Returns false (and sets status) on breakdown.
 __device__ __forceinline__ bool scalars(Ctl& c, int it) {
   if (it > 0) {
@@ -945,18 +983,28 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
         }
         c.pass = P_SETUP2; c.state = S_AFTER_SETUP2; return;
       case S_AFTER_SETUP2:
-        take_dots(c); c.state = S_TOP; break;
+        take_dots(c); c.rr_valid = 1; c.state = S_TOP; break;
       case S_AFTER_ITER:
         c.gamma_prev = c.gamma; c.alpha_prev = c.alpha; c.iter++; c.restart = 0;
-        take_dots(c); c.state = S_TOP; break;
+        take_dots(c);
+        c.rr_valid = c.want_rr;
+        if (!c.want_rr) c.norm = HUGE_VAL;   // not accumulated this pass (see S_TOP)
+        c.state = S_TOP; break;
+      case S_AFTER_NORM:
+        c.norm = sqrt(c.red[2]); c.rr_valid = 1; c.state = c.norm_return; break;
       case S_AFTER_RR2:
-        take_dots(c); c.rr_count++; c.last_rr_iter = c.iter;
+        take_dots(c); c.rr_valid = 1; c.rr_count++; c.last_rr_iter = c.iter;
         if (passed(c, S)) { c.status = PPCG_OK; c.state = S_FINAL; break; }
         c.state = S_TOP; break;
       case S_TOP: {
         if (c.iter >= iter_end) { c.pass = P_NONE; c.exit_now = 1; return; }
         if (S.rr_period > 0 && c.iter > 0 && c.iter % S.rr_period == 0 && c.last_rr_iter != c.iter) {
           c.pass = P_RR1; c.state = S_AFTER_RR1; return;
+        }
+        // ||r||^2 lies in [dmin, dmax] * gamma ((u,u) in gamma * [1/dmax, 1/dmin]); when the
+        // last pass skipped the norm and the bound allows convergence, compute it exactly.
+        if (!c.rr_valid && may_pass(c, S, 1.001)) {
+          c.norm_return = S_TOP; c.pass = P_NORM; c.state = S_AFTER_NORM; return;
         }
         if (passed(c, S)) {
           if (S.norm == PPCG_NORM_PAPER_U_ABS) { c.status = PPCG_OK; c.state = S_FINAL; break; }
@@ -973,6 +1021,8 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
           c.status = PPCG_ERR_BREAKDOWN; c.state = S_FINAL; break;
         }
         c.first = (c.iter == 0 || c.restart);
+        // accumulate the norm only where the next residual could be within 8x of the target
+        c.want_rr = may_pass(c, S, 64.0) ? 1 : 0;
         c.pass = P_ITER; c.state = S_AFTER_ITER; return;
       }
       case S_AFTER_TRUE:
@@ -982,6 +1032,7 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
       case S_AFTER_RR1:
         c.pass = P_RR2; c.state = S_AFTER_RR2; return;
       case S_FINAL:
+        if (!c.rr_valid) { c.norm_return = S_FINAL; c.pass = P_NORM; c.state = S_AFTER_NORM; return; }
         c.pass = P_TRUE; c.state = S_AFTER_FINAL; return;
       case S_AFTER_FINAL:
         c.res_true = sqrt(c.red[0]); c.state = S_DONE; c.pass = P_NONE; return;
@@ -1117,9 +1168,10 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
         case P_SETUP1: spass_setup1(S, L, d, S.x_zero != 0); break;
         case P_SETUP2: spass_setup2(S, L, d, paper); break;
         case P_ITER:
-          if (C.first) spass_iter<true>(S, L, d, C.alpha, C.beta, C.iter, paper);
-          else spass_iter<false>(S, L, d, C.alpha, C.beta, C.iter, paper);
+          if (C.first) spass_iter<true>(S, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
+          else spass_iter<false>(S, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
           break;
+        case P_NORM: spass_norm(S, L, d, paper); break;
         case P_TRUE: spass_true(S, L, d); break;
         case P_RR1: spass_rr1(S, L, C.iter == 0 || C.restart); partials = false; break;
         case P_RR2: spass_rr2(S, L, d, C.iter, paper); break;
@@ -1140,11 +1192,12 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
             if (C.first) pass_iter_staged<double, kNS64, true>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, wst, bars, phases, S.err);
             else pass_iter_staged<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, wst, bars, phases, S.err);
           } else {
-            if (C.first) pass_iter<double, kNS64, true>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper);
-            else pass_iter<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper);
+            if (C.first) pass_iter<double, kNS64, true>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
+            else pass_iter<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
           }
           break;
         case P_TRUE: pass_true<kNS64, V_X>(S, L, d); break;
+        case P_NORM: pass_norm(S.A, V, L, d, paper); break;
         case P_RR1: pass_rr1(S.A, V, L, C.iter == 0 || C.restart); partials = false; break;
         case P_RR2: pass_rr2(S.A, V, L, d, C.iter, paper); break;
         case P_ZERO_X: pass_zero_x<kNS64, V_X>(S, L); partials = false; break;
