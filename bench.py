@@ -224,7 +224,7 @@ def measure_batch(pp, torch, count, seed=11, precision=0):
     iters = sum(i.iters for i in infos_bat)
     for s in seq + bat:
         s.close()
-    return {"systems": count, "rows": rows, "precision": "fp64" if precision == 0 else "fp32_ir",
+    return {"systems": count, "rows": rows, "precision": ("fp64", "fp32_ir", "fp32_ru")[precision],
             "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat, "all_ok": ok, "not_ok": bad,
             "iters_total": iters, "row_iters_per_s": sum(i.iters * a.n for i, (a, _) in zip(infos_bat, systems)) / t_bat}
 
@@ -254,7 +254,7 @@ def _serving_pool(seed, count, hi, buckets=24):
     return reqs
 
 
-def run_server(pp, reqs, arrivals, precision=1, epoch_iters=128):
+def run_server(pp, reqs, arrivals, precision=2, epoch_iters=128):
     """Submit reqs at the given arrival offsets (s); poll until all finish.  Returns
     (latencies, wall seconds, statuses)."""
     srv = pp.Server(precision=precision, epoch_iters=epoch_iters)
@@ -291,8 +291,19 @@ def measure_serving(pp, nreq=160, hi=2e5, seed=5, rate_factors=(0.5,)):
     run_server(pp, reqs[:8], [0.0] * 8)                       # warm-up
     lat, wall, st = run_server(pp, reqs, [0.0] * len(reqs))
     sat = len(reqs) / wall
-    out = {"requests": nreq, "size_range": [1e3, hi], "precision": "fp32_ir", "saturation_solves_per_s": sat,
-           "all_ok": all(s == pp.OK for s in st), "rates": []}
+    # the plain FP64 solver on the same stream, one request after another: create from the
+    # host CSR, solve, read x back (what the server does per request, without overlap)
+    t0 = time.perf_counter()
+    seq_ok = True
+    for a, b in reqs:
+        s = pp.Solver.from_csr(a)
+        x, info = s.solve(b, tol=TOL, maxit=SERVE_MAXIT)
+        seq_ok &= info.status == pp.OK
+        s.close()
+    seq = len(reqs) / (time.perf_counter() - t0)
+    out = {"requests": nreq, "size_range": [1e3, hi], "precision": "fp32_ru", "saturation_solves_per_s": sat,
+           "sequential_fp64_solves_per_s": seq, "speedup_vs_sequential_fp64": sat / seq,
+           "all_ok": all(s == pp.OK for s in st) and seq_ok, "rates": []}
     rng = np.random.default_rng(seed)
     for f in rate_factors:
         rate = f * sat
@@ -306,16 +317,16 @@ def measure_serving(pp, nreq=160, hi=2e5, seed=5, rate_factors=(0.5,)):
 
 
 def measure_rgg(pp, torch, npts=4_000_000, seed=3):
-    """Random geometric graph Laplacian (expected degree 14) + 1e-3 I: FP32+IR to 1e-8 and
-    FP64 to 1e-8 and 1e-10, time to solution and the FP32+IR error against the FP64 1e-10
-    solution."""
+    """Random geometric graph Laplacian (expected degree 14) + 1e-3 I: FP32_RU and FP32_IR to
+    1e-8 and FP64 to 1e-8 and 1e-10, time to solution and each result's error against the
+    FP64 1e-10 solution."""
     radius = (3 * 14.0 / (4 * np.pi * npts)) ** (1 / 3)
     a = synth.rgg_laplacian(npts, radius, 1e-3, seed)
     b = torch.from_numpy(synth.rhs_uniform(a.n, seed)).cuda()
     out = {"workload": f"RGG Laplacian {npts} points, radius {radius:.6f}, shift 1e-3", "N": a.n, "nnz": a.nnz}
     runs = {}
     for name, prec, tol in (("fp64_1e-10", pp.FP64, 1e-10), ("fp64_1e-8", pp.FP64, 1e-8),
-                            ("fp32_ir_1e-8", pp.FP32_IR, 1e-8)):
+                            ("fp32_ru_1e-8", pp.FP32_RU, 1e-8), ("fp32_ir_1e-8", pp.FP32_IR, 1e-8)):
         s = pp.Solver.from_csr(a, precision=prec)
         x = torch.empty_like(b)
         s.solve(b, None, x, tol=tol, maxit=MAXIT)
@@ -331,6 +342,7 @@ def measure_rgg(pp, torch, npts=4_000_000, seed=3):
         out[name] = {"s": t, "iters": info.iters, "outer": info.outer_iters, "status": pp.status_name(info.status),
                      "rel_res_true": info.rel_res_true,
                      "err_vs_fp64_1e-10": (torch.linalg.norm(x - ref) / torch.linalg.norm(ref)).item()}
+    out["fp32_ru_speedup_vs_fp64_1e-8"] = runs["fp64_1e-8"][2] / runs["fp32_ru_1e-8"][2]
     out["fp32_ir_speedup_vs_fp64_1e-8"] = runs["fp64_1e-8"][2] / runs["fp32_ir_1e-8"][2]
     return out
 
@@ -392,7 +404,7 @@ def main():
             res = {"mode": "rgg", "rgg": measure_rgg(pp, torch)}
         elif args.mode == "batch":
             res = {"mode": "batch", "fp64": measure_batch(pp, torch, args.batch_count),
-                   "fp32_ir": measure_batch(pp, torch, args.batch_count, precision=1)}
+                   "fp32_ru": measure_batch(pp, torch, args.batch_count, precision=pp.FP32_RU)}
         else:
             res = {"mode": "serve", "serving": measure_serving(pp, nreq=400, hi=4e6,
                                                                rate_factors=(0.25, 0.5, 1.0, 2.0, 4.0))}
@@ -504,22 +516,25 @@ def main():
             "gpu_launches": 2 * args.steps}
 
     if not args.no_mixed:
-        sm = pp.Solver.from_csr(a, precision=pp.FP32_IR)
-        xm = torch.empty(n, dtype=torch.float64, device="cuda")
-        sm.solve(b_d, None, xm, tol=TOL, maxit=MAXIT)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, im = sm.solve(b_d, None, xm, tol=TOL, maxit=MAXIT, sync=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_mixed = e0.elapsed_time(e1) * 1e-3
-        err = (torch.linalg.norm(xm - x_d) / torch.linalg.norm(x_d)).item()
-        line["mixed_vs_fp64"] = {"fp64_s": per_launch_s, "fp32_ir_s": t_mixed,
-                                 "speedup": per_launch_s / t_mixed, "fp32_ir_iters": im.iters,
-                                 "outer": im.outer_iters, "status": pp.status_name(im.status),
-                                 "rel_res_true": im.rel_res_true, "err_vs_fp64_solution": err,
-                                 "fp32_bytes_per_iter": b_alg(n, nnz, 4)}
-        sm.close()
+        # FP32 recurrences with FP64 reliable updates (the mixed-precision form), and FP32
+        # inner solves inside FP64 iterative refinement, against the FP64 solve above
+        line["mixed_vs_fp64"] = {"fp64_s": per_launch_s, "fp32_bytes_per_iter": b_alg(n, nnz, 4)}
+        for name, prec in (("fp32_ru", pp.FP32_RU), ("fp32_ir", pp.FP32_IR)):
+            sm = pp.Solver.from_csr(a, precision=prec)
+            xm = torch.empty(n, dtype=torch.float64, device="cuda")
+            sm.solve(b_d, None, xm, tol=TOL, maxit=MAXIT)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, im = sm.solve(b_d, None, xm, tol=TOL, maxit=MAXIT, sync=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_mixed = e0.elapsed_time(e1) * 1e-3
+            err = (torch.linalg.norm(xm - x_d) / torch.linalg.norm(x_d)).item()
+            line["mixed_vs_fp64"][name] = {"s": t_mixed, "speedup": per_launch_s / t_mixed, "iters": im.iters,
+                                           "outer": im.outer_iters, "status": pp.status_name(im.status),
+                                           "fp64_fallback": im.fp64_fallback, "rel_res_true": im.rel_res_true,
+                                           "err_vs_fp64_solution": err}
+            sm.close()
 
     if not args.no_mixed:
         # the Jacobi-scaled form of the same iteration (u = r, q = s; 13 streams per row)

@@ -53,7 +53,11 @@ typedef enum {
   PPCG_ERR_UNKNOWN_TICKET = -10
 } ppcg_status;
 
-typedef enum { PPCG_FP64 = 0, PPCG_FP32_IR = 1 } ppcg_precision;
+typedef enum {
+  PPCG_FP64 = 0,     /* every vector and the matrix in FP64 */
+  PPCG_FP32_IR = 1,  /* FP32 inner solves inside FP64 iterative refinement (restarted per step) */
+  PPCG_FP32_RU = 2   /* FP32 recurrences with FP64 reliable updates (one Krylov sequence) */
+} ppcg_precision;
 typedef enum { PPCG_FMT_AUTO = 0, PPCG_FMT_CSR = 1, PPCG_FMT_SELL = 2 } ppcg_format;
 typedef enum {
   PPCG_NORM_REL_R = 0,      /* ||r||_2 <= tol * ||b||_2 on the recursive residual, then a true-residual check */
@@ -74,17 +78,32 @@ typedef struct {
   int32_t precision;        /* ppcg_precision.  FP32_IR: FP32 matrix values and vectors inside an
                                FP64 iterative-refinement loop (FP64 outer residual and solution);
                                a refinement step that does not halve the FP64 residual is undone
-                               and the solve continues with the FP64 iteration. */
+                               and the solve continues with the FP64 iteration.
+                               FP32_RU: one pipelined iteration whose vectors and matrix values
+                               are FP32; the solution is accumulated in FP64, and a reliable
+                               update (FP64 residual b - A x, FP32 recurrences restarted from it,
+                               search direction kept) runs every rr_period iterations, whenever
+                               the recursive residual has fallen by inner_tol since the last one,
+                               and whenever it passes the stopping test, which the FP64 residual
+                               then decides.  Three updates in a row where the recursion claims
+                               a 4x fall and the FP64 residual does not halve, a non-finite
+                               value, or a breakdown past max_restarts switch to the FP64
+                               iteration from the last updated x.  REL_R norm only. */
   int32_t format;           /* ppcg_format.  The matrix is always converted to SELL-C-sigma (C = 32)
                                on the device; FMT_CSR forces sigma = 1 (CSR row order kept). */
   int32_t norm;             /* ppcg_norm */
   int32_t path;             /* ppcg_path.  GRID: one cooperative persistent launch over the whole GPU.
                                CLUSTER: one thread-block cluster per system.  AUTO picks by size. */
-  int32_t sigma;            /* SELL sorting window in rows (0 = autotune, 1 = no sorting) */
+  int32_t sigma;            /* SELL sorting window in rows (1 = no sorting; 0 = autotune over
+                               {1, 256, 2048}: padded matrix bytes plus a gather-locality cost
+                               for sorted windows, whose chunks mix rows from all over the window) */
   int32_t rr_period;        /* residual replacement every rr_period iterations.  FP64: 0 = only when the
                                recursive residual passes but the true residual does not.  FP32_IR: the
-                               period inside each inner solve, 0 = 25 */
-  double inner_tol;         /* FP32_IR: relative residual reduction asked of each inner solve */
+                               period inside each inner solve, 0 = 25.  FP32_RU: the iterations
+                               between reliable updates, 0 = 15 */
+  double inner_tol;         /* FP32_IR: relative residual reduction asked of each inner solve.
+                               FP32_RU: the fall of the recursive residual that triggers a
+                               reliable update */
   int32_t inner_maxit;      /* FP32_IR: iteration cap of one inner solve */
   int32_t max_outer;        /* FP32_IR: cap on refinement steps */
   int64_t spin_limit_ns;    /* time limit of one device-side barrier wait (ns); exceeded -> TIMEOUT */
@@ -104,7 +123,7 @@ typedef struct {
   int32_t status;            /* ppcg_status */
   int32_t iters;             /* iterations of Alg. 2 (executions of the vector-update block); FP32_IR:
                                 summed over inner solves */
-  int32_t outer_iters;       /* FP32_IR refinement steps (0 for FP64) */
+  int32_t outer_iters;       /* FP32_IR refinement steps; FP32_RU FP64 residual evaluations (0 for FP64) */
   int32_t rr_count;          /* residual replacements performed (restarts included) */
   double rel_res_recursive;  /* stopping norm at exit, divided by ||b|| (REL_R) or absolute (PAPER_U_ABS) */
   double rel_res_true;       /* ||b - A x||_2 / ||b||_2 at exit, FP64 (0 when b = 0) */
@@ -112,7 +131,8 @@ typedef struct {
   double bytes_per_iter;     /* algorithmic bytes of one iteration: (v+4) nnz + 4 (N+1) + 17 v N */
   double bnorm;              /* ||b||_2 */
   int32_t fp64_fallback;     /* FP32_IR: 1 when a refinement step failed to halve the FP64 residual and
-                                the solve finished with the FP64 iteration from the previous x */
+                                the solve finished with the FP64 iteration from the previous x;
+                                FP32_RU: 1 when the solve finished with the FP64 iteration */
   int32_t reserved;
 } ppcg_info;
 

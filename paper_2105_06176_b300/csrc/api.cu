@@ -237,13 +237,15 @@ void stage_outputs(ppcg_ctx* h, double* x, cudaStream_t st) {
 void prepare_control(ppcg_ctx* h, double tol, int32_t maxit, cudaStream_t st) {
   h->desc.tol = tol;
   h->desc.maxit = maxit;
-  k_init_ctl<<<1, 1, 0, st>>>(h->ctl, h->opts.precision == PPCG_FP32_IR ? S_O_START : S_START);
+  k_init_ctl<<<1, 1, 0, st>>>(h->ctl, h->opts.precision == PPCG_FP32_IR   ? S_O_START
+                                      : h->opts.precision == PPCG_FP32_RU ? S_U_START
+                                                                          : S_START);
   cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st);
   cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
 }
 
 size_t footprint_bytes(int64_t n, int64_t nnz, int32_t precision) {
-  const bool fp32 = precision == PPCG_FP32_IR;
+  const bool fp32 = precision != PPCG_FP64;
   const double slots = 1.05 * (double)nnz + 32.0 * ((double)n / 32.0 + 1.0);
   double bytes = slots * (fp32 ? 16.0 : 12.0) + (double)n * 8.0 * 6.0;   // matrix + cptr/diag/invd/b/tmp/perm
   bytes += (double)n * 8.0 * 10.0 + (fp32 ? (double)n * 4.0 * 11.0 : 0.0);
@@ -321,7 +323,12 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   ppcg_ctx* h = new ppcg_ctx();
   ppcg_opts_default(&h->opts);
   if (opts) h->opts = *opts;
-  if (h->opts.precision != PPCG_FP64 && h->opts.precision != PPCG_FP32_IR) { delete h; set_error("ppcg_create: bad precision"); return PPCG_ERR_ARG; }
+  if (h->opts.precision != PPCG_FP64 && h->opts.precision != PPCG_FP32_IR && h->opts.precision != PPCG_FP32_RU) {
+    delete h; set_error("ppcg_create: bad precision"); return PPCG_ERR_ARG;
+  }
+  if (h->opts.precision == PPCG_FP32_RU && h->opts.norm != PPCG_NORM_REL_R) {
+    delete h; set_error("ppcg_create: FP32_RU stops on the relative FP64 residual (norm REL_R only)"); return PPCG_ERR_ARG;
+  }
   if (h->opts.norm != PPCG_NORM_REL_R && h->opts.norm != PPCG_NORM_PAPER_U_ABS) { delete h; set_error("ppcg_create: bad norm"); return PPCG_ERR_ARG; }
   if (h->opts.variant != PPCG_VARIANT_ALG2 && h->opts.variant != PPCG_VARIANT_JACOBI_SCALED) {
     delete h; set_error("ppcg_create: bad variant"); return PPCG_ERR_ARG;
@@ -365,7 +372,7 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
     return PPCG_ERR_OOM;
   }
   int32_t sigma = h->opts.format == PPCG_FMT_CSR ? 1 : h->opts.sigma;
-  ppcg_status s = convert_csr_to_sell(n, nnz, d_rp, d_col, d_val, sigma, h->opts.precision == PPCG_FP32_IR,
+  ppcg_status s = convert_csr_to_sell(n, nnz, d_rp, d_col, d_val, sigma, h->opts.precision != PPCG_FP64,
                                       h->opts.variant == PPCG_VARIANT_JACOBI_SCALED, stream, h->allocs, &h->sell,
                                       &h->A, &h->perm);
   free_tmp();
@@ -392,7 +399,7 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
     h->grid = kClusterSize;
     h->nparts = kClusterSize;
   }
-  const bool fp32 = h->opts.precision == PPCG_FP32_IR;
+  const bool fp32 = h->opts.precision != PPCG_FP64;
   const double v = fp32 ? 4.0 : 8.0;
   h->bytes_per_iter = (v + 4.0) * (double)nnz + 4.0 * (double)(n + 1) + 17.0 * v * (double)n;
   if (h->opts.variant == PPCG_VARIANT_JACOBI_SCALED)   // off-diagonals, 13 vector streams
@@ -431,9 +438,13 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   d.A = h->A;
   d.precision = h->opts.precision;
   d.norm = h->opts.norm;
-  // FP32 pipelined recurrences drift far faster than FP64 ones: replace residuals in the
-  // inner solve every 25 iterations unless the caller chose a period.
-  d.rr_period = fp32 && h->opts.rr_period == 0 ? 25 : h->opts.rr_period;
+  // FP32 pipelined recurrences drift far faster than FP64 ones: unless the caller chose a
+  // period, FP32_IR replaces residuals every 25 inner iterations and FP32_RU makes a
+  // reliable update every 15 iterations.
+  d.rr_period = h->opts.rr_period != 0                ? h->opts.rr_period
+                : h->opts.precision == PPCG_FP32_IR ? 25
+                : h->opts.precision == PPCG_FP32_RU ? 15
+                                                    : 0;
   d.inner_maxit = h->opts.inner_maxit;
   d.max_outer = h->opts.max_outer;
   d.max_restarts = h->opts.max_restarts < 0 ? 0 : h->opts.max_restarts;

@@ -25,7 +25,7 @@ struct DevMatrix {
   const int64_t* cptr;   // [nchunks + 1] slot offset of each chunk (multiple of 32)
   const int32_t* col;    // [nslots] column-major within a chunk: slot(base + j*32 + lane)
   const double* val;     // [nslots] a_ij / a_jj
-  const float* val32;    // [nslots] same rounded to FP32 (FP32_IR only)
+  const float* val32;    // [nslots] same rounded to FP32 (FP32 modes only)
   const double* invd;    // [n] 1 / a_ii
   const float* invd32;   // [n]
   const double* diag;    // [n] a_ii
@@ -47,14 +47,22 @@ enum Pass : int32_t {
   P_OUPD,      // FP32_IR: x += ||r64|| * d32
   P_OUNDO,     // FP32_IR: x -= ||r64_prev|| * d32 (undo a refinement step that did not help)
   P_NORM,      // stopping norm only (after an iteration pass that skipped it)
+  P_URES,      // FP32_RU: t = b - A x in FP64 ; r32 = t ; u32 = M^-1 r32 ; s32 = A p32 ;
+               //          q32 = M^-1 s32 ; partials (t,t) (b,b)
+  P_URR2,      // FP32_RU: w32 = A u32 ; z32 = A q32 ; partials
+  P_UFLUSH,    // FP32_RU: x += d32 ; d32 = 0
 };
 
-// Control states (see solver.cuh: control()).
+// Control states (see control() in solver.cu).
 enum State : int32_t {
+  // FP64 iteration (also the FP32 modes' fallback): every state below S_O_START
   S_START = 0, S_AFTER_SETUP1, S_AFTER_SETUP2, S_TOP, S_AFTER_ITER, S_AFTER_TRUE, S_AFTER_RR1,
-  S_AFTER_RR2, S_FINAL, S_AFTER_FINAL, S_DONE,
+  S_AFTER_RR2, S_FINAL, S_AFTER_FINAL, S_DONE, S_AFTER_NORM,
+  // FP32_IR
   S_O_START, S_O_AFTER_ORES, S_O_AFTER_ZERO, S_O_AFTER_OINIT, S_I_AFTER_SETUP2, S_I_TOP,
-  S_I_AFTER_ITER, S_I_AFTER_RR1, S_I_AFTER_RR2, S_O_AFTER_OUPD, S_O_AFTER_UNDO, S_AFTER_NORM,
+  S_I_AFTER_ITER, S_I_AFTER_RR1, S_I_AFTER_RR2, S_O_AFTER_OUPD, S_O_AFTER_UNDO,
+  // FP32_RU
+  S_U_START, S_U_AFTER_RES, S_U_AFTER_RR2, S_U_TOP, S_U_AFTER_ITER, S_U_AFTER_FLUSH,
 };
 
 // Device-resident control block of one solve.  Read by every CTA at launch start, written
@@ -66,6 +74,8 @@ struct Ctl {
   int32_t restarts, fallback;   // fallback: FP32_IR switched to the FP64 iteration
   int32_t want_rr, rr_valid;    // the next iteration pass accumulates the norm; norm is current
   int32_t norm_return, pad4;    // state to resume after a P_NORM pass
+  int32_t stalls, ru_due;       // FP32_RU: reliable updates in a row without progress; this one was due
+  double rmax;                  // FP32_RU: largest recursive norm since the last reliable update
   double gamma, gamma_prev, delta, alpha, alpha_prev, beta, norm;
   double bnorm, rn, rn_prev, res_true, inner_norm0, inner_target, rr_norm_prev;
   unsigned long long t_start, t_end;

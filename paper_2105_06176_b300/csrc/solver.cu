@@ -252,6 +252,50 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* _
   return acc;
 }
 
+// Two products over the same row in one sweep of its slots: acc1 += A x1, acc2 += A x2.
+// Each accumulator sees the same FMA sequence as a row_dot of its own, so results are
+// identical; the matrix slots are read once instead of twice.
+template <typename T, bool SCALE, class G1, class G2>
+__device__ __forceinline__ void row_dot2(const int32_t* __restrict__ col, const T* __restrict__ val, const G1& x1,
+                                         const G2& x2, const T* __restrict__ dsc, int64_t base, int len, T& acc1,
+                                         T& acc2) {
+  int j = 0;
+  for (; j + 8 <= len; j += 8) {
+    int32_t c[8];
+    T a[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      c[k] = ld_stream(col + base + (int64_t)(j + k) * kChunk);
+      a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      T v1 = x1(c[k]), v2 = x2(c[k]);
+      if (SCALE) { const T sc = __ldg(dsc + c[k]); v1 = sc * v1; v2 = sc * v2; }
+      acc1 = fma(a[k], v1, acc1);
+      acc2 = fma(a[k], v2, acc2);
+    }
+  }
+  int32_t c[7];
+  T a[7];
+#pragma unroll
+  for (int k = 0; k < 7; k++) {
+    if (j + k < len) {
+      c[k] = ld_stream(col + base + (int64_t)(j + k) * kChunk);
+      a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 7; k++) {
+    if (j + k < len) {
+      T v1 = x1(c[k]), v2 = x2(c[k]);
+      if (SCALE) { const T sc = __ldg(dsc + c[k]); v1 = sc * v1; v2 = sc * v2; }
+      acc1 = fma(a[k], v1, acc1);
+      acc2 = fma(a[k], v2, acc2);
+    }
+  }
+}
+
 // Vector slots.  FP64 block (NS 10): r u wa wb z q s p x invd.  FP32 block (NS 11):
 // r u wa wb z q s p d invd rhs (d: inner solution).  FP32_IR keeps its FP64 outer residual
 // and solution in slots r and x of the FP64 block.
@@ -557,8 +601,8 @@ __device__ __forceinline__ void pass_rr1(const DevMatrix& A, const View<T, NS>& 
       ax = di * ldcg(pc + V_X * kChunk);
       if (!p_zero) ap = di * ldcg(pc + V_P * kChunk);
     }
-    ax = row_dot<T, true>(A.col, V.val, gx, V.dsc, base, len, ax);
-    if (!p_zero) ap = row_dot<T, true>(A.col, V.val, gp, V.dsc, base, len, ap);
+    if (p_zero) ax = row_dot<T, true>(A.col, V.val, gx, V.dsc, base, len, ax);
+    else row_dot2<T, true>(A.col, V.val, gx, gp, V.dsc, base, len, ax, ap);
     if (in) {
       const T ri = rh - ax;
       stcs(pc + V_R * kChunk, ri);
@@ -584,8 +628,8 @@ __device__ __forceinline__ void pass_rr2(const DevMatrix& A, const View<T, NS>& 
     T* pc = V.v.chunk(c, L.lane);
     T ri = T(0), ui = T(0), si = T(0);
     if (in) { ri = ldcg(pc + V_R * kChunk); ui = ldcs(pc + V_U * kChunk); si = ldcg(pc + V_S * kChunk); }
-    const T wi = row_dot<T, false>(A.col, V.val, gr, nullptr, base, len, ri);
-    const T zi = row_dot<T, false>(A.col, V.val, gs, nullptr, base, len, si);
+    T wi = ri, zi = si;
+    row_dot2<T, false>(A.col, V.val, gr, gs, nullptr, base, len, wi, zi);
     if (in) {
       stcs(pc + wcs * kChunk, wi);
       stcs(pc + V_Z * kChunk, zi);
@@ -772,8 +816,8 @@ __device__ __forceinline__ void spass_rr1(const SysDesc& S, const Lanes& L, bool
       ax = ldcg(pc + VS_X * kChunk);
       if (!p_zero) ap = ldcg(pc + VS_P * kChunk);
     }
-    ax = row_dot<double, false>(A.col, A.val, gx, nullptr, base, len, ax);
-    if (!p_zero) ap = row_dot<double, false>(A.col, A.val, gp, nullptr, base, len, ap);
+    if (p_zero) ax = row_dot<double, false>(A.col, A.val, gx, nullptr, base, len, ax);
+    else row_dot2<double, false>(A.col, A.val, gx, gp, nullptr, base, len, ax, ap);
     if (in) {
       stcs(pc + VS_R * kChunk, fma(sg, bi, -ax));
       stcs(pc + VS_S * kChunk, ap);
@@ -800,8 +844,8 @@ __device__ __forceinline__ void spass_rr2(const SysDesc& S, const Lanes& L, Dots
       si = ldcg(pc + VS_S * kChunk);
       if (paper) sg = ldcs(pc + VS_SIG * kChunk); else di = ldcs(pc + VS_D * kChunk);
     }
-    const double wi = row_dot<double, false>(A.col, A.val, gr, nullptr, base, len, ri);
-    const double zi = row_dot<double, false>(A.col, A.val, gs, nullptr, base, len, si);
+    double wi = ri, zi = si;
+    row_dot2<double, false>(A.col, A.val, gr, gs, nullptr, base, len, wi, zi);
     if (in) {
       stcs(pc + wcs * kChunk, wi);
       stcs(pc + VS_Z * kChunk, zi);
@@ -884,6 +928,112 @@ __device__ __forceinline__ void pass_oupd(const SysDesc& S, const Lanes& L, doub
     if (row < S.A.n) {
       double* px = v64.chunk(c, L.lane) + IR_X * kChunk;
       *px = fma(rn, (double)ldcs(v32.chunk(c, L.lane) + V_X * kChunk), *px);
+    }
+  }
+}
+
+// ------------------------------- FP32 recurrences with FP64 reliable updates (FP32_RU) --
+// x (FP64 block, slot x) holds the solution up to the last reliable update; d32 (FP32 block,
+// slot d) the FP32 sum of alpha p since then.  A reliable update folds d32 into x, then
+// recomputes the residual in FP64 and restarts the FP32 recurrences of r, u, w, s, q, z
+// from it (p is kept, so the Krylov space is not restarted).
+
+// t_x += A x and (DP) t_p += A p over one row's slots in one sweep: x in FP64 against the
+// FP64 values, p in FP32 against the FP32 values.
+template <bool DP>
+__device__ __forceinline__ void row_dot_ures(const DevMatrix& A, const GatherSlot<double, kNS64>& gx,
+                                             const GatherSlot<float, kNS32>& gp, int64_t base, int len, double& ax,
+                                             float& ap) {
+  int j = 0;
+  for (; j + 8 <= len; j += 8) {
+    int32_t c[8];
+    double a[8];
+    float b[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      c[k] = ld_stream(A.col + base + (int64_t)(j + k) * kChunk);
+      a[k] = ld_stream(A.val + base + (int64_t)(j + k) * kChunk);
+      if (DP) b[k] = ld_stream(A.val32 + base + (int64_t)(j + k) * kChunk);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      ax = fma(a[k], __ldg(A.diag + c[k]) * gx(c[k]), ax);
+      if (DP) ap = fmaf(b[k], __ldg(A.diag32 + c[k]) * gp(c[k]), ap);
+    }
+  }
+  int32_t c[7];
+  double a[7];
+  float b[7];
+#pragma unroll
+  for (int k = 0; k < 7; k++) {
+    if (j + k < len) {
+      c[k] = ld_stream(A.col + base + (int64_t)(j + k) * kChunk);
+      a[k] = ld_stream(A.val + base + (int64_t)(j + k) * kChunk);
+      if (DP) b[k] = ld_stream(A.val32 + base + (int64_t)(j + k) * kChunk);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 7; k++) {
+    if (j + k < len) {
+      ax = fma(a[k], __ldg(A.diag + c[k]) * gx(c[k]), ax);
+      if (DP) ap = fmaf(b[k], __ldg(A.diag32 + c[k]) * gp(c[k]), ap);
+    }
+  }
+}
+
+// P_URES (d32 already folded into x).  x_zero: x = 0 (first update of a solve with x0 = 0);
+// d_zero: d32 unset, set it to 0 (first update); p_zero: p = 0 (first update or a restart),
+// so s = q = 0.
+__device__ __forceinline__ void pass_ures(const SysDesc& S, const Lanes& L, Dots<double>& d, bool x_zero,
+                                          bool d_zero, bool p_zero) {
+  const DevMatrix& A = S.A;
+  const Blk<double, kNS64> v64{S.v64};
+  const Blk<float, kNS32> v32{S.v32};
+  const GatherSlot<double, kNS64> gx{S.v64 + IR_X * kChunk};
+  const GatherSlot<float, kNS32> gp{S.v32 + V_P * kChunk};
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
+    const bool in = row < A.n;
+    float* p32 = v32.chunk(c, L.lane);
+    double ax = 0.0, bi = 0.0;
+    float ap = 0.0f, id = 0.0f;
+    if (in) {
+      bi = __ldg(S.b + row);
+      id = ldcs(p32 + V_INVD * kChunk);
+      if (!x_zero) ax = __ldg(A.diag + row) * ldcg(v64.chunk(c, L.lane) + IR_X * kChunk);
+      if (!p_zero) ap = __ldg(A.diag32 + row) * ldcg(p32 + V_P * kChunk);
+    }
+    if (!x_zero) {
+      if (p_zero) row_dot_ures<false>(A, gx, gp, base, len, ax, ap);
+      else row_dot_ures<true>(A, gx, gp, base, len, ax, ap);
+    }
+    if (in) {
+      const double t = bi - ax;
+      const float r = (float)t;
+      stcs(p32 + V_R * kChunk, r);
+      stcs(p32 + V_U * kChunk, id * r);
+      stcs(p32 + V_S * kChunk, ap);
+      stcs(p32 + V_Q * kChunk, id * ap);
+      if (d_zero) stcs(p32 + V_X * kChunk, 0.0f);
+      d.add(0, t, t);
+      d.add(1, bi, bi);
+    }
+  }
+}
+
+// P_UFLUSH: x += d32 ; d32 = 0.
+__device__ __forceinline__ void pass_uflush(const SysDesc& S, const Lanes& L) {
+  const Blk<double, kNS64> v64{S.v64};
+  const Blk<float, kNS32> v32{S.v32};
+  FOR_CHUNKS(S.A, L) {
+    const int32_t row = c * kChunk + L.lane;
+    if (row < S.A.n) {
+      double* px = v64.chunk(c, L.lane) + IR_X * kChunk;
+      float* pd = v32.chunk(c, L.lane) + V_X * kChunk;
+      *px = *px + (double)*pd;
+      *pd = 0.0f;
     }
   }
 }
@@ -1114,6 +1264,75 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
       case S_O_AFTER_OUPD:
         c.outer++; c.rn_prev = c.rn;
         c.pass = P_ORES; c.state = S_O_AFTER_ORES; return;
+
+      // ---- FP32 recurrences with FP64 reliable updates.  An update is due every rr_period
+      // iterations and when the recursive residual has fallen by inner_tol from its largest
+      // value since the last one, and is forced when the recursive residual passes the
+      // stopping test or maxit is reached; the FP64 residual it computes decides.
+      case S_U_START:
+        c.pass = P_URES; c.state = S_U_AFTER_RES; return;
+      case S_U_AFTER_FLUSH:
+        c.pass = P_URES; c.state = S_U_AFTER_RES; return;
+      case S_U_AFTER_RES: {
+        const double rt = sqrt(c.red[0]);
+        const bool first = c.outer == 0;
+        if (first) c.bnorm = sqrt(c.red[1]);
+        c.outer++;
+        if (c.bnorm == 0.0) { c.status = PPCG_OK; c.pass = P_ZERO_X; c.state = S_O_AFTER_ZERO; return; }
+        if (!isfinite(rt)) {
+          if (first) { c.status = PPCG_ERR_NONFINITE; c.res_true = rt; c.state = S_DONE; c.pass = P_NONE; return; }
+          c.state = S_O_AFTER_UNDO; break;   // FP64 iteration from x
+        }
+        if (!first && c.ru_due) {
+          // A stall: the FP32 recursion claimed at least a 4x fall since the last update
+          // and the FP64 residual did not even halve.  Three in a row: FP32 cannot make
+          // progress on this system (kappa * eps32 too large).
+          if (rt <= 0.5 * c.rn) c.stalls = 0;
+          else if (c.rr_norm_prev <= 0.25 * c.rn) c.stalls++;
+          if (c.stalls >= 3) { c.state = S_O_AFTER_UNDO; break; }
+        }
+        c.ru_due = 0;
+        c.rn_prev = c.rn; c.rn = rt; c.res_true = rt;
+        if (rt <= S.tol * c.bnorm || c.iter >= S.maxit) {   // x already holds every step
+          c.status = rt <= S.tol * c.bnorm ? PPCG_OK : PPCG_ERR_NOT_CONVERGED;
+          c.state = S_DONE; c.pass = P_NONE; return;
+        }
+        c.last_rr_iter = c.iter;
+        c.pass = first ? P_SETUP2 : P_URR2; c.state = S_U_AFTER_RR2; return;
+      }
+      case S_U_AFTER_RR2:
+        take_dots(c);
+        if (c.outer > 1) c.rr_count++;
+        c.rmax = c.norm;
+        c.state = S_U_TOP; break;
+      case S_U_AFTER_ITER:
+        c.gamma_prev = c.gamma; c.alpha_prev = c.alpha; c.iter++; c.inner_iter++; c.restart = 0;
+        take_dots(c);
+        c.rmax = fmax(c.rmax, c.norm);
+        c.state = S_U_TOP; break;
+      case S_U_TOP: {
+        if (c.iter >= iter_end) { c.pass = P_NONE; c.exit_now = 1; return; }
+        if (!isfinite(c.gamma) || !isfinite(c.delta) || !isfinite(c.norm)) { c.state = S_O_AFTER_UNDO; break; }
+        if (c.last_rr_iter != c.iter) {
+          const bool periodic = S.rr_period > 0 && c.iter - c.last_rr_iter >= S.rr_period;
+          if (periodic || c.norm <= S.inner_tol * c.rmax || c.norm <= S.tol * c.bnorm || c.iter >= S.maxit) {
+            c.ru_due = 1; c.rr_norm_prev = c.norm;
+            c.pass = P_UFLUSH; c.state = S_U_AFTER_FLUSH; return;
+          }
+        }
+        if (!scalars(c, c.restart ? 0 : c.inner_iter)) {
+          if (c.inner_iter > 0 && !c.restart && c.restarts < S.max_restarts) {
+            c.restarts++; c.restart = 1; c.ru_due = 0;   // update with p = 0: next beta = 0
+            c.pass = P_UFLUSH; c.state = S_U_AFTER_FLUSH; return;
+          }
+          if (c.inner_iter == 0) {
+            c.status = PPCG_ERR_BREAKDOWN; c.pass = P_TRUE; c.state = S_AFTER_FINAL; return;
+          }
+          c.state = S_O_AFTER_UNDO; break;   // restarts used up: FP64 iteration from x
+        }
+        c.first = (c.inner_iter == 0 || c.restart);
+        c.pass = P_ITER; c.state = S_U_AFTER_ITER; return;
+      }
       default:
         c.status = PPCG_ERR_ARG; c.state = S_DONE; c.pass = P_NONE; return;
     }
@@ -1159,7 +1378,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
     __syncthreads();
     const int pass = C.pass;
     if (pass == P_NONE) break;
-    const bool fp32 = S.precision == PPCG_FP32_IR && (C.state >= S_O_START);
+    const bool fp32 = S.precision != PPCG_FP64 && (C.state >= S_O_START);
     double* slot = S.part + ((size_t)C.parity * P + g.rank()) * 4;
     bool partials = true;
     if (!fp32 && S.variant == PPCG_VARIANT_JACOBI_SCALED) {
@@ -1204,9 +1423,14 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
         default: partials = false; break;
       }
       if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
-    } else if (pass == P_ORES || pass == P_ZERO_X || pass == P_OINIT || pass == P_OUPD || pass == P_OUNDO) {
+    } else if (pass == P_ORES || pass == P_ZERO_X || pass == P_OINIT || pass == P_OUPD || pass == P_OUNDO ||
+               pass == P_URES || pass == P_UFLUSH) {
       Dots<double> d;
       switch (pass) {
+        case P_URES:
+          pass_ures(S, L, d, S.x_zero != 0 && C.outer == 0, C.outer == 0, C.inner_iter == 0 || C.restart);
+          break;
+        case P_UFLUSH: pass_uflush(S, L); partials = false; break;
         case P_ORES: pass_ores(S, L, d); break;
         case P_ZERO_X: pass_zero_x<kNS64, IR_X>(S, L); partials = false; break;
         case P_OINIT: pass_oinit(S, L, 1.0 / C.rn); partials = false; break;
@@ -1233,6 +1457,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
           break;
         case P_RR1: pass_rr1(S.A, V, L, C.inner_iter == 0 || C.restart); partials = false; break;
         case P_RR2: pass_rr2(S.A, V, L, d, C.inner_iter, paper); break;
+        case P_URR2: pass_rr2(S.A, V, L, d, C.inner_iter, paper); break;
         default: partials = false; break;
       }
       if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);

@@ -81,6 +81,68 @@ def test_fp32_ir_falls_back_to_fp64_when_refinement_stalls():
     assert np.linalg.norm(bn - a.to_scipy() @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(bn)
 
 
+# ------------------------------------------------- FP32 with FP64 reliable updates ----
+
+@pytest.mark.parametrize("name", ["varcoeff3d_40", "rgg_30k", "poisson2d_64"])
+@pytest.mark.parametrize("path", [1, 2], ids=["grid", "cluster"])
+def test_fp32_ru_reaches_fp64_accuracy(name, path):
+    """One FP32 Krylov sequence with FP64 reliable updates: true residual <= 1e-8, and (the
+    point of keeping the search direction across updates) about the FP64 iteration count."""
+    m = pp()
+    if name == "varcoeff3d_40":
+        a = synth.varcoeff3d(40, seed=2); b = synth.rhs_uniform(a.n, 2)
+    elif name == "rgg_30k":
+        a = rgg(30000, 3); b = synth.rhs_uniform(a.n, 3)
+    else:
+        a = synth.poisson2d(64); b = a.to_scipy() @ synth.xtrue_uniform(a.n, 1)
+    ref = oracle.pipecg(a, b, tol=1e-10, maxit=50000)
+    it64 = oracle.pipecg(a, b, tol=1e-8, maxit=50000)["result"]["iters"]
+    s = m.Solver.from_csr(a, precision=m.FP32_RU, path=path)
+    x, info = s.solve(dev(b), tol=1e-8, maxit=50000)
+    x = x.cpu().numpy()
+    assert info.status == m.OK, info
+    t = np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)
+    assert t <= 1e-8 and info.rel_res_true <= 1e-8
+    # rel_res_true is the FP64 residual of the returned x, computed on the device
+    assert abs(t - info.rel_res_true) <= 1e-3 * t + 1e-15
+    assert info.fp64_fallback == 0 and info.outer_iters >= 2
+    assert info.iters <= 1.6 * it64 + 10, (info.iters, it64)
+    assert rel(x, ref["x"]) <= 1e-4
+
+
+def test_fp32_ru_hard_system_finishes_in_fp64_accuracy():
+    """kappa near 1/eps32 (2-D log-normal, 1164^2 rows): whether the reliable updates keep the
+    FP32 sequence going or the solve falls back to the FP64 iteration, the returned x meets
+    the FP64 residual bar."""
+    m = pp()
+    a = synth.varcoeff2d(1164, 77)
+    b = dev(synth.rhs_uniform(a.n, 78))
+    s = m.Solver.from_csr(a, precision=m.FP32_RU)
+    x, info = s.solve(b, tol=1e-8, maxit=200000)
+    assert info.status == m.OK, info
+    bn = b.cpu().numpy()
+    assert np.linalg.norm(bn - a.to_scipy() @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(bn)
+
+
+def test_fp32_ru_edge_cases():
+    m = pp()
+    a = synth.poisson2d(40)
+    s = m.Solver.from_csr(a, precision=m.FP32_RU)
+    x, info = s.solve(torch.zeros(a.n, dtype=torch.float64, device="cuda"), tol=1e-8, maxit=100)
+    assert info.status == m.OK and info.iters == 0 and not x.abs().max().item()
+    xt = synth.xtrue_uniform(a.n, 4)
+    b = a.to_scipy() @ xt
+    x, info = s.solve(dev(b), x0=dev(xt), tol=1e-8, maxit=100)     # exact initial guess
+    assert info.status == m.OK and info.iters == 0
+    assert np.array_equal(x.cpu().numpy(), xt)
+    x, info = s.solve(dev(b), tol=1e-8, maxit=5)                     # maxit: x still written
+    assert info.status == m.ERR_NOT_CONVERGED and info.iters == 5
+    t = np.linalg.norm(b - a.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert abs(t - info.rel_res_true) <= 1e-6 * t
+    with pytest.raises(m.PPCGError):
+        m.Solver.from_csr(a, precision=m.FP32_RU, norm=m.NORM_PAPER_U_ABS)
+
+
 # ------------------------------------------------------------------ batched ------------
 
 def _batch_systems():
@@ -88,7 +150,7 @@ def _batch_systems():
     return [synth.build_spec(s) for s in specs]
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32_ir"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "fp32_ir", "fp32_ru"])
 def test_batch_bitwise_equals_solo(precision):
     m = pp()
     systems = _batch_systems()
@@ -143,7 +205,7 @@ def _wait(srv, tickets, n_of, timeout=120.0):
     return out
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32_ir"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "fp32_ir", "fp32_ru"])
 def test_server_results_same_alone_and_in_mix(precision):
     m = pp()
     systems = _batch_systems()[:6] + [(rgg(40000, 9), synth.rhs_uniform(40000, 9))]

@@ -55,7 +55,7 @@ def problem(name):
     if name == "varcoeff2d_150":
         a = synth.varcoeff2d(150, seed=4)
         return a, synth.rhs_uniform(a.n, 4)
-    if name == "rgg_20k":               # irregular rows: sigma-sorted SELL with a row permutation
+    if name == "rgg_20k":               # irregular row lengths (sorted SELL windows: see below)
         a = synth.rgg_laplacian(20000, (3 * 14.0 / (4 * np.pi * 20000)) ** (1 / 3), 1e-3, 5)
         return a, synth.rhs_uniform(a.n, 5)
     raise KeyError(name)
@@ -73,6 +73,21 @@ def test_fixed_k_parity(name, k, opts):
     x, info = gpu(a, b, tol=0.0, maxit=k, **opts)
     assert info.status == pp().ERR_NOT_CONVERGED and info.iters == k
     assert rel(x, ref["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("sigma", [256, 2048])
+@pytest.mark.parametrize("opts", PATHS, ids=["grid", "cluster"])
+def test_sorted_sell_parity(sigma, opts):
+    """Rows sorted by length inside sigma-row windows: the solver runs on the permuted
+    system and maps b, x0 and x through the permutation."""
+    a, b = problem("rgg_20k")
+    ref = oracle.pipecg(a, b, tol=0.0, maxit=20)
+    x, info = gpu(a, b, tol=0.0, maxit=20, sigma=sigma, **opts)
+    assert info.iters == 20 and rel(x, ref["x"]) <= 1e-10
+    full = oracle.pipecg(a, b, tol=1e-8, maxit=5000)["result"]["iters"]
+    x, info = gpu(a, b, tol=1e-8, maxit=5000, sigma=sigma, **opts)
+    assert info.status == pp().OK and abs(info.iters - full) <= 2
+    assert np.linalg.norm(b - a.to_scipy() @ x) <= 1e-8 * np.linalg.norm(b)
 
 
 @pytest.mark.parametrize("name", ["poisson2d_64", "varcoeff3d_31", "rgg_20k"])
