@@ -38,7 +38,8 @@ SEED = 1
 TOL = 1e-8
 MAXIT = 20000
 SERVE_MAXIT = 200000       # served requests include 2-D stencils of up to 4e6 rows (kappa ~1e7)
-WORKLOAD = ("3D 7-point variable-coefficient diffusion 256^3 (N=16,777,216, nnz=117,047,296), "
+def workload(g, n, nnz):
+    return (f"3D 7-point variable-coefficient diffusion {g}^3 (N={n:,}, nnz={nnz:,}), "
             "log-normal(0,1) face coefficients, Jacobi, b~U[-1,1], x0=0, rel tol 1e-8, FP64 pipelined PCG")
 
 
@@ -347,6 +348,56 @@ def measure_rgg(pp, torch, npts=4_000_000, seed=3):
     return out
 
 
+def measure_paper(pp, torch, batch_count=1024):
+    """The paper's own experimental setting (Sec. VI): stop when sqrt((u, u)) <= 1e-5
+    (absolute, preconditioned), maxit 10000, exact solution x = 1/sqrt(N) (b = A x), x0 = 0,
+    FP64 -- on the 2-D 64^2 Poisson system, the 256^3 diffusion system, the 4M-point RGG
+    Laplacian and the ragged batch."""
+    def one(a, label):
+        xe = np.full(a.n, 1.0 / np.sqrt(a.n))
+        b = torch.from_numpy(a.to_scipy() @ xe).cuda()
+        s = pp.Solver.from_csr(a, norm=pp.NORM_PAPER_U_ABS)
+        x = torch.empty_like(b)
+        s.solve(b, None, x, tol=1e-5, maxit=10000)
+        e0, e1 = _events()
+        e0.record()
+        _, info = s.solve(b, None, x, tol=1e-5, maxit=10000, sync=False)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        err = float(np.linalg.norm(x.cpu().numpy() - xe) / np.linalg.norm(xe))
+        s.close()
+        return {"workload": label, "N": a.n, "nnz": a.nnz, "iters": info.iters, "s": t,
+                "iters_per_s": info.iters / t, "status": pp.status_name(info.status),
+                "u_norm_at_exit": info.rel_res_recursive, "rel_res_true": info.rel_res_true,
+                "err_vs_exact": err}
+    out = {"setting": "sqrt((u,u)) <= 1e-5 absolute, maxit 10000, x_exact = 1/sqrt(N), x0 = 0, FP64"}
+    out["poisson2d_64"] = one(synth.poisson2d(64), "2D 5-point Poisson 64x64")
+    out["varcoeff3d_256"] = one(synth.varcoeff3d(GRID_N, SEED), "3D 7-point log-normal diffusion 256^3")
+    npts = 4_000_000
+    out["rgg_4M"] = one(synth.rgg_laplacian(npts, (3 * 14.0 / (4 * np.pi * npts)) ** (1 / 3), 1e-3, 3),
+                        "RGG Laplacian 4M points + 1e-3 I")
+    systems = [synth.build_spec(sp)[0] for sp in synth.batch_mix(batch_count, 11)]
+    hs = [pp.Solver.from_csr(a, norm=pp.NORM_PAPER_U_ABS, path=pp.PATH_CLUSTER) for a in systems]
+    xes = [np.full(a.n, 1.0 / np.sqrt(a.n)) for a in systems]
+    bs = [torch.from_numpy(a.to_scipy() @ xe).cuda() for a, xe in zip(systems, xes)]
+    xs = [torch.empty_like(b) for b in bs]
+    pp.batch_solve(hs[:2], bs[:2], xs[:2], tol=1e-5, maxit=10000)
+    e0, e1 = _events()
+    e0.record()
+    infos = pp.batch_solve(hs, bs, xs, tol=1e-5, maxit=10000, sync=False)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    errs = [float(np.linalg.norm(x.cpu().numpy() - xe) / np.linalg.norm(xe)) for x, xe in zip(xs, xes)]
+    out["batch"] = {"systems": batch_count, "rows": sum(a.n for a in systems), "s": t,
+                    "iters_total": sum(i.iters for i in infos), "all_ok": all(i.status == pp.OK for i in infos),
+                    "err_vs_exact_max": max(errs), "err_vs_exact_median": float(np.median(errs))}
+    for h in hs:
+        h.close()
+    return out
+
+
 def run_reference(args, ws, rank):
     """Reference arm: the oracle, as it stands, on the host cores (rank 0 only)."""
     if rank != 0:
@@ -369,7 +420,7 @@ def run_reference(args, ws, rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": f"{k} iterations per step incl. setup and final residual"},
+            "config": {"workload": workload(GRID_N, a.n, a.nnz), "sample": f"{k} iterations per step incl. setup and final residual"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{k} iterations of the 256^3 system per step, including setup "
                                        f"(3 SpMV) and the final residual, single-thread plain C"},
@@ -387,9 +438,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the latency, batch and serving figures")
-    ap.add_argument("--mode", default="main", choices=["main", "batch", "serve", "rgg"],
+    ap.add_argument("--mode", default="main", choices=["main", "batch", "serve", "rgg", "paper"],
                     help="batch: the 1024-system ragged batch; serve: the serving rate sweep; "
-                         "rgg: FP32+IR vs FP64 on the 4M-point random geometric graph")
+                         "rgg: FP32 forms vs FP64 on the 4M-point random geometric graph; "
+                         "paper: the paper's stopping rule and exact solution on every config")
     ap.add_argument("--batch-count", type=int, default=1024)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
@@ -402,11 +454,13 @@ def main():
         torch.cuda.set_device(local)
         if args.mode == "rgg":
             res = {"mode": "rgg", "rgg": measure_rgg(pp, torch)}
+        elif args.mode == "paper":
+            res = {"mode": "paper", "paper": measure_paper(pp, torch, args.batch_count)}
         elif args.mode == "batch":
             res = {"mode": "batch", "fp64": measure_batch(pp, torch, args.batch_count),
                    "fp32_ru": measure_batch(pp, torch, args.batch_count, precision=pp.FP32_RU)}
         else:
-            res = {"mode": "serve", "serving": measure_serving(pp, nreq=400, hi=4e6,
+            res = {"mode": "serve", "serving": measure_serving(pp, nreq=2000, hi=4e6,
                                                                rate_factors=(0.25, 0.5, 1.0, 2.0, 4.0))}
         if rank == 0:
             print(json.dumps(res), flush=True)
@@ -507,10 +561,10 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": args.grid, "N": n, "nnz": nnz,
+            "config": {"workload": workload(args.grid, n, nnz), "grid": args.grid, "N": n, "nnz": nnz,
                        "iters_per_solve": iters_per_solve, "format": "SELL-C-sigma C=32",
                        "path": "grid (cooperative persistent kernel)",
-                       "l2": "inputs larger than L2 (3.75 GB streamed per iteration vs 126 MB L2)",
+                       "l2": f"inputs larger than L2 ({bytes_iter / 1e9:.2f} GB streamed per iteration vs 126 MB L2)",
                        "parallelism": f"replicas x{ws}"},
             "e2e": e2e, "roofline": roofline, "clocks": clocks,
             "gpu_launches": 2 * args.steps}

@@ -4,11 +4,14 @@
 //   admitter  -- takes queued requests in arrival order while their device footprint fits
 //                in the HBM budget, builds the handle (CSR -> SELL on the device), stages b
 //                and x0, and hands the resident solve to the executor;
-//   executor  -- runs epochs: every resident CLUSTER-path solve advances by at most
-//                `epoch_iters` iterations inside one persistent cluster launch (their work
-//                overlaps on the device), each GRID-path solve gets one whole-GPU launch of
-//                the same budget; finished solves are copied out, their memory released,
-//                and requests that arrived meanwhile join at the next epoch.
+//   executor  -- runs epochs: every resident CLUSTER-path solve (up to 131,072 rows)
+//                advances inside one persistent cluster launch by its own budget,
+//                epoch_iters * 131072 / n iterations (clamped to [2, 64 epoch_iters]), so
+//                each gets about the same device time and their work overlaps; GRID-path
+//                solves run in arrival order, the two oldest getting a whole-GPU slice of
+//                clamp(2.5e8 / n, 32, 4000) iterations (about 20 ms) per epoch; finished
+//                solves are copied out, their memory released, and requests that arrived
+//                meanwhile join at the next epoch.
 // A solve's vectors, scalars and control block stay on the device between epochs, and its
 // partition over CTAs depends only on its handle, so a result is bitwise the same alone or
 // in any mix.
