@@ -398,6 +398,51 @@ def measure_paper(pp, torch, batch_count=1024):
     return out
 
 
+def measure_box125(pp, torch, sizes=(165, 170, 181, 185), seed=9):
+    """Table II's 125-point box-stencil Poisson family (diag 124, off -1; N = n^3, nnz =
+    (5n - 6)^3, 549M-776M nonzeros): the SpMV-dominated regime.  FP64 and FP32_RU to rel 1e-8
+    from b ~ U[-1, 1]; iterations/s and algorithmic GB/s against the measured HBM peak."""
+    peaks, _ = measured_peaks()
+    out = {"workload": "125-point box stencil n^3 (Table II sizes), diag 124, off -1, b~U[-1,1], x0=0, rel tol 1e-8",
+           "runs": []}
+    for n in sizes:
+        t0 = time.perf_counter()
+        a = synth.box125(n)
+        t_gen = time.perf_counter() - t0
+        b = torch.from_numpy(synth.rhs_uniform(a.n, seed)).cuda()
+        rec = {"n": n, "N": a.n, "nnz": a.nnz, "gen_s": t_gen}
+        x64 = None
+        for name, prec in (("fp64", pp.FP64), ("fp32_ru", pp.FP32_RU)):
+            t0 = time.perf_counter()
+            s = pp.Solver.from_csr(a, precision=prec)
+            torch.cuda.synchronize()
+            t_create = time.perf_counter() - t0
+            x = torch.empty_like(b)
+            s.solve(b, None, x, tol=TOL, maxit=3)                  # first launch
+            e0, e1 = _events()
+            e0.record()
+            _, info = s.solve(b, None, x, tol=TOL, maxit=MAXIT, sync=False)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
+            balg = b_alg(a.n, a.nnz, 8 if prec == pp.FP64 else 4)
+            r = {"s": t, "iters": info.iters, "iters_per_s": info.iters / t, "status": pp.status_name(info.status),
+                 "rel_res_true": info.rel_res_true, "create_s": t_create, "b_alg_per_iter": balg}
+            if prec == pp.FP64:
+                r["achieved_gbs"] = balg * info.iters / t / 1e9
+                r["frac_of_measured_hbm"] = r["achieved_gbs"] / peaks["hbm_gbs"]
+                x64 = x.clone()
+            else:
+                r["speedup_vs_fp64"] = rec["fp64"]["s"] / t
+                r["err_vs_fp64_solution"] = (torch.linalg.norm(x - x64) / torch.linalg.norm(x64)).item()
+            rec[name] = r
+            s.close()
+            del x
+        out["runs"].append(rec)
+        del a, b, x64
+    return out
+
+
 def run_reference(args, ws, rank):
     """Reference arm: the oracle, as it stands, on the host cores (rank 0 only)."""
     if rank != 0:
@@ -438,10 +483,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the latency, batch and serving figures")
-    ap.add_argument("--mode", default="main", choices=["main", "batch", "serve", "rgg", "paper"],
+    ap.add_argument("--mode", default="main", choices=["main", "batch", "serve", "rgg", "paper", "box125"],
                     help="batch: the 1024-system ragged batch; serve: the serving rate sweep; "
                          "rgg: FP32 forms vs FP64 on the 4M-point random geometric graph; "
-                         "paper: the paper's stopping rule and exact solution on every config")
+                         "paper: the paper's stopping rule and exact solution on every config; "
+                         "box125: Table II's 125-point family")
     ap.add_argument("--batch-count", type=int, default=1024)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
@@ -454,6 +500,8 @@ def main():
         torch.cuda.set_device(local)
         if args.mode == "rgg":
             res = {"mode": "rgg", "rgg": measure_rgg(pp, torch)}
+        elif args.mode == "box125":
+            res = {"mode": "box125", "box125": measure_box125(pp, torch)}
         elif args.mode == "paper":
             res = {"mode": "paper", "paper": measure_paper(pp, torch, args.batch_count)}
         elif args.mode == "batch":

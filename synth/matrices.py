@@ -141,14 +141,38 @@ def box125_nnz(n):
     return int(c.sum()) ** 3
 
 
-def box125(n):
+def box125(n, slab=8):
     """125-point box stencil on an n^3 grid: every cell within Chebyshev distance 2,
-    diag 124, off-diag -1 (irreducibly diagonally dominant, so SPD)."""
-    offs = [(dz, dy, dx) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)]
-    centre = offs.index((0, 0, 0))
-    return _stencil((n, n, n), offs,
-                    lambda j, z, y, x: np.full(z.shape, 124.0 if j == centre else -1.0),
-                    f"box125_{n}")
+    diag 124, off-diag -1 (irreducibly diagonally dominant, so SPD).  Built `slab`
+    z-planes at a time straight into arrays of the final size (n = 185 has 776M nonzeros),
+    so the peak host memory is the CSR itself plus one slab of candidates."""
+    offs = np.array([(dz, dy, dx) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)])
+    nnz = box125_nnz(n)
+    N = n ** 3
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    is_diag = np.all(offs == 0, axis=1)
+    pos = 0
+    for z0 in range(0, n, slab):
+        z1 = min(n, z0 + slab)
+        z, y, x = np.meshgrid(np.arange(z0, z1), np.arange(n), np.arange(n), indexing="ij")
+        z, y, x = z.ravel(), y.ravel(), x.ravel()
+        nz_ = z[:, None] + offs[None, :, 0]
+        ny_ = y[:, None] + offs[None, :, 1]
+        nx_ = x[:, None] + offs[None, :, 2]
+        ok = (nz_ >= 0) & (nz_ < n) & (ny_ >= 0) & (ny_ < n) & (nx_ >= 0) & (nx_ < n)
+        # with every coordinate inside [0, n) the (dz, dy, dx) order is ascending column order
+        cols = ((nz_ * n + ny_) * n + nx_)[ok]
+        vals = np.where(np.broadcast_to(is_diag[None, :], ok.shape), 124.0, -1.0)[ok]
+        r0 = z0 * n * n
+        np.cumsum(ok.sum(axis=1), out=row_ptr[r0 + 1:r0 + 1 + ok.shape[0]])
+        row_ptr[r0 + 1:r0 + 1 + ok.shape[0]] += pos
+        col[pos:pos + cols.size] = cols
+        val[pos:pos + vals.size] = vals
+        pos += cols.size
+    assert pos == nnz
+    return CSR(N, row_ptr, col, val, f"box125_{n}")
 
 
 def rgg_laplacian(npts, radius, shift, seed, chunk=1 << 22):

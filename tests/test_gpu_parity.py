@@ -58,6 +58,9 @@ def problem(name):
     if name == "rgg_20k":               # irregular row lengths (sorted SELL windows: see below)
         a = synth.rgg_laplacian(20000, (3 * 14.0 / (4 * np.pi * 20000)) ** (1 / 3), 1e-3, 5)
         return a, synth.rhs_uniform(a.n, 5)
+    if name == "box125_12":             # Table II structure: 124 off-diagonals per interior row
+        a = synth.box125(12)
+        return a, synth.rhs_uniform(a.n, 6)
     raise KeyError(name)
 
 
@@ -65,7 +68,7 @@ PATHS = [dict(path=1), dict(path=2)]      # GRID, CLUSTER
 
 
 @pytest.mark.parametrize("name,k", [("poisson2d_64", 50), ("varcoeff3d_31", 20), ("varcoeff2d_150", 30),
-                                    ("rgg_20k", 20)])
+                                    ("rgg_20k", 20), ("box125_12", 15)])
 @pytest.mark.parametrize("opts", PATHS, ids=["grid", "cluster"])
 def test_fixed_k_parity(name, k, opts):
     a, b = problem(name)
@@ -90,7 +93,7 @@ def test_sorted_sell_parity(sigma, opts):
     assert np.linalg.norm(b - a.to_scipy() @ x) <= 1e-8 * np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("name", ["poisson2d_64", "varcoeff3d_31", "rgg_20k"])
+@pytest.mark.parametrize("name", ["poisson2d_64", "varcoeff3d_31", "rgg_20k", "box125_12"])
 @pytest.mark.parametrize("opts", PATHS, ids=["grid", "cluster"])
 def test_full_solve_parity(name, opts):
     a, b = problem(name)

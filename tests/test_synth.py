@@ -59,6 +59,21 @@ def test_box125_structure(n):
     assert (A.diagonal() == 124).all()
 
 
+@pytest.mark.parametrize("n,slab", [(3, 1), (4, 3), (6, 8), (7, 2)])
+def test_box125_matches_brute_force(n, slab):
+    """Every pair of cells within Chebyshev distance 2 is an entry (124 on the diagonal,
+    -1 off it), and the slab-wise construction does not depend on the slab height."""
+    a = synth.box125(n, slab=slab)
+    N = n ** 3
+    idx = np.arange(N)
+    zyx = np.stack([idx // (n * n), (idx // n) % n, idx % n], axis=1)
+    cheb = np.abs(zyx[:, None, :] - zyx[None, :, :]).max(axis=2)
+    expect = np.where(cheb <= 2, -1.0, 0.0)
+    np.fill_diagonal(expect, 124.0)
+    assert np.array_equal(a.dense(), expect)
+    assert np.all(np.diff(a.col[a.row_ptr[0]:a.row_ptr[1]]) > 0)
+
+
 def test_box125_reproduces_table2():
     for name, N, nnz in _rows("table2_poisson125.txt"):
         n = round(int(N) ** (1 / 3))
