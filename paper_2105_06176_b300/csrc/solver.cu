@@ -296,6 +296,30 @@ __device__ __forceinline__ void row_dot2(const int32_t* __restrict__ col, const 
   }
 }
 
+// L2 prefetch of the lines chunk c will read (its vector tile and its matrix slots), issued
+// one chunk ahead by the warp that will process it: the lines are in flight while the warp
+// works on its current chunk, at no register cost.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+template <typename T, int NS>
+__device__ __forceinline__ void prefetch_chunk(const int64_t* __restrict__ cptr, const int32_t* __restrict__ col,
+                                               const T* __restrict__ val, const T* blk, int32_t c, int lane) {
+  constexpr int kTileBytes = NS * kChunk * (int)sizeof(T);
+  const char* tile = reinterpret_cast<const char*>(blk + (int64_t)c * NS * kChunk);
+  for (int off = lane * 128; off < kTileBytes; off += 32 * 128) prefetch_l2(tile + off);
+  const int64_t b0 = __ldg(cptr + c), b1 = __ldg(cptr + c + 1);
+  const char* pc = reinterpret_cast<const char*>(col + b0);
+  const char* pv = reinterpret_cast<const char*>(val + b0);
+  const int nc = (int)((b1 - b0) * 4), nv = (int)((b1 - b0) * (int64_t)sizeof(T));
+  for (int off = lane * 128; off < nc; off += 32 * 128) prefetch_l2(pc + off);
+  for (int off = lane * 128; off < nv; off += 32 * 128) prefetch_l2(pv + off);
+}
+
+#ifndef PPCG_PREFETCH
+#define PPCG_PREFETCH 1
+#endif
+
 // Vector slots.  FP64 block (NS 10): r u wa wb z q s p x invd.  FP32 block (NS 11):
 // r u wa wb z q s p d invd rhs (d: inner solution).  FP32_IR keeps its FP64 outer residual
 // and solution in slots r and x of the FP64 block.
@@ -396,6 +420,11 @@ __device__ __forceinline__ void pass_iter(const DevMatrix& A, const View<T, NS>&
   const T* __restrict__ val = V.val;
   const int32_t n = (int32_t)A.n;
   FOR_CHUNKS(A, L) {
+    // FP32 only: the FP32 pass is latency-bound (half the bytes in flight of FP64 at the
+    // same occupancy), 433 -> 350 us per 256^3 iteration; the FP64 pass, already near the
+    // HBM and FP64-pipe limits, ran 10-20% slower with it.
+    if (PPCG_PREFETCH && sizeof(T) == 4 && c + L.W < (int32_t)A.nchunks)
+      prefetch_chunk<T, NS>(A.cptr, col, val, V.v.b, c + L.W, L.lane);
     int64_t base; int len;
     chunk_slots(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
@@ -621,6 +650,8 @@ __device__ __forceinline__ void pass_rr2(const DevMatrix& A, const View<T, NS>& 
   const GatherSlot<T, NS> gr{V.v.b + V_R * kChunk};
   const GatherSlot<T, NS> gs{V.v.b + V_S * kChunk};
   FOR_CHUNKS(A, L) {
+    if (PPCG_PREFETCH && sizeof(T) == 4 && c + L.W < (int32_t)A.nchunks)
+      prefetch_chunk<T, NS>(A.cptr, A.col, V.val, V.v.b, c + L.W, L.lane);
     int64_t base; int len;
     chunk_slots(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
