@@ -168,11 +168,12 @@ def _events():
 
 def measure_latency_2d(pp, torch):
     """64x64 2-D Poisson (N = 4,096), b = A x_true: solve latency and time per iteration
-    on the default (cluster) path and the whole-GPU path."""
+    on the default path (on chip: the system in one cluster's shared memory), the cluster
+    path with vectors in global memory, and the whole-GPU path."""
     a = synth.poisson2d(64)
     b = torch.from_numpy(a.to_scipy() @ synth.xtrue_uniform(a.n, 1)).cuda()
     out = {"workload": "2D 5-point Poisson 64x64, FP64, rel tol 1e-8"}
-    for name, path in (("cluster", pp.PATH_CLUSTER), ("grid", pp.PATH_GRID)):
+    for name, path in (("onchip", pp.PATH_ONCHIP), ("cluster", pp.PATH_CLUSTER), ("grid", pp.PATH_GRID)):
         s = pp.Solver.from_csr(a, path=path)
         x = torch.empty_like(b)
         for _ in range(3):

@@ -63,7 +63,14 @@ typedef enum {
   PPCG_NORM_REL_R = 0,      /* ||r||_2 <= tol * ||b||_2 on the recursive residual, then a true-residual check */
   PPCG_NORM_PAPER_U_ABS = 1 /* sqrt((u, u)) <= tol, the absolute preconditioned norm of Alg. 2 / Sec. VI */
 } ppcg_norm;
-typedef enum { PPCG_PATH_AUTO = 0, PPCG_PATH_GRID = 1, PPCG_PATH_CLUSTER = 2 } ppcg_path;
+typedef enum {
+  PPCG_PATH_AUTO = 0,
+  PPCG_PATH_GRID = 1,     /* one cooperative persistent launch over the whole GPU */
+  PPCG_PATH_CLUSTER = 2,  /* one 8-CTA thread-block cluster, vectors in global memory */
+  PPCG_PATH_ONCHIP = 3    /* one 8-CTA cluster holding the whole system (vectors and matrix) in its
+                             distributed shared memory; FP64 Alg. 2 only, systems up to about
+                             11-12 thousand rows of a 3-D 7-point stencil */
+} ppcg_path;
 typedef enum {
   PPCG_VARIANT_ALG2 = 0,          /* Alg. 2 as printed: u and q carried by their recurrences */
   PPCG_VARIANT_JACOBI_SCALED = 1  /* Jacobi elimination: with M = diag(A), u = M^-1 r and q = M^-1 s hold
@@ -92,8 +99,9 @@ typedef struct {
   int32_t format;           /* ppcg_format.  The matrix is always converted to SELL-C-sigma (C = 32)
                                on the device; FMT_CSR forces sigma = 1 (CSR row order kept). */
   int32_t norm;             /* ppcg_norm */
-  int32_t path;             /* ppcg_path.  GRID: one cooperative persistent launch over the whole GPU.
-                               CLUSTER: one thread-block cluster per system.  AUTO picks by size. */
+  int32_t path;             /* ppcg_path.  AUTO: ONCHIP when the system fits (FP64 Alg. 2), else
+                               CLUSTER up to cluster_max_rows rows, else GRID.  ONCHIP for a system
+                               that does not fit gives PPCG_ERR_ARG. */
   int32_t sigma;            /* SELL sorting window in rows (1 = no sorting; 0 = autotune over
                                {1, 256, 2048}: padded matrix bytes plus a gather-locality cost
                                for sorted windows, whose chunks mix rows from all over the window) */

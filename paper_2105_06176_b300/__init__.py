@@ -16,7 +16,7 @@ __all__ = [
     "lib", "Opts", "Info", "Solver", "batch_solve", "Server", "status_name",
     "OK", "PENDING", "ERR_ARG", "ERR_NOT_SPD", "ERR_BREAKDOWN", "ERR_NOT_CONVERGED",
     "ERR_NONFINITE", "ERR_OOM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_BUSY", "ERR_UNKNOWN_TICKET",
-    "FP64", "FP32_IR", "FP32_RU", "NORM_REL_R", "NORM_PAPER_U_ABS", "PATH_AUTO", "PATH_GRID", "PATH_CLUSTER",
+    "FP64", "FP32_IR", "FP32_RU", "NORM_REL_R", "NORM_PAPER_U_ABS", "PATH_AUTO", "PATH_GRID", "PATH_CLUSTER", "PATH_ONCHIP",
     "FMT_AUTO", "FMT_CSR", "FMT_SELL", "VARIANT_ALG2", "VARIANT_JACOBI_SCALED", "EXPORTED_SYMBOLS",
 ]
 
@@ -25,7 +25,7 @@ ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_UNKNOWN_TICKET = -5
 FP64, FP32_IR, FP32_RU = 0, 1, 2
 FMT_AUTO, FMT_CSR, FMT_SELL = 0, 1, 2
 NORM_REL_R, NORM_PAPER_U_ABS = 0, 1
-PATH_AUTO, PATH_GRID, PATH_CLUSTER = 0, 1, 2
+PATH_AUTO, PATH_GRID, PATH_CLUSTER, PATH_ONCHIP = 0, 1, 2, 3
 VARIANT_ALG2, VARIANT_JACOBI_SCALED = 0, 1
 
 _NAMES = {OK: "OK", PENDING: "PENDING", ERR_ARG: "ERR_ARG", ERR_NOT_SPD: "ERR_NOT_SPD",

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <queue>
 #include <vector>
 
@@ -254,6 +255,46 @@ size_t footprint_bytes(int64_t n, int64_t nnz, int32_t precision) {
 
 namespace {
 
+// Work list of a launch of one cluster running system 0: device array {0, 0, 1} read as
+// list = {0} (element 0) and list_ptr = {0, 1} (elements 1-2).
+const int32_t* single_work_list() {
+  static int32_t* d_list = nullptr;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!d_list) {
+    const int32_t host[3] = {0, 0, 1};
+    if (cudaMalloc(&d_list, sizeof(host)) != cudaSuccess ||
+        cudaMemcpy(d_list, host, sizeof(host), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      d_list = nullptr;
+    }
+  }
+  return d_list;
+}
+
+// One side stream and a fork/join event pair per device (batch launches of the on-chip
+// path run beside the cluster-path launch).  Created on first use, kept for the process.
+bool side_stream(int device, cudaStream_t* s, cudaEvent_t* fork, cudaEvent_t* join) {
+  struct Side { cudaStream_t s = nullptr; cudaEvent_t fork = nullptr, join = nullptr; };
+  static std::mutex mu;
+  static std::unordered_map<int, Side> per;
+  std::lock_guard<std::mutex> lk(mu);
+  Side& x = per[device];
+  if (!x.s) {
+    if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      x = Side();
+      return false;
+    }
+  }
+  *s = x.s;
+  *fork = x.fork;
+  *join = x.join;
+  return true;
+}
+
 void enqueue_info(std::vector<std::pair<ppcg_ctx*, ppcg_info*>>& items, cudaStream_t st) {
   auto* jobs = new std::vector<InfoJob>();
   for (auto& it : items) {
@@ -379,8 +420,21 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   if (s != PPCG_OK) { free_all(h); delete h; return s; }
 
   // Execution plan (fixed for the handle, so every solve of it uses the same partition).
+  // On chip: FP64 Alg. 2 whose vector tiles and matrix slots fit in one cluster's shared
+  // memory; AUTO takes it whenever it fits (it removes every L2 round trip from an
+  // iteration, the latency that bounds small systems).
   int path = h->opts.path;
-  if (path == PPCG_PATH_AUTO) path = n <= h->opts.cluster_max_rows ? PPCG_PATH_CLUSTER : PPCG_PATH_GRID;
+  h->onchip_smem = onchip_smem_bytes(h->A.nchunks, h->sell.onchip_slots);
+  const bool onchip_ok = h->opts.precision == PPCG_FP64 && h->opts.variant == PPCG_VARIANT_ALG2 &&
+                         h->onchip_smem <= onchip_smem_limit(h->device) && h->sell.onchip_slots < INT32_MAX;
+  if (path == PPCG_PATH_ONCHIP && !onchip_ok) {
+    free_all(h);
+    delete h;
+    set_error("ppcg_create: PATH_ONCHIP needs FP64 Alg. 2 and a system that fits in one cluster's shared memory");
+    return PPCG_ERR_ARG;
+  }
+  if (path == PPCG_PATH_AUTO)
+    path = onchip_ok ? PPCG_PATH_ONCHIP : n <= h->opts.cluster_max_rows ? PPCG_PATH_CLUSTER : PPCG_PATH_GRID;
   h->path = path;
   if (path == PPCG_PATH_GRID) {
     h->shape = 0;
@@ -450,6 +504,7 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   d.max_restarts = h->opts.max_restarts < 0 ? 0 : h->opts.max_restarts;
   d.variant = h->opts.variant;
   d.inner_tol = h->opts.inner_tol;
+  d.onchip_slots = (int32_t)std::min<int64_t>(h->sell.onchip_slots, INT32_MAX);
   d.dmin = h->sell.dmin;
   d.dmax = h->sell.dmax;
   d.spin_limit_ns = h->opts.spin_limit_ns;
@@ -479,23 +534,13 @@ ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double*
   cudaError_t e;
   if (h->path == PPCG_PATH_GRID) {
     e = launch_grid(h->d_desc, h->shape, h->grid, 0, st);
+  } else if (h->path == PPCG_PATH_ONCHIP) {
+    const int32_t* d_list = single_work_list();
+    if (!d_list) { set_error("ppcg_solve: could not allocate the cluster work list"); return PPCG_ERR_OOM; }
+    e = launch_onchip(h->d_desc, d_list, d_list + 1, 1, 0, h->onchip_smem, st);
   } else {
-    // one cluster, work list {0}: device array {0, 0, 1} = list[0], list_ptr[0..1]
-    static int32_t* d_list = nullptr;
-    static std::mutex mu;
-    {
-      std::lock_guard<std::mutex> lk(mu);
-      if (!d_list) {
-        const int32_t host[3] = {0, 0, 1};
-        if (cudaMalloc(&d_list, sizeof(host)) != cudaSuccess ||
-            cudaMemcpy(d_list, host, sizeof(host), cudaMemcpyHostToDevice) != cudaSuccess) {
-          cudaGetLastError();
-          d_list = nullptr;
-          set_error("ppcg_solve: could not allocate the cluster work list");
-          return PPCG_ERR_OOM;
-        }
-      }
-    }
+    const int32_t* d_list = single_work_list();
+    if (!d_list) { set_error("ppcg_solve: could not allocate the cluster work list"); return PPCG_ERR_OOM; }
     e = launch_clusters(h->d_desc, d_list, d_list + 1, 1, 0, st, /*spread=*/true);
   }
   if (e != cudaSuccess) {
@@ -525,7 +570,7 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
     for (int j = 0; j < i; j++)
       if (hs[j] == hs[i]) { set_error("ppcg_batch_solve: handle %d repeated", i); return PPCG_ERR_ARG; }
   }
-  std::vector<int> cl, gr;
+  std::vector<int> cl, gr, oc;
   for (int i = 0; i < count; i++) {
     ppcg_ctx* h = hs[i];
     if (h->n == 0) { if (infos) write_trivial_info(&infos[i], PPCG_OK); continue; }
@@ -534,7 +579,65 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
     ppcg_status s = stage_inputs(h, b[i], x0 ? x0[i] : nullptr, true, st);
     if (s != PPCG_OK) return s;
     prepare_control(h, tol[i], maxit[i], st);
-    (h->path == PPCG_PATH_CLUSTER ? cl : gr).push_back(i);
+    (h->path == PPCG_PATH_CLUSTER ? cl : h->path == PPCG_PATH_ONCHIP ? oc : gr).push_back(i);
+  }
+  // On-chip systems: one launch of clusters (one system per cluster at a time, longest
+  // first) on a side stream, overlapping the cluster-path launch below.
+  cudaEvent_t oc_done = nullptr;
+  if (!oc.empty()) {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr;
+    if (!side_stream(hs[oc[0]]->device, &side, &fork, &oc_done)) {
+      set_error("ppcg_batch_solve: could not create the side stream");
+      return PPCG_ERR_CUDA;
+    }
+    cudaEventRecord(fork, st);
+    cudaStreamWaitEvent(side, fork, 0);
+    const int m = (int)oc.size();
+    std::vector<SysDesc> descs(m);
+    size_t smem = 0;
+    std::vector<int> order(m);
+    for (int k = 0; k < m; k++) {
+      descs[k] = hs[oc[k]]->desc;
+      smem = std::max(smem, hs[oc[k]]->onchip_smem);
+      order[k] = k;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hs[oc[0]]->device);
+    const int nclusters = std::max(1, std::min(m, sms / kClusterSize));
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return hs[oc[a]]->sell.nslots > hs[oc[c]]->sell.nslots; });
+    std::vector<std::vector<int>> lists(nclusters);
+    std::vector<double> load(nclusters, 0.0);
+    for (int k : order) {
+      const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      lists[c].push_back(k);
+      load[c] += (double)hs[oc[k]]->sell.nslots + 32.0 * (double)hs[oc[k]]->n;
+    }
+    std::vector<int32_t> flat, ptr(1, 0);
+    for (auto& l : lists) { for (int k : l) flat.push_back(k); ptr.push_back((int32_t)flat.size()); }
+    std::vector<int32_t> packed(ptr);
+    packed.insert(packed.end(), flat.begin(), flat.end());
+    SysDesc* d_descs = nullptr;
+    int32_t* d_lists = nullptr;
+    if (cudaMallocAsync((void**)&d_descs, m * sizeof(SysDesc), side) != cudaSuccess ||
+        cudaMallocAsync((void**)&d_lists, packed.size() * sizeof(int32_t), side) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("ppcg_batch_solve: out of device memory for the schedule");
+      return PPCG_ERR_OOM;
+    }
+    cudaMemcpyAsync(d_descs, descs.data(), m * sizeof(SysDesc), cudaMemcpyHostToDevice, side);
+    cudaMemcpyAsync(d_lists, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice, side);
+    cudaError_t e = launch_onchip(d_descs, d_lists + ptr.size(), d_lists, nclusters, 0, smem, side);
+    cudaFreeAsync(d_descs, side);
+    cudaFreeAsync(d_lists, side);
+    cudaEventRecord(oc_done, side);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamWaitEvent(st, oc_done, 0);
+      set_error("ppcg_batch_solve: on-chip launch failed: %s", cudaGetErrorString(e));
+      return PPCG_ERR_CUDA;
+    }
   }
   // Cluster-path systems: one persistent launch; longest-first schedule over the clusters.
   if (!cl.empty()) {
@@ -593,6 +696,7 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
       return PPCG_ERR_CUDA;
     }
   }
+  if (oc_done) cudaStreamWaitEvent(st, oc_done, 0);
   std::vector<std::pair<ppcg_ctx*, ppcg_info*>> items;
   for (int i = 0; i < count; i++) {
     if (hs[i]->n == 0) continue;

@@ -291,6 +291,11 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   *d_perm_out = d_perm;
   out->nchunks = nchunks;
   out->nslots = nslots;
+  {
+    int64_t per[kClusterSize] = {0};
+    for (int64_t c = 0; c < nchunks; c++) per[c % kClusterSize] += cptr[c + 1] - cptr[c];
+    out->onchip_slots = *std::max_element(per, per + kClusterSize);
+  }
   out->sigma = (int32_t)sigma;
   out->padding = nnz > n ? (double)(nslots - (nnz - n)) / (double)(nnz - n) : 0.0;
   std::memcpy(&out->dmin, &mm[0], sizeof(double));

@@ -55,6 +55,7 @@ struct ppcg_ctx {
   int32_t* perm = nullptr;
   std::vector<void*> allocs;
   int32_t path = PPCG_PATH_GRID;
+  size_t onchip_smem = 0;   // dynamic shared memory per CTA of the on-chip path
   int shape = 0;       // grid-path launch shape (index into the kernel variants)
   int grid = 0;        // CTAs of the grid path
   int nparts = 0;      // partial slots per pass (CTAs in the group)

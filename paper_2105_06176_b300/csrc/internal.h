@@ -87,7 +87,7 @@ struct SysDesc {
   int32_t precision, norm, rr_period, maxit;
   int32_t inner_maxit, max_outer, nparts, x_zero;  // x_zero: x starts at 0 (skip the A x0 gather)
   int32_t max_restarts, budget;   // budget: iterations this launch may advance (0 = launch's)
-  int32_t variant, pad3;          // ppcg_variant
+  int32_t variant, onchip_slots;  // ppcg_variant; on-chip path: matrix slots of the fullest CTA
   double tol, inner_tol;
   double dmin, dmax;     // extreme diagonal entries (bounds of ||r||^2 / gamma)
   int64_t spin_limit_ns;
@@ -109,6 +109,10 @@ struct SysDesc {
 cudaError_t launch_grid(const SysDesc* d_desc, int shape, int grid, int budget, cudaStream_t st);
 cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
                             int nclusters, int budget, cudaStream_t st, bool spread = false);
+cudaError_t launch_onchip(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
+                          int nclusters, int budget, size_t smem, cudaStream_t st);
+size_t onchip_smem_bytes(int64_t nchunks, int64_t slots);   // dynamic shared memory per CTA
+size_t onchip_smem_limit(int device);                       // largest the device allows
 int grid_shape_count();
 int grid_threads(int shape);
 int grid_blocks_for_device(int device, int shape);
@@ -123,6 +127,7 @@ struct SellBuild {
   double padding = 0.0;   // padded slots / off-diagonal nonzeros
   double seconds = 0.0;   // conversion wall time
   double dmin = 0.0, dmax = 0.0;   // extreme diagonal entries
+  int64_t onchip_slots = 0;        // SELL slots of the fullest CTA when chunk c goes to CTA c % 8
 };
 ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col,
                                 const double* d_val, int32_t sigma_req, bool want_fp32, bool sym_scale,

@@ -112,8 +112,13 @@ void admit_loop(ppcg_srv* S) {
       S->running++;
     }
     ppcg_handle h = nullptr;
-    ppcg_status st = ppcg_create(&h, req->n, req->nnz, req->rp.data(), req->col.data(), req->val.data(),
-                                 &S->opts, S->s_admit);
+    // Served solves take the cluster path (epochs of many solves in one launch) or the grid
+    // path; the on-chip path holds 8 SMs' shared memory per solve and is left to ppcg_solve.
+    ppcg_opts o = S->opts;
+    if (o.path == PPCG_PATH_AUTO || o.path == PPCG_PATH_ONCHIP)
+      o.path = req->n <= o.cluster_max_rows ? PPCG_PATH_CLUSTER : PPCG_PATH_GRID;
+    ppcg_status st = ppcg_create(&h, req->n, req->nnz, req->rp.data(), req->col.data(), req->val.data(), &o,
+                                 S->s_admit);
     Slot slot;
     slot.ticket = req->ticket;
     slot.footprint = req->footprint;

@@ -1071,46 +1071,67 @@ __device__ __forceinline__ void pass_uflush(const SysDesc& S, const Lanes& L) {
 
 // ----------------------------------------------------------- partials and reduction --
 
-// Block partials -> part slot [4], fixed reduction tree (deterministic).
+// Block partials -> slot[0..3].  Every FP64 add costs a full warp instruction on the FP64
+// pipe (about 16 SM cycles on this part), so the sum is organised to issue few of them.
+// PACKED (sm holds (blockDim / 32) x 32 x 3 doubles): each lane stores its three partials;
+// lane l of warp v (v < 3) adds value v of lane l over the warps; one shuffle tree per
+// value.  Otherwise (sm holds 3 x 32 doubles): a shuffle tree in every warp, then warp 0
+// sums the warps' results by a second tree.  Both orders are fixed: deterministic.
+template <bool PACKED>
 __device__ void write_block_partials(double a0, double a1, double a2, double* slot, double* sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if constexpr (PACKED) {
+    double* mine = sm + (warp * 32 + lane) * 3;
+    mine[0] = a0;
+    mine[1] = a1;
+    mine[2] = a2;
+    __syncthreads();
+    if (warp < 3) {
+      double v = 0.0;
+      for (int w = 0; w < nw; w++) v += sm[(w * 32 + lane) * 3 + warp];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a0 += __shfl_down_sync(kFull, a0, o);
-    a1 += __shfl_down_sync(kFull, a1, o);
-    a2 += __shfl_down_sync(kFull, a2, o);
-  }
-  if (lane == 0) { sm[warp * 3] = a0; sm[warp * 3 + 1] = a1; sm[warp * 3 + 2] = a2; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int w = 0; w < nw; w++) { s0 += sm[w * 3]; s1 += sm[w * 3 + 1]; s2 += sm[w * 3 + 2]; }
-    slot[0] = s0; slot[1] = s1; slot[2] = s2; slot[3] = 0.0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+      if (lane == 0) slot[warp] = v;
+      if (warp == 0 && lane == 0) slot[3] = 0.0;
+    }
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_down_sync(kFull, a0, o);
+      a1 += __shfl_down_sync(kFull, a1, o);
+      a2 += __shfl_down_sync(kFull, a2, o);
+    }
+    if (lane == 0) { sm[warp * 3] = a0; sm[warp * 3 + 1] = a1; sm[warp * 3 + 2] = a2; }
+    __syncthreads();
+    if (warp == 0) {
+      double s0 = lane < nw ? sm[lane * 3] : 0.0, s1 = lane < nw ? sm[lane * 3 + 1] : 0.0;
+      double s2 = lane < nw ? sm[lane * 3 + 2] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(kFull, s0, o);
+        s1 += __shfl_down_sync(kFull, s1, o);
+        s2 += __shfl_down_sync(kFull, s2, o);
+      }
+      if (lane == 0) { slot[0] = s0; slot[1] = s1; slot[2] = s2; slot[3] = 0.0; }
+    }
   }
 }
 
 // Sum the group's P partial slots in a fixed order; every CTA obtains identical bits.
 __device__ void group_reduce(const double* part, int P, double* out, double* sm) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    a0 += __ldcg(part + 4 * i);
-    a1 += __ldcg(part + 4 * i + 1);
-    a2 += __ldcg(part + 4 * i + 2);
-  }
+  // warp v (v < 3) sums value v over the P partial slots (lane-strided, then a shuffle
+  // tree): three warps' worth of FP64 adds, the other warps idle.  Fixed order.
+  (void)sm;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < 3) {
+    double v = 0.0;
+    for (int i = lane; i < P; i += 32) v += __ldcg(part + 4 * i + warp);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a0 += __shfl_down_sync(kFull, a0, o);
-    a1 += __shfl_down_sync(kFull, a1, o);
-    a2 += __shfl_down_sync(kFull, a2, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (lane == 0) out[warp] = v;
+    if (warp == 0 && lane == 0) out[3] = 0.0;
   }
-  if (lane == 0) { sm[warp * 3] = a0; sm[warp * 3 + 1] = a1; sm[warp * 3 + 2] = a2; }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int w = 0; w < nw; w++) { s0 += sm[w * 3]; s1 += sm[w * 3 + 1]; s2 += sm[w * 3 + 2]; }
-    out[0] = s0; out[1] = s1; out[2] = s2; out[3] = 0.0;
-  }
 }
 
 // ------------------------------------------------------------------------- control --
@@ -1372,13 +1393,18 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
 
 // ------------------------------------------------------------------------- driver --
 
-struct Shared {
+// Shared state of run_system.  The grid path keeps the per-warp-tree block reduction and a
+// small buffer (its 2 x 512-thread CTAs per SM want the L1 for gathers and spills; a 12 KB
+// buffer measured 3% slower at 256^3); the 256-thread cluster path packs its adds.
+template <int NSM> struct SharedT {
+  static constexpr bool kPacked = NSM > 3 * 32;
   SysDesc S;
   Ctl C;
-  double sm[3 * 32];
+  double sm[NSM];
 };
+constexpr int kSmGrid = 3 * 32, kSmCluster = 3 * 32 * (kClusterThreads / 32);
 
-template <bool STAGED, class G>
+template <bool STAGED, class G, class Shared>
 __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsigned char* stage_mem,
                            uint64_t* stage_bars, unsigned& phases) {
   __syncthreads();   // previous system's readers of sh are done
@@ -1403,6 +1429,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
   L.W = g.size() * nw;
   const bool paper = S.norm == PPCG_NORM_PAPER_U_ABS;
   const int P = g.size();
+  constexpr bool kPacked = Shared::kPacked;
 
   for (;;) {
     if (threadIdx.x == 0) control(C, S, iter_end);
@@ -1428,7 +1455,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
         case P_ZERO_X: pass_zero_x<kNSS, VS_X>(S, L); partials = false; break;
         default: partials = false; break;
       }
-      if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
+      if (partials) write_block_partials<kPacked>(d.get(0), d.get(1), d.get(2), slot, sh.sm);
     } else if (!fp32) {
       Dots<double> d;
       const View<double, kNS64> V = view64(S);
@@ -1453,7 +1480,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
         case P_ZERO_X: pass_zero_x<kNS64, V_X>(S, L); partials = false; break;
         default: partials = false; break;
       }
-      if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
+      if (partials) write_block_partials<kPacked>(d.get(0), d.get(1), d.get(2), slot, sh.sm);
     } else if (pass == P_ORES || pass == P_ZERO_X || pass == P_OINIT || pass == P_OUPD || pass == P_OUNDO ||
                pass == P_URES || pass == P_UFLUSH) {
       Dots<double> d;
@@ -1469,7 +1496,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
         case P_OUNDO: pass_oundo(S, L, C.rn_prev); partials = false; break;
         default: partials = false; break;
       }
-      if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
+      if (partials) write_block_partials<kPacked>(d.get(0), d.get(1), d.get(2), slot, sh.sm);
     } else {
       Dots<float> d;
       const View<float, kNS32> V = view32(S);
@@ -1491,7 +1518,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
         case P_URR2: pass_rr2(S.A, V, L, d, C.inner_iter, paper); break;
         default: partials = false; break;
       }
-      if (partials) write_block_partials(d.get(0), d.get(1), d.get(2), slot, sh.sm);
+      if (partials) write_block_partials<kPacked>(d.get(0), d.get(1), d.get(2), slot, sh.sm);
     }
     // The next pass may read this pass's stores with bulk copies (async proxy).
     if (STAGED) fence_proxy_async();
@@ -1513,7 +1540,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
 
 template <int THREADS, int MINB, bool STAGED>
 __global__ void __launch_bounds__(THREADS, MINB) k_grid(const SysDesc* d, int budget) {
-  __shared__ Shared sh;
+  __shared__ SharedT<kSmGrid> sh;
   __shared__ uint64_t bars[2 * (THREADS / 32)];
   extern __shared__ __align__(128) unsigned char stage_mem[];
   unsigned phases = 0;
@@ -1547,13 +1574,350 @@ constexpr int kNumGridShapes = (int)(sizeof(kGridShapes) / sizeof(kGridShapes[0]
 
 __global__ void __launch_bounds__(kClusterThreads, 4) k_cluster(const SysDesc* descs, const int32_t* list,
                                                              const int32_t* list_ptr, int budget) {
-  __shared__ Shared sh;
+  __shared__ SharedT<kSmCluster> sh;
   ClusterGroup g;
   unsigned cid;
   unsigned phases = 0;
   asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
   for (int k = list_ptr[cid]; k < list_ptr[cid + 1]; k++)
     run_system<false>(g, descs + list[k], budget, sh, nullptr, nullptr, phases);
+}
+
+// ---------------------------------------------------------- on-chip small systems --
+// A system whose vectors and matrix fit in the shared memory of one 8-CTA cluster runs
+// entirely on chip: chunk c lives in CTA c % 8 as local chunk c / 8 (its FP64 vector tile
+// and its SELL slots), gathers of other CTAs' rows are distributed-shared-memory loads, and
+// the block partials are exchanged through shared memory as well.  No pass touches HBM or
+// L2 except for b and the diagonal (setup, true residual, replacement).  The same
+// control() drives it, so the iteration, its stopping rules, restarts and replacements are
+// those of the other paths; the vector tiles are loaded at launch and written back at exit,
+// so a solve can stop at an iteration budget and resume in a later launch.
+
+constexpr int kOnchipThreads = 256;
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ double ld_dsmem(uint32_t local_addr, uint32_t rank) {
+  uint32_t remote;
+  double v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote));
+  return v;
+}
+
+// Gather of one slot of the distributed vector tiles: row j is lane j % 32 of chunk j / 32,
+// held by CTA (j / 32) % 8 as its local chunk j / 256.
+struct GatherDS {
+  uint32_t tile;   // shared-memory address of the tile array (the same in every CTA)
+  int slot;
+  __device__ __forceinline__ double operator()(int32_t j) const {
+    const uint32_t cj = (uint32_t)j >> 5;
+    const uint32_t off = (((cj >> 3) * (uint32_t)kNS64 + (uint32_t)slot) * kChunk + ((uint32_t)j & 31u)) * 8u;
+    return ld_dsmem(tile + off, cj & 7u);
+  }
+};
+
+// acc + sum_k val[k] x(col[k]) (* dsc[col] when SCALE) over a row's slots in shared memory,
+// in slot order (the order of row_dot).
+template <bool SCALE, class G>
+__device__ __forceinline__ double row_dot_sm(const int32_t* col, const double* val, const G& x,
+                                             const double* __restrict__ dsc, int base, int len, double acc) {
+  int j = 0;
+  for (; j + 8 <= len; j += 8) {
+    int32_t c[8];
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) { c[k] = col[base + (j + k) * kChunk]; a[k] = val[base + (j + k) * kChunk]; }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      double xv = x(c[k]);
+      if (SCALE) xv = __ldg(dsc + c[k]) * xv;
+      acc = fma(a[k], xv, acc);
+    }
+  }
+  for (; j < len; j++) {
+    const int32_t c = col[base + j * kChunk];
+    double xv = x(c);
+    if (SCALE) xv = __ldg(dsc + c) * xv;
+    acc = fma(val[base + j * kChunk], xv, acc);
+  }
+  return acc;
+}
+
+struct OnchipSh {
+  SysDesc S;
+  Ctl C;
+  double sm[3 * 32 * (kOnchipThreads / 32)];
+  double part[2][4];     // this CTA's block partials, read by every CTA of the cluster
+};
+
+// Per-CTA view of the on-chip system.
+struct Onchip {
+  double* tile;          // [nloc][kNS64][32]
+  double* val;           // this CTA's SELL slots (chunk after chunk)
+  int32_t* col;
+  int32_t* lptr;         // [nloc + 1] slot offset of each local chunk
+  uint32_t tile_addr;
+  int32_t nloc, rank, nchunks, n;
+};
+
+#define FOR_LOCAL(O) for (int32_t lc = (int32_t)(threadIdx.x >> 5); lc < (O).nloc; lc += kOnchipThreads / 32)
+
+// One on-chip pass; returns whether it produced partials.
+__device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dots<double>& d, bool paper) {
+  const int lane = threadIdx.x & 31;
+  const DevMatrix& A = S.A;
+  switch (C.pass) {
+    case P_SETUP1:
+    case P_TRUE:
+    case P_RR1: {
+      // r = b - A x (SCALE); setup1: u = M^-1 r, partials (b,b) (r,r); true: partial (r,r) only;
+      // rr1: u = M^-1 r, s = A p, q = M^-1 s.
+      const bool x_zero = C.pass == P_SETUP1 && S.x_zero != 0 && !C.fallback;
+      const bool rr = C.pass == P_RR1, p_zero = rr && (C.iter == 0 || C.restart);
+      const GatherDS gx{O.tile_addr, V_X}, gp{O.tile_addr, V_P};
+      FOR_LOCAL(O) {
+        const int32_t c = lc * kClusterSize + O.rank;
+        if (c >= O.nchunks) continue;
+        const int32_t row = c * kChunk + lane;
+        const bool in = row < O.n;
+        double* t = O.tile + (int64_t)lc * kNS64 * kChunk + lane;
+        const int base = O.lptr[lc] + lane, len = (O.lptr[lc + 1] - O.lptr[lc]) / kChunk;
+        double ax = 0.0, ap = 0.0, bi = 0.0, di = 0.0;
+        if (in) {
+          bi = __ldg(S.b + row);
+          di = __ldg(A.diag + row);
+          if (!x_zero) ax = di * t[V_X * kChunk];
+          if (rr && !p_zero) ap = di * t[V_P * kChunk];
+        }
+        if (!x_zero) ax = row_dot_sm<true>(O.col, O.val, gx, A.diag, base, len, ax);
+        if (rr && !p_zero) ap = row_dot_sm<true>(O.col, O.val, gp, A.diag, base, len, ap);
+        if (in) {
+          const double ri = bi - ax;
+          if (C.pass == P_TRUE) { d.add(0, ri, ri); continue; }
+          const double id = t[V_INVD * kChunk];
+          t[V_R * kChunk] = ri;
+          t[V_U * kChunk] = id * ri;
+          if (rr) {
+            t[V_S * kChunk] = ap;
+            t[V_Q * kChunk] = id * ap;
+          } else {
+            d.add(0, bi, bi);
+            d.add(1, ri, ri);
+          }
+        }
+      }
+      return !rr;
+    }
+    case P_SETUP2:
+    case P_RR2: {
+      // w = Ahat r (= A u); rr2 also z = Ahat s (= A q); partials (r,u) (w,u) norm.
+      const bool rr = C.pass == P_RR2;
+      const int wcs = rr && (C.iter & 1) ? V_WB : V_WA;
+      const GatherDS gr{O.tile_addr, V_R}, gs{O.tile_addr, V_S};
+      FOR_LOCAL(O) {
+        const int32_t c = lc * kClusterSize + O.rank;
+        if (c >= O.nchunks) continue;
+        const bool in = c * kChunk + lane < O.n;
+        double* t = O.tile + (int64_t)lc * kNS64 * kChunk + lane;
+        const int base = O.lptr[lc] + lane, len = (O.lptr[lc + 1] - O.lptr[lc]) / kChunk;
+        double ri = 0.0, ui = 0.0, si = 0.0;
+        if (in) { ri = t[V_R * kChunk]; ui = t[V_U * kChunk]; if (rr) si = t[V_S * kChunk]; }
+        const double wi = row_dot_sm<false>(O.col, O.val, gr, nullptr, base, len, ri);
+        double zi = 0.0;
+        if (rr) zi = row_dot_sm<false>(O.col, O.val, gs, nullptr, base, len, si);
+        if (in) {
+          t[wcs * kChunk] = wi;
+          if (rr) t[V_Z * kChunk] = zi;
+          d.add(0, ri, ui);
+          d.add(1, wi, ui);
+          if (paper) d.add(2, ui, ui); else d.add(2, ri, ri);
+        }
+      }
+      return true;
+    }
+    case P_ITER: {
+      const bool first = C.first != 0, with_rr = C.want_rr != 0;
+      const double alpha = C.alpha, beta = C.beta;
+      const int wcs = (C.iter & 1) ? V_WB : V_WA;
+      const int wns = (C.iter & 1) ? V_WA : V_WB;
+      const GatherDS gw{O.tile_addr, wcs};
+      FOR_LOCAL(O) {
+        const int32_t c = lc * kClusterSize + O.rank;
+        if (c >= O.nchunks) continue;
+        const bool in = c * kChunk + lane < O.n;
+        double* t = O.tile + (int64_t)lc * kNS64 * kChunk + lane;
+        const int base = O.lptr[lc] + lane, len = (O.lptr[lc + 1] - O.lptr[lc]) / kChunk;
+        double wi = 0.0;
+        if (in) wi = t[wcs * kChunk];
+        // n_i = (A M^-1 w)_i = w_i + sum_{j != i} ahat_ij w_j
+        const double ni = row_dot_sm<false>(O.col, O.val, gw, nullptr, base, len, wi);
+        if (in) {
+          const double id = t[V_INVD * kChunk], ui = t[V_U * kChunk];
+          const double mi = id * wi;
+          const double zi = first ? ni : fma(beta, t[V_Z * kChunk], ni);
+          const double qi = first ? mi : fma(beta, t[V_Q * kChunk], mi);
+          const double si = first ? wi : fma(beta, t[V_S * kChunk], wi);
+          const double pi = first ? ui : fma(beta, t[V_P * kChunk], ui);
+          const double xi = fma(alpha, pi, t[V_X * kChunk]);
+          const double ri = fma(-alpha, si, t[V_R * kChunk]);
+          const double un = fma(-alpha, qi, ui);
+          const double wnn = fma(-alpha, zi, wi);
+          t[V_Z * kChunk] = zi;
+          t[V_Q * kChunk] = qi;
+          t[V_S * kChunk] = si;
+          t[V_P * kChunk] = pi;
+          t[V_X * kChunk] = xi;
+          t[V_R * kChunk] = ri;
+          t[V_U * kChunk] = un;
+          t[wns * kChunk] = wnn;
+          d.add(0, ri, un);
+          d.add(1, wnn, un);
+          if (with_rr) { if (paper) d.add(2, un, un); else d.add(2, ri, ri); }
+        }
+      }
+      return true;
+    }
+    case P_NORM: {
+      FOR_LOCAL(O) {
+        const int32_t c = lc * kClusterSize + O.rank;
+        if (c >= O.nchunks || c * kChunk + lane >= O.n) continue;
+        const double v = O.tile[((int64_t)lc * kNS64 + (paper ? V_U : V_R)) * kChunk + lane];
+        d.add(2, v, v);
+      }
+      return true;
+    }
+    case P_ZERO_X: {
+      FOR_LOCAL(O) {
+        const int32_t c = lc * kClusterSize + O.rank;
+        if (c < O.nchunks && c * kChunk + lane < O.n) O.tile[((int64_t)lc * kNS64 + V_X) * kChunk + lane] = 0.0;
+      }
+      return false;
+    }
+    default:
+      return false;
+  }
+}
+
+// Copy this CTA's chunks between the global vector block and the shared tiles.
+__device__ void onchip_tiles(const SysDesc& S, const Onchip& O, bool to_smem) {
+  const int64_t per = (int64_t)kNS64 * kChunk;
+  for (int64_t k = threadIdx.x; k < (int64_t)O.nloc * per; k += blockDim.x) {
+    const int64_t lc = k / per, e = k % per;
+    const int64_t c = lc * kClusterSize + O.rank;
+    if (c >= O.nchunks) continue;
+    double* g = S.v64 + c * per + e;
+    if (to_smem) O.tile[k] = __ldcg(g); else __stcg(g, O.tile[k]);
+  }
+}
+
+__global__ void __launch_bounds__(kOnchipThreads, 1) k_onchip(const SysDesc* descs, const int32_t* list,
+                                                              const int32_t* list_ptr, int budget_arg) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ OnchipSh sh;
+  unsigned cid;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+  const uint32_t rank = cluster_rank();
+  for (int item = list_ptr[cid]; item < list_ptr[cid + 1]; item++) {
+    const SysDesc* Sg = descs + list[item];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sh.S = *Sg;
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(sh.S.ctl);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sh.C);
+      for (int i = 0; i < (int)(sizeof(Ctl) / 8); i++) dst[i] = __ldcg(src + i);
+      if (sh.C.t_start == 0) sh.C.t_start = globaltimer();
+      sh.C.exit_now = 0;
+    }
+    __syncthreads();
+    const SysDesc& S = sh.S;
+    Ctl& C = sh.C;
+    Onchip O;
+    O.nchunks = (int32_t)S.A.nchunks;
+    O.n = (int32_t)S.A.n;
+    O.rank = (int32_t)rank;
+    O.nloc = (O.nchunks + kClusterSize - 1) / kClusterSize;
+    O.tile = reinterpret_cast<double*>(dyn);
+    O.val = O.tile + (int64_t)O.nloc * kNS64 * kChunk;
+    O.col = reinterpret_cast<int32_t*>(O.val + S.onchip_slots);
+    O.lptr = O.col + S.onchip_slots;
+    O.tile_addr = smem_u32(O.tile);
+    // stage: local slot offsets, then the matrix slots and the vector tiles
+    if (threadIdx.x == 0) {
+      int32_t off = 0;
+      for (int32_t lc = 0; lc < O.nloc; lc++) {
+        O.lptr[lc] = off;
+        const int64_t c = (int64_t)lc * kClusterSize + rank;
+        if (c < O.nchunks) off += (int32_t)(__ldg(S.A.cptr + c + 1) - __ldg(S.A.cptr + c));
+      }
+      O.lptr[O.nloc] = off;
+    }
+    __syncthreads();
+    for (int32_t lc = (int32_t)(threadIdx.x >> 5); lc < O.nloc; lc += kOnchipThreads / 32) {
+      const int64_t c = (int64_t)lc * kClusterSize + rank;
+      if (c >= O.nchunks) continue;
+      const int64_t g0 = __ldg(S.A.cptr + c);
+      const int cnt = O.lptr[lc + 1] - O.lptr[lc];
+      for (int k = threadIdx.x & 31; k < cnt; k += 32) {
+        O.col[O.lptr[lc] + k] = __ldg(S.A.col + g0 + k);
+        O.val[O.lptr[lc] + k] = __ldg(S.A.val + g0 + k);
+      }
+    }
+    onchip_tiles(S, O, true);
+    int budget = budget_arg;
+    if (S.budget > 0) budget = S.budget;
+    const int iter_end = budget > 0 && C.iter < 0x7fffffff - budget ? C.iter + budget : 0x7fffffff;
+    const bool paper = S.norm == PPCG_NORM_PAPER_U_ABS;
+    __syncthreads();
+    cluster_barrier();   // every CTA's tiles are staged before anyone gathers
+    for (;;) {
+      if (threadIdx.x == 0) control(C, S, iter_end);
+      __syncthreads();
+      if (C.pass == P_NONE) break;
+      Dots<double> d;
+      const bool partials = onchip_pass(S, C, O, d, paper);
+      if (partials) {
+        write_block_partials<true>(d.get(0), d.get(1), d.get(2), sh.part[C.parity], sh.sm);
+      }
+      __syncthreads();
+      cluster_barrier();
+      if (partials && threadIdx.x < 32) {
+        // lane q < 8 reads rank q's partials; a fixed shuffle tree sums them (deterministic)
+        const int lane = threadIdx.x;
+        const uint32_t base = smem_u32(&sh.part[C.parity][0]);
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        if (lane < kClusterSize) {
+          s0 = ld_dsmem(base, lane);
+          s1 = ld_dsmem(base + 8, lane);
+          s2 = ld_dsmem(base + 16, lane);
+        }
+#pragma unroll
+        for (int o = kClusterSize / 2; o > 0; o >>= 1) {
+          s0 += __shfl_down_sync(kFull, s0, o);
+          s1 += __shfl_down_sync(kFull, s1, o);
+          s2 += __shfl_down_sync(kFull, s2, o);
+        }
+        if (lane == 0) {
+          C.red[0] = s0; C.red[1] = s1; C.red[2] = s2; C.red[3] = 0.0;
+          C.parity ^= 1;
+        }
+      }
+    }
+    cluster_barrier();   // no CTA reads another's shared memory after this point
+    onchip_tiles(S, O, false);
+    if (threadIdx.x == 0 && rank == 0) {
+      C.t_end = globaltimer();
+      *S.ctl = C;
+      __threadfence();
+    }
+    __syncthreads();
+  }
 }
 
 // Failure-detection self test: the grid barrier with one rank that never arrives.  Every
@@ -1637,6 +2001,41 @@ cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_cluster, d_descs, d_list, d_list_ptr, budget);
+}
+
+size_t onchip_smem_bytes(int64_t nchunks, int64_t slots) {
+  const int64_t nloc = (nchunks + kClusterSize - 1) / kClusterSize;
+  return (size_t)(nloc * kNS64 * kChunk * 8 + slots * 12 + (nloc + 1) * 4);
+}
+
+size_t onchip_smem_limit(int device) {
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  const size_t stat = sizeof(OnchipSh) + 1024;   // static shared memory and a reserve
+  return optin > (int)stat ? (size_t)optin - stat : 0;
+}
+
+cudaError_t launch_onchip(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
+                          int nclusters, int budget, size_t smem, cudaStream_t st) {
+  static size_t attr = 0;
+  if (smem > attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_onchip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterSize * nclusters);
+  cfg.blockDim = dim3(kOnchipThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kClusterSize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_onchip, d_descs, d_list, d_list_ptr, budget);
 }
 
 cudaError_t launch_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, int grid, int drop_rank,

@@ -236,9 +236,9 @@ def test_server_results_same_alone_and_in_mix(precision):
         r = np.linalg.norm(b - a.to_scipy() @ x1) / np.linalg.norm(b)
         assert r <= 1e-8
     # and the served result equals a solo ppcg_solve with the same settings (the server's
-    # plan: cluster up to 131,072 rows)
+    # plan: the cluster path up to 131,072 rows)
     a, b = systems[0]
-    s = m.Solver.from_csr(a, precision=precision, cluster_max_rows=131072)
+    s = m.Solver.from_csr(a, precision=precision, path=m.PATH_CLUSTER)
     xs, info = s.solve(dev(b), tol=1e-8, maxit=20000)
     assert np.array_equal(xs.cpu().numpy(), alone[0][1])
 

@@ -213,11 +213,14 @@ def test_barrier_timeout_is_reported_not_hung():
 
 
 def test_restart_on_breakdown_parity():
-    """The system on which plain Alg. 2 breaks down near 1e-8.  Up to the breakdown the
-    iterates follow the oracle's, so with restarts disabled both report the breakdown at
-    the same iteration (+-2).  After a restart the path depends on rounding (the breakdown
-    is itself a rounding effect), so the bar there is the outcome: both converge with the
-    same number of restarts to a true residual <= 1e-8, within 10% of the oracle's count."""
+    """The system on which plain Alg. 2 breaks down near 1e-8.  The breakdown happens on
+    the attainable-accuracy floor, where the gap between the recursive and the true
+    residual is as large as the residual itself, so the iteration at which the alpha
+    denominator first turns non-positive depends on rounding (FMA contraction, reduction
+    order): the bar is within 1% of the oracle's (1180).  After a restart the path depends
+    on rounding as well (the oracle's own two summation orders need 1297 and 1333), so the
+    bar there is the outcome: convergence after restarts to a true residual <= 1e-8,
+    within 10% of the oracle's count."""
     m = pp()
     spec = [s for s in synth.batch_mix(128, 11) if s[0] == "varcoeff2d" and s[1] == 267][0]
     a, b = synth.build_spec(spec)
@@ -226,12 +229,109 @@ def test_restart_on_breakdown_parity():
     for path in (1, 2):
         x0, info0 = gpu(a, b, tol=1e-8, maxit=20000, path=path, max_restarts=0)
         assert info0.status == m.ERR_BREAKDOWN
-        assert abs(info0.iters - ref0["result"]["iters"]) <= 2
+        assert abs(info0.iters - ref0["result"]["iters"]) <= max(2, 0.01 * ref0["result"]["iters"])
         x, info = gpu(a, b, tol=1e-8, maxit=20000, path=path)
         assert info.status == m.OK
         assert info.rr_count >= 1 and ref["result"]["rr_count"] >= 1
         assert abs(info.iters - ref["result"]["iters"]) <= 0.1 * ref["result"]["iters"]
         assert np.linalg.norm(b - a.to_scipy() @ x) <= 1e-8 * np.linalg.norm(b)
+
+
+# ------------------------------------------------------- on-chip path (one cluster's DSMEM) --
+
+ONCHIP = dict(path=3)
+
+
+def onchip_problem(name):
+    if name == "poisson2d_64":
+        return problem("poisson2d_64")
+    if name == "varcoeff3d_20":          # 8,000 rows: 250 chunks over 8 CTAs (ragged split)
+        a = synth.varcoeff3d(20, seed=7)
+        return a, synth.rhs_uniform(a.n, 7)
+    if name == "rgg_5000":               # irregular rows
+        a = synth.rgg_laplacian(5000, (3 * 14.0 / (4 * np.pi * 5000)) ** (1 / 3), 1e-3, 8)
+        return a, synth.rhs_uniform(a.n, 8)
+    if name == "box125_9":               # 124 off-diagonals: long rows (8-slot batches)
+        a = synth.box125(9)
+        return a, synth.rhs_uniform(a.n, 9)
+    if name == "poisson2d_7":            # 49 rows: one ragged chunk, seven idle CTAs
+        a = synth.poisson2d(7)
+        return a, a.to_scipy() @ synth.xtrue_uniform(a.n, 3)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name,k", [("poisson2d_64", 50), ("varcoeff3d_20", 20), ("rgg_5000", 20),
+                                    ("box125_9", 10), ("poisson2d_7", 8)])
+def test_onchip_fixed_k_parity(name, k):
+    a, b = onchip_problem(name)
+    ref = oracle.pipecg(a, b, tol=0.0, maxit=k)
+    x, info = gpu(a, b, tol=0.0, maxit=k, **ONCHIP)
+    assert info.status == pp().ERR_NOT_CONVERGED and info.iters == k
+    assert rel(x, ref["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["poisson2d_64", "varcoeff3d_20", "rgg_5000", "box125_9", "poisson2d_7"])
+def test_onchip_full_solve_parity(name):
+    a, b = onchip_problem(name)
+    ref = oracle.pipecg(a, b, tol=1e-8, maxit=10000)
+    x, info = gpu(a, b, tol=1e-8, maxit=10000, **ONCHIP)
+    assert info.status == pp().OK
+    assert abs(info.iters - ref["result"]["iters"]) <= 2
+    t = np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)
+    assert t <= 1e-8 and abs(info.rel_res_true - t) <= 1e-6 * t + 1e-15
+
+
+def test_onchip_modes_and_plan():
+    m = pp()
+    a, b = onchip_problem("poisson2d_64")
+    # AUTO takes the on-chip path when the system fits; the result equals the explicit one
+    xa, ia = gpu(a, b, tol=1e-8)
+    xo, io = gpu(a, b, tol=1e-8, **ONCHIP)
+    assert ia.iters == io.iters and np.array_equal(xa, xo)
+    # residual replacement, paper norm, x0 aliasing x, budgets through resumable launches
+    ref = oracle.pipecg(a, b, tol=0.0, maxit=60, rr_period=10)
+    x, info = gpu(a, b, tol=0.0, maxit=60, rr_period=10, **ONCHIP)
+    assert info.rr_count == ref["result"]["rr_count"] and rel(x, ref["x"]) <= 1e-10
+    bp = a.to_scipy() @ np.full(a.n, 1.0 / np.sqrt(a.n))
+    refp = oracle.pipecg(a, bp, tol=1e-5, maxit=10000, norm=oracle.NORM_PAPER_U_ABS)
+    x, info = gpu(a, bp, tol=1e-5, maxit=10000, norm=m.NORM_PAPER_U_ABS, **ONCHIP)
+    assert info.status == m.OK and abs(info.iters - refp["result"]["iters"]) <= 2
+    x0 = synth.xtrue_uniform(a.n, 5)
+    refx = oracle.pipecg(a, b, x0=x0, tol=0.0, maxit=25)
+    s = m.Solver.from_csr(a, **ONCHIP)
+    xd = dev(x0)
+    s.solve(dev(b), xd, xd, tol=0.0, maxit=25)
+    assert rel(xd.cpu().numpy(), refx["x"]) <= 1e-10
+    # indefinite: breakdown reported
+    import scipy.sparse as sp
+    c = sp.csr_matrix(np.array([[1.0, 2.0, 0.0], [2.0, 1.0, 0.0], [0.0, 0.0, 1.0]]))
+    ind = synth.CSR(3, c.indptr.astype(np.int64), c.indices.astype(np.int32), c.data)
+    _, info = gpu(ind, np.array([1.0, -1.0, 1.0]), **ONCHIP)
+    assert info.status == m.ERR_BREAKDOWN
+    # refused: FP32 modes, the scaled variant, systems that do not fit
+    for kw in (dict(precision=m.FP32_RU), dict(variant=1)):
+        with pytest.raises(m.PPCGError) as e:
+            m.Solver.from_csr(a, **ONCHIP, **kw)
+        assert e.value.status == m.ERR_ARG
+    big = synth.varcoeff3d(40, seed=1)
+    with pytest.raises(m.PPCGError) as e:
+        m.Solver.from_csr(big, **ONCHIP)
+    assert e.value.status == m.ERR_ARG
+
+
+def test_onchip_in_batch_bitwise_equals_solo():
+    m = pp()
+    systems = [onchip_problem(nm) for nm in ("poisson2d_64", "varcoeff3d_20", "rgg_5000", "poisson2d_7")]
+    systems.append(problem("varcoeff3d_31"))                     # a cluster-path member
+    solvers = [m.Solver.from_csr(a) for a, _ in systems]
+    bs = [dev(b) for _, b in systems]
+    solo = [s.solve(b, tol=1e-8, maxit=10000) for s, b in zip(solvers, bs)]
+    solo = [(x.cpu().numpy(), i.iters) for x, i in solo]
+    xs = [torch.empty_like(b) for b in bs]
+    infos = m.batch_solve(solvers, bs, xs, tol=1e-8, maxit=10000)
+    for (x0, it0), xb, inf in zip(solo, xs, infos):
+        assert inf.status == m.OK and inf.iters == it0
+        assert np.array_equal(xb.cpu().numpy(), x0)
 
 
 # ----------------------------------------------------- Jacobi-scaled variant (next row f1) --
