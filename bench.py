@@ -303,6 +303,8 @@ def measure_serving(pp, nreq=160, hi=2e5, seed=5, rate_factors=(0.5,)):
         seq_ok &= info.status == pp.OK
         s.close()
     seq = len(reqs) / (time.perf_counter() - t0)
+    print(json.dumps({"progress": {"saturation_solves_per_s": sat, "sequential_fp64_solves_per_s": seq}}),
+          file=sys.stderr, flush=True)
     out = {"requests": nreq, "size_range": [1e3, hi], "precision": "fp32_ru", "saturation_solves_per_s": sat,
            "sequential_fp64_solves_per_s": seq, "speedup_vs_sequential_fp64": sat / seq,
            "all_ok": all(s == pp.OK for s in st) and seq_ok, "rates": []}
@@ -315,6 +317,7 @@ def measure_serving(pp, nreq=160, hi=2e5, seed=5, rate_factors=(0.5,)):
         out["rates"].append({"rate_factor": f, "offered_per_s": rate, "solves_per_s": len(reqs) / wall,
                              "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                              "all_ok": all(s == pp.OK for s in st)})
+        print(json.dumps({"progress": out["rates"][-1]}), file=sys.stderr, flush=True)
     return out
 
 
