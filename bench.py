@@ -487,11 +487,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the latency, batch and serving figures")
-    ap.add_argument("--mode", default="main", choices=["main", "batch", "serve", "rgg", "paper", "box125"],
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ru", "fp32_ir"],
+                    help="precision of the main line's timed solver (the headline is fp64; the "
+                         "others exist to profile the FP32 kernels on the same workload)")
+    ap.add_argument("--mode", default="main",
+                    choices=["main", "batch", "serve", "rgg", "paper", "box125", "latency"],
                     help="batch: the 1024-system ragged batch; serve: the serving rate sweep; "
                          "rgg: FP32 forms vs FP64 on the 4M-point random geometric graph; "
                          "paper: the paper's stopping rule and exact solution on every config; "
-                         "box125: Table II's 125-point family")
+                         "box125: Table II's 125-point family; latency: the 64^2 solve latency")
     ap.add_argument("--batch-count", type=int, default=1024)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
@@ -508,6 +512,8 @@ def main():
             res = {"mode": "box125", "box125": measure_box125(pp, torch)}
         elif args.mode == "paper":
             res = {"mode": "paper", "paper": measure_paper(pp, torch, args.batch_count)}
+        elif args.mode == "latency":
+            res = {"mode": "latency", "latency_2d64": measure_latency_2d(pp, torch)}
         elif args.mode == "batch":
             res = {"mode": "batch", "fp64": measure_batch(pp, torch, args.batch_count),
                    "fp32_ru": measure_batch(pp, torch, args.batch_count, precision=pp.FP32_RU)}
@@ -534,7 +540,8 @@ def main():
     a = synth.varcoeff3d(args.grid, SEED)
     b = synth.rhs_uniform(a.n, SEED)
     n, nnz = a.n, a.nnz
-    solver = pp.Solver.from_csr(a)
+    prec = {"fp64": pp.FP64, "fp32_ru": pp.FP32_RU, "fp32_ir": pp.FP32_IR}[args.precision]
+    solver = pp.Solver.from_csr(a, precision=prec)
     b_d = torch.from_numpy(b).cuda()
     x_d = torch.empty(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -597,11 +604,15 @@ def main():
 
     # roofline of the solve kernel (one launch = one step)
     peaks, peak_kind = measured_peaks()
-    bytes_iter = b_alg(n, nnz, 8)
+    # (FP32 modes: B_alg of an FP32 iteration; the FP64 reliable updates are not counted)
+    bytes_iter = b_alg(n, nnz, 8 if prec == pp.FP64 else 4)
     per_launch_s = float(np.mean(step_s))
     achieved = bytes_iter * (iters / len(infos)) / per_launch_s / 1e9
     kernel_s = float(np.mean([i.seconds for i in infos]))
-    traffic, traffic_src = profiled_traffic(bytes_iter, iters / len(infos))
+    if prec == pp.FP64:
+        traffic, traffic_src = profiled_traffic(bytes_iter, iters / len(infos))
+    else:
+        traffic, traffic_src = None, "captured for the FP64 solve only"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_src,
                 "peak_kind": peak_kind,
@@ -612,14 +623,16 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == pp.FP64 else "f32+f64",
+            "data": "synthetic",
             "config": {"workload": workload(args.grid, n, nnz), "grid": args.grid, "N": n, "nnz": nnz,
+                       "precision": args.precision,
                        "iters_per_solve": iters_per_solve, "format": "SELL-C-sigma C=32",
                        "path": "grid (cooperative persistent kernel)",
                        "l2": f"inputs larger than L2 ({bytes_iter / 1e9:.2f} GB streamed per iteration vs 126 MB L2)",
                        "parallelism": f"replicas x{ws}"},
             "e2e": e2e, "roofline": roofline, "clocks": clocks,
-            "gpu_launches": 2 * args.steps}
+            "gpu_launches": 4 * args.steps}   # per solve: x0 fill, control init, k_grid, x copy-out
 
     if not args.no_mixed:
         # FP32 recurrences with FP64 reliable updates (the mixed-precision form), and FP32

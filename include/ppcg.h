@@ -157,7 +157,8 @@ void ppcg_opts_default(ppcg_opts* opts);
  *   that stream before returning, so the handle is ready to use on any stream.
  * The matrix is validated (monotone row_ptr, columns in range), the Jacobi diagonal
  * extracted (missing or non-positive -> PPCG_ERR_NOT_SPD), and the values pre-scaled
- * column-wise to A D^-1 and converted to SELL-C-sigma on the device.
+ * column-wise to A D^-1 and converted to SELL-C-sigma on the device.  The execution path
+ * (opts->path) is fixed here for every later solve of the handle.
  * Errors: PPCG_ERR_ARG, PPCG_ERR_NOT_SPD, PPCG_ERR_OOM, PPCG_ERR_CUDA; *handle is then NULL.
  */
 ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64_t* row_ptr,
@@ -182,7 +183,8 @@ ppcg_status ppcg_solve(ppcg_handle handle, const double* b, const double* x0, do
  * Solve count independent systems, each with its own handle, in as few launches as the
  * handles' paths allow: every CLUSTER-path system runs inside one persistent launch of
  * thread-block clusters (a host-side longest-first schedule spreads them over the
- * clusters); GRID-path systems run one after another over the whole GPU.
+ * clusters); ONCHIP-path systems run in one launch of on-chip clusters on a side stream,
+ * overlapping it; GRID-path systems run one after another over the whole GPU.
  * b[i], x0[i] (or NULL, or x0 == NULL for all zero), x[i]: DEVICE pointers.
  * tol[i], maxit[i] per system; infos[count] host array or NULL.
  * Each result is bitwise identical to ppcg_solve on the same handle: a system's
@@ -204,8 +206,9 @@ void ppcg_destroy(ppcg_handle handle);
  * that arrive while others run join at the next epoch.  opts may be NULL.  With
  * opts->path == PPCG_PATH_AUTO and the default cluster_max_rows, requests of up to 131,072
  * rows run on the CLUSTER path (all of them share one launch per epoch) and larger ones on
- * the GRID path (the two oldest advance each epoch by a slice of about 20 ms).  A solve's
- * result equals ppcg_solve on a handle created with the same options and cluster_max_rows.
+ * the GRID path (the two oldest advance each epoch by a slice of about 20 ms); the ONCHIP
+ * path is not used by the server.  A solve's result equals ppcg_solve on a handle created
+ * with the same options and that path.
  */
 ppcg_status ppcg_server_create(ppcg_server* server, size_t hbm_budget, const ppcg_opts* opts);
 

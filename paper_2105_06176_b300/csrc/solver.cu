@@ -40,6 +40,7 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 // Whole-grid group (cooperative launch: all CTAs are co-resident).  The barrier is a
 // monotone arrival counter zeroed before the launch; each wait is bounded in time.
 struct GridGroup {
+  static constexpr bool kCluster = false;
   unsigned* bar;
   int32_t* err;
   long long limit_ns;
@@ -78,7 +79,26 @@ struct GridGroup {
 
 // One thread-block cluster.  barrier.cluster with release/acquire orders the global
 // writes of each pass before the next pass's gathers (which use ld.global.cg, L2).
+// Distributed shared memory of a thread-block cluster.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ double ld_dsmem(uint32_t local_addr, uint32_t rank) {
+  uint32_t remote;
+  double v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote));
+  return v;
+}
+
 struct ClusterGroup {
+  static constexpr bool kCluster = true;
   __device__ int rank() const {
     unsigned r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -1401,7 +1421,31 @@ template <int NSM> struct SharedT {
   SysDesc S;
   Ctl C;
   double sm[NSM];
+  double part[2][4];   // cluster path: this CTA's block partials, read by the whole cluster
 };
+
+// Cluster path: the cluster's block partials, read from every CTA's shared memory by lanes
+// 0-7 of warp 0 and summed by a fixed shuffle tree (deterministic).  out is written by
+// thread 0.
+__device__ __forceinline__ void cluster_reduce(const double* part, double* out) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const uint32_t base = smem_addr(part);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    if (lane < kClusterSize) {
+      s0 = ld_dsmem(base, lane);
+      s1 = ld_dsmem(base + 8, lane);
+      s2 = ld_dsmem(base + 16, lane);
+    }
+#pragma unroll
+    for (int o = kClusterSize / 2; o > 0; o >>= 1) {
+      s0 += __shfl_down_sync(kFull, s0, o);
+      s1 += __shfl_down_sync(kFull, s1, o);
+      s2 += __shfl_down_sync(kFull, s2, o);
+    }
+    if (lane == 0) { out[0] = s0; out[1] = s1; out[2] = s2; out[3] = 0.0; }
+  }
+}
 constexpr int kSmGrid = 3 * 32, kSmCluster = 3 * 32 * (kClusterThreads / 32);
 
 template <bool STAGED, class G, class Shared>
@@ -1437,7 +1481,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
     const int pass = C.pass;
     if (pass == P_NONE) break;
     const bool fp32 = S.precision != PPCG_FP64 && (C.state >= S_O_START);
-    double* slot = S.part + ((size_t)C.parity * P + g.rank()) * 4;
+    double* slot = G::kCluster ? &sh.part[C.parity][0] : S.part + ((size_t)C.parity * P + g.rank()) * 4;
     bool partials = true;
     if (!fp32 && S.variant == PPCG_VARIANT_JACOBI_SCALED) {
       Dots<double> d;
@@ -1527,9 +1571,15 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
       break;
     }
     if (partials) {
-      group_reduce(S.part + (size_t)C.parity * P * 4, P, C.red, sh.sm);
+      if constexpr (G::kCluster) cluster_reduce(sh.part[C.parity], C.red);
+      else group_reduce(S.part + (size_t)C.parity * P * 4, P, C.red, sh.sm);
       if (threadIdx.x == 0) C.parity ^= 1;
     }
+  }
+  if constexpr (G::kCluster) {
+    // other CTAs may still read this CTA's partials; the next system (or the exit) waits
+    __syncthreads();
+    cluster_barrier();
   }
   if (threadIdx.x == 0 && g.rank() == 0) {
     C.t_end = globaltimer();
@@ -1595,21 +1645,6 @@ __global__ void __launch_bounds__(kClusterThreads, 4) k_cluster(const SysDesc* d
 
 constexpr int kOnchipThreads = 256;
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_barrier() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ double ld_dsmem(uint32_t local_addr, uint32_t rank) {
-  uint32_t remote;
-  double v;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote));
-  return v;
-}
 
 // Gather of one slot of the distributed vector tiles: row j is lane j % 32 of chunk j / 32,
 // held by CTA (j / 32) % 8 as its local chunk j / 256.
