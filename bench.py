@@ -404,8 +404,9 @@ def measure_paper(pp, torch, batch_count=1024):
 
 def measure_box125(pp, torch, sizes=(165, 170, 181, 185), seed=9):
     """Table II's 125-point box-stencil Poisson family (diag 124, off -1; N = n^3, nnz =
-    (5n - 6)^3, 549M-776M nonzeros): the SpMV-dominated regime.  FP64 and FP32_RU to rel 1e-8
-    from b ~ U[-1, 1]; iterations/s and algorithmic GB/s against the measured HBM peak."""
+    (5n - 6)^3, 549M-776M nonzeros): the SpMV-dominated regime.  FP64 with the SELL matrix,
+    FP64 matrix-free (axis-wise box sums, no matrix stream) and FP32_RU with the SELL matrix,
+    to rel 1e-8 from b ~ U[-1, 1]; iterations/s and GB/s against the measured HBM peak."""
     peaks, _ = measured_peaks()
     out = {"workload": "125-point box stencil n^3 (Table II sizes), diag 124, off -1, b~U[-1,1], x0=0, rel tol 1e-8",
            "runs": []}
@@ -416,9 +417,10 @@ def measure_box125(pp, torch, sizes=(165, 170, 181, 185), seed=9):
         b = torch.from_numpy(synth.rhs_uniform(a.n, seed)).cuda()
         rec = {"n": n, "N": a.n, "nnz": a.nnz, "gen_s": t_gen}
         x64 = None
-        for name, prec in (("fp64", pp.FP64), ("fp32_ru", pp.FP32_RU)):
+        for name, prec, fmt in (("fp64", pp.FP64, pp.FMT_SELL), ("fp64_matrix_free", pp.FP64, pp.FMT_BOX),
+                                ("fp32_ru", pp.FP32_RU, pp.FMT_SELL)):
             t0 = time.perf_counter()
-            s = pp.Solver.from_csr(a, precision=prec)
+            s = pp.Solver.from_csr(a, precision=prec, format=fmt, path=pp.PATH_GRID)
             torch.cuda.synchronize()
             t_create = time.perf_counter() - t0
             x = torch.empty_like(b)
@@ -429,15 +431,17 @@ def measure_box125(pp, torch, sizes=(165, 170, 181, 185), seed=9):
             e1.record()
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1) * 1e-3
-            balg = b_alg(a.n, a.nnz, 8 if prec == pp.FP64 else 4)
+            # bytes per iteration: B_alg for the SELL plans; 21 v N (17 vector streams and the
+            # two stage arrays) for the matrix-free plan (info.bytes_per_iter is the library's)
+            balg = info.bytes_per_iter
             r = {"s": t, "iters": info.iters, "iters_per_s": info.iters / t, "status": pp.status_name(info.status),
-                 "rel_res_true": info.rel_res_true, "create_s": t_create, "b_alg_per_iter": balg}
-            if prec == pp.FP64:
-                r["achieved_gbs"] = balg * info.iters / t / 1e9
-                r["frac_of_measured_hbm"] = r["achieved_gbs"] / peaks["hbm_gbs"]
+                 "rel_res_true": info.rel_res_true, "create_s": t_create, "bytes_per_iter": balg,
+                 "achieved_gbs": balg * info.iters / t / 1e9}
+            r["frac_of_measured_hbm"] = r["achieved_gbs"] / peaks["hbm_gbs"]
+            if name == "fp64":
                 x64 = x.clone()
             else:
-                r["speedup_vs_fp64"] = rec["fp64"]["s"] / t
+                r["speedup_vs_fp64_sell"] = rec["fp64"]["s"] / t
                 r["err_vs_fp64_solution"] = (torch.linalg.norm(x - x64) / torch.linalg.norm(x64)).item()
             rec[name] = r
             s.close()

@@ -58,7 +58,17 @@ typedef enum {
   PPCG_FP32_IR = 1,  /* FP32 inner solves inside FP64 iterative refinement (restarted per step) */
   PPCG_FP32_RU = 2   /* FP32 recurrences with FP64 reliable updates (one Krylov sequence) */
 } ppcg_precision;
-typedef enum { PPCG_FMT_AUTO = 0, PPCG_FMT_CSR = 1, PPCG_FMT_SELL = 2 } ppcg_format;
+typedef enum {
+  PPCG_FMT_AUTO = 0,  /* SELL-C-sigma; a constant-coefficient box stencil on the grid path is
+                         detected and run matrix-free (see PPCG_FMT_BOX) */
+  PPCG_FMT_CSR = 1,   /* SELL-C-sigma with sigma = 1 (CSR row order kept) */
+  PPCG_FMT_SELL = 2,  /* SELL-C-sigma, never matrix-free */
+  PPCG_FMT_BOX = 3    /* matrix-free: A = c_d I + c_o (adjacency of the (2R+1)^3 box, R <= 3, on a
+                         g^3 grid, truncated at the boundary, rows in grid order, x fastest) -- the
+                         125-point Poisson family of Table II for R = 2.  A v is formed from axis-wise
+                         box sums of v, no matrix is read.  FP64 Alg. 2 on the grid path; a matrix of
+                         another form gives PPCG_ERR_ARG */
+} ppcg_format;
 typedef enum {
   PPCG_NORM_REL_R = 0,      /* ||r||_2 <= tol * ||b||_2 on the recursive residual, then a true-residual check */
   PPCG_NORM_PAPER_U_ABS = 1 /* sqrt((u, u)) <= tol, the absolute preconditioned norm of Alg. 2 / Sec. VI */
@@ -96,8 +106,9 @@ typedef struct {
                                a 4x fall and the FP64 residual does not halve, a non-finite
                                value, or a breakdown past max_restarts switch to the FP64
                                iteration from the last updated x.  REL_R norm only. */
-  int32_t format;           /* ppcg_format.  The matrix is always converted to SELL-C-sigma (C = 32)
-                               on the device; FMT_CSR forces sigma = 1 (CSR row order kept). */
+  int32_t format;           /* ppcg_format.  The matrix is converted to SELL-C-sigma (C = 32) on the
+                               device; FMT_CSR forces sigma = 1 (CSR row order kept); FMT_BOX and
+                               AUTO's detection use the matrix-free box product instead. */
   int32_t norm;             /* ppcg_norm */
   int32_t path;             /* ppcg_path.  AUTO: ONCHIP when the system fits (FP64 Alg. 2), else
                                CLUSTER up to cluster_max_rows rows, else GRID.  ONCHIP for a system

@@ -17,13 +17,13 @@ __all__ = [
     "OK", "PENDING", "ERR_ARG", "ERR_NOT_SPD", "ERR_BREAKDOWN", "ERR_NOT_CONVERGED",
     "ERR_NONFINITE", "ERR_OOM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_BUSY", "ERR_UNKNOWN_TICKET",
     "FP64", "FP32_IR", "FP32_RU", "NORM_REL_R", "NORM_PAPER_U_ABS", "PATH_AUTO", "PATH_GRID", "PATH_CLUSTER", "PATH_ONCHIP",
-    "FMT_AUTO", "FMT_CSR", "FMT_SELL", "VARIANT_ALG2", "VARIANT_JACOBI_SCALED", "EXPORTED_SYMBOLS",
+    "FMT_AUTO", "FMT_CSR", "FMT_SELL", "FMT_BOX", "VARIANT_ALG2", "VARIANT_JACOBI_SCALED", "EXPORTED_SYMBOLS",
 ]
 
 OK, PENDING, ERR_ARG, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_NOT_CONVERGED = 0, 1, -1, -2, -3, -4
 ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_UNKNOWN_TICKET = -5, -6, -7, -8, -9, -10
 FP64, FP32_IR, FP32_RU = 0, 1, 2
-FMT_AUTO, FMT_CSR, FMT_SELL = 0, 1, 2
+FMT_AUTO, FMT_CSR, FMT_SELL, FMT_BOX = 0, 1, 2, 3
 NORM_REL_R, NORM_PAPER_U_ABS = 0, 1
 PATH_AUTO, PATH_GRID, PATH_CLUSTER, PATH_ONCHIP = 0, 1, 2, 3
 VARIANT_ALG2, VARIANT_JACOBI_SCALED = 0, 1

@@ -371,6 +371,7 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
     delete h; set_error("ppcg_create: FP32_RU stops on the relative FP64 residual (norm REL_R only)"); return PPCG_ERR_ARG;
   }
   if (h->opts.norm != PPCG_NORM_REL_R && h->opts.norm != PPCG_NORM_PAPER_U_ABS) { delete h; set_error("ppcg_create: bad norm"); return PPCG_ERR_ARG; }
+  if (h->opts.format < PPCG_FMT_AUTO || h->opts.format > PPCG_FMT_BOX) { delete h; set_error("ppcg_create: bad format"); return PPCG_ERR_ARG; }
   if (h->opts.variant != PPCG_VARIANT_ALG2 && h->opts.variant != PPCG_VARIANT_JACOBI_SCALED) {
     delete h; set_error("ppcg_create: bad variant"); return PPCG_ERR_ARG;
   }
@@ -412,12 +413,27 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
     set_error("ppcg_create: could not stage the CSR arrays on the device");
     return PPCG_ERR_OOM;
   }
-  int32_t sigma = h->opts.format == PPCG_FMT_CSR ? 1 : h->opts.sigma;
+  const bool want_box = h->opts.format == PPCG_FMT_AUTO || h->opts.format == PPCG_FMT_BOX;
+  int32_t sigma = h->opts.format == PPCG_FMT_CSR || h->opts.format == PPCG_FMT_BOX ? 1 : h->opts.sigma;
   ppcg_status s = convert_csr_to_sell(n, nnz, d_rp, d_col, d_val, sigma, h->opts.precision != PPCG_FP64,
                                       h->opts.variant == PPCG_VARIANT_JACOBI_SCALED, stream, h->allocs, &h->sell,
                                       &h->A, &h->perm);
+  // Matrix-free box stencil: a constant-coefficient box on a g^3 grid in grid row order,
+  // solved by FP64 Alg. 2 on the grid path.
+  bool box = false;
+  if (s == PPCG_OK && want_box && h->opts.precision == PPCG_FP64 && h->opts.variant == PPCG_VARIANT_ALG2 &&
+      !h->perm)
+    box = detect_box_stencil(n, nnz, d_rp, d_col, d_val, stream, &h->box_g, &h->box_r, &h->box_cd, &h->box_co);
   free_tmp();
   if (s != PPCG_OK) { free_all(h); delete h; return s; }
+  if (h->opts.format == PPCG_FMT_BOX &&
+      (!box || h->opts.path == PPCG_PATH_CLUSTER || h->opts.path == PPCG_PATH_ONCHIP)) {
+    free_all(h);
+    delete h;
+    set_error("ppcg_create: FMT_BOX needs a constant-coefficient box stencil in grid row order, FP64 Alg. 2 "
+              "and the grid path");
+    return PPCG_ERR_ARG;
+  }
 
   // Execution plan (fixed for the handle, so every solve of it uses the same partition).
   // On chip: FP64 Alg. 2 whose vector tiles and matrix slots fit in one cluster's shared
@@ -433,9 +449,12 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
     set_error("ppcg_create: PATH_ONCHIP needs FP64 Alg. 2 and a system that fits in one cluster's shared memory");
     return PPCG_ERR_ARG;
   }
+  if (path == PPCG_PATH_AUTO && h->opts.format == PPCG_FMT_BOX) path = PPCG_PATH_GRID;
   if (path == PPCG_PATH_AUTO)
     path = onchip_ok ? PPCG_PATH_ONCHIP : n <= h->opts.cluster_max_rows ? PPCG_PATH_CLUSTER : PPCG_PATH_GRID;
   h->path = path;
+  if (path != PPCG_PATH_GRID) box = false;
+  if (!box) h->box_g = 0;
   if (path == PPCG_PATH_GRID) {
     h->shape = 0;
     if (const char* e = getenv("PPCG_GRID_SHAPE")) h->shape = atoi(e);   // launch-shape tuning knob
@@ -458,6 +477,8 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   h->bytes_per_iter = (v + 4.0) * (double)nnz + 4.0 * (double)(n + 1) + 17.0 * v * (double)n;
   if (h->opts.variant == PPCG_VARIANT_JACOBI_SCALED)   // off-diagonals, 13 vector streams
     h->bytes_per_iter = (v + 4.0) * (double)(nnz - n) + 4.0 * (double)(n + 1) + 13.0 * v * (double)n;
+  if (h->box_g > 0)   // no matrix: 17 vector streams + two stage arrays written and read
+    h->bytes_per_iter = 21.0 * v * (double)n;
 
   // Workspace.
   SysDesc& d = h->desc;
@@ -473,6 +494,7 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
             walloc(h, &h->bar, 1) && walloc(h, &h->err, 1) && walloc(h, &h->d_desc, 1) &&
             walloc(h, &d.v64, rows_padded * h->ns64);
   if (ok && fp32) ok = walloc(h, &d.v32, rows_padded * kSlots32);
+  if (ok && h->box_g > 0) ok = walloc(h, &d.box_t, 4 * (size_t)n);
   if (ok) {
     if (scaled)
       k_fill_scale_slots<<<blocks_for(n, 256), 256, 0, stream>>>(n, h->A.diag, d.v64, kSlotsS, kSlotDS, kSlotSigS);
@@ -505,6 +527,10 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   d.variant = h->opts.variant;
   d.inner_tol = h->opts.inner_tol;
   d.onchip_slots = (int32_t)std::min<int64_t>(h->sell.onchip_slots, INT32_MAX);
+  d.box_g = h->box_g;
+  d.box_r = h->box_r;
+  d.box_cd = h->box_cd;
+  d.box_co = h->box_co;
   d.dmin = h->sell.dmin;
   d.dmax = h->sell.dmax;
   d.spin_limit_ns = h->opts.spin_limit_ns;

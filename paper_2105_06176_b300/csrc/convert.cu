@@ -10,6 +10,7 @@
 // A v) exactly, as the first term of each row sum.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -164,7 +165,68 @@ int64_t sell_slots(const std::vector<int32_t>& len, int64_t sigma, std::vector<i
   return slots;
 }
 
+// One thread per row: does the row hold exactly the in-grid cells of its (2R+1)^3 box in
+// ascending column order, with value cd on the diagonal and co elsewhere?
+__global__ void k_box_check(int64_t n, int32_t g, int32_t R, const int64_t* __restrict__ rp,
+                            const int32_t* __restrict__ col, const double* __restrict__ val, double cd,
+                            double co, int32_t* bad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t x = (int32_t)(i % g), y = (int32_t)((i / g) % g), z = (int32_t)(i / ((int64_t)g * g));
+  auto span = [&](int32_t c) { return min(c, R) + min(g - 1 - c, R) + 1; };
+  const int64_t a = rp[i], e = rp[i + 1];
+  if (e - a != (int64_t)span(x) * span(y) * span(z)) { atomicOr(bad, 1); return; }
+  int64_t prev = -1;
+  for (int64_t k = a; k < e; k++) {
+    const int64_t j = col[k];
+    const int32_t jx = (int32_t)(j % g), jy = (int32_t)((j / g) % g), jz = (int32_t)(j / ((int64_t)g * g));
+    const bool in = abs(jx - x) <= R && abs(jy - y) <= R && abs(jz - z) <= R;
+    const double want = j == i ? cd : co;
+    if (j <= prev || !in || val[k] != want) { atomicOr(bad, 1); return; }
+    prev = j;
+  }
+}
+
 }  // namespace
+
+bool detect_box_stencil(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col, const double* d_val,
+                        cudaStream_t st, int32_t* g_out, int32_t* r_out, double* cd_out, double* co_out) {
+  if (n < 27) return false;
+  const int32_t g = (int32_t)std::llround(std::cbrt((double)n));
+  if ((int64_t)g * g * g != n) return false;
+  // row 0 is a corner: (R + 1)^3 entries, the diagonal first
+  int64_t rp01[2];
+  if (cudaMemcpyAsync(rp01, d_rp, sizeof(rp01), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) { cudaGetLastError(); return false; }
+  const int64_t cnt = rp01[1] - rp01[0];
+  const int32_t R = (int32_t)std::llround(std::cbrt((double)cnt)) - 1;
+  if (R < 1 || R > 3 || (int64_t)(R + 1) * (R + 1) * (R + 1) != cnt || g < 2 * R + 1) return false;
+  int32_t c2[2];
+  double v2[2];
+  if (cudaMemcpyAsync(c2, d_col + rp01[0], sizeof(c2), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(v2, d_val + rp01[0], sizeof(v2), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) { cudaGetLastError(); return false; }
+  if (c2[0] != 0 || c2[1] == 0) return false;
+  const double cd = v2[0], co = v2[1];
+  if (!(cd > 0.0) || !(co != 0.0)) return false;
+  int32_t* d_bad = nullptr;
+  if (pool_alloc((void**)&d_bad, sizeof(int32_t), st) != cudaSuccess) { cudaGetLastError(); return false; }
+  cudaMemsetAsync(d_bad, 0, sizeof(int32_t), st);
+  const int tb = 256;
+  k_box_check<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(n, g, R, d_rp, d_col, d_val, cd, co, d_bad);
+  int32_t bad = 1;
+  cudaMemcpyAsync(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  const bool ok = cudaStreamSynchronize(st) == cudaSuccess && bad == 0;
+  cudaGetLastError();
+  pool_free(d_bad, st);
+  (void)nnz;
+  if (!ok) return false;
+  *g_out = g;
+  *r_out = R;
+  *cd_out = cd;
+  *co_out = co;
+  return true;
+}
 
 ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col,
                                 const double* d_val, int32_t sigma_req, bool want_fp32, bool sym_scale,

@@ -90,6 +90,12 @@ struct SysDesc {
   int32_t variant, onchip_slots;  // ppcg_variant; on-chip path: matrix slots of the fullest CTA
   double tol, inner_tol;
   double dmin, dmax;     // extreme diagonal entries (bounds of ||r||^2 / gamma)
+  // Matrix-free box stencil (box_g > 0): A = box_cd I + box_co (adjacency of the
+  // (2 box_r + 1)^3 box on a box_g^3 grid, truncated at the boundary); box_t holds the
+  // four n-row stage arrays (x-sums and y-sums of up to two source vectors).
+  int32_t box_g, box_r;
+  double box_cd, box_co;
+  double* box_t;
   int64_t spin_limit_ns;
   const double* b;       // right-hand side, solver order (plain array)
   // Per-row vectors in chunk-interleaved blocks (for each 32-row chunk, the block's slots
@@ -133,6 +139,11 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
                                 const double* d_val, int32_t sigma_req, bool want_fp32, bool sym_scale,
                                 cudaStream_t st, std::vector<void*>& allocs, SellBuild* out,
                                 DevMatrix* A, int32_t** d_perm_out);
+
+// Is the (validated, device) CSR a constant-coefficient box stencil cd I + co (box adjacency)
+// on a g^3 grid, rows in grid order?  Synchronises st.
+bool detect_box_stencil(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col, const double* d_val,
+                        cudaStream_t st, int32_t* g, int32_t* r, double* cd, double* co);
 
 void set_error(const char* fmt, ...);
 

@@ -329,6 +329,10 @@ __device__ __forceinline__ void prefetch_chunk(const int64_t* __restrict__ cptr,
   const char* tile = reinterpret_cast<const char*>(blk + (int64_t)c * NS * kChunk);
   for (int off = lane * 128; off < kTileBytes; off += 32 * 128) prefetch_l2(tile + off);
   const int64_t b0 = __ldg(cptr + c), b1 = __ldg(cptr + c + 1);
+  // Long rows (over 16 slots) keep enough loads in flight on their own, and prefetching
+  // their matrix slots a chunk ahead from every warp would overflow L2 (the 125-point box:
+  // 32 KB per chunk); only the vector tile is prefetched for them.
+  if (b1 - b0 > 16 * kChunk) return;
   const char* pc = reinterpret_cast<const char*>(col + b0);
   const char* pv = reinterpret_cast<const char*>(val + b0);
   const int nc = (int)((b1 - b0) * 4), nv = (int)((b1 - b0) * (int64_t)sizeof(T));
@@ -1411,6 +1415,207 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
   }
 }
 
+// ------------------------------------ matrix-free constant-coefficient box stencil --
+// When A = cd I + co (adjacency of the (2R+1)^3 box on a g^3 grid, truncated at the
+// boundary) -- the 125-point Poisson family of Table II for R = 2 -- a product A v needs no
+// matrix: the box sum B(v)_i (v summed over row i's box, i included) is taken axis by axis.
+// Stage X writes t1 = the x-sums of v, stage Y writes t2 = the y-sums of t1, and the
+// consuming pass adds the z-sums of t2.  Rows are in grid order (x fastest), so each stage
+// reads its 2R+1 neighbours at fixed row offsets (1, g, g^2): for a warp, contiguous 32-row
+// runs.  Per product and row: 6R FP64 adds and 4 intermediate streams instead of (2R+1)^3-1
+// FMAs and the matrix stream.  Then (A v)_i = cd v_i + co (B_i - v_i) and
+// (A D^-1 v)_i = v_i + (co / cd) (B_i - v_i).
+
+__device__ __forceinline__ void box_coords(int32_t row, int32_t g, int32_t& z, int32_t& y, int32_t& x) {
+  const int32_t zy = row / g;
+  x = row - zy * g;
+  z = zy / g;
+  y = zy - z * g;
+}
+
+// Stage X for one or two FP64-block slots (slot_b < 0: one).
+__device__ void box_stage_x(const SysDesc& S, const Lanes& L, int slot_a, int slot_b) {
+  const int32_t n = (int32_t)S.A.n, g = S.box_g, R = S.box_r;
+  const GatherSlot<double, kNS64> va{S.v64 + slot_a * kChunk};
+  const GatherSlot<double, kNS64> vb{S.v64 + (slot_b < 0 ? slot_a : slot_b) * kChunk};
+  double* t1a = S.box_t;
+  double* t1b = S.box_t + n;
+  FOR_CHUNKS(S.A, L) {
+    const int32_t row = c * kChunk + L.lane;
+    if (row >= n) continue;
+    int32_t z, y, x;
+    box_coords(row, g, z, y, x);
+    double sa = 0.0, sb = 0.0;
+    for (int32_t d = -R; d <= R; d++) {
+      if (x + d < 0 || x + d >= g) continue;
+      sa += va(row + d);
+      if (slot_b >= 0) sb += vb(row + d);
+    }
+    __stcg(t1a + row, sa);
+    if (slot_b >= 0) __stcg(t1b + row, sb);
+  }
+}
+
+// Stage Y: t2 = y-sums of t1 (one or two arrays).
+__device__ void box_stage_y(const SysDesc& S, const Lanes& L, bool two) {
+  const int32_t n = (int32_t)S.A.n, g = S.box_g, R = S.box_r;
+  const double* t1a = S.box_t;
+  const double* t1b = S.box_t + n;
+  double* t2a = S.box_t + 2 * (int64_t)n;
+  double* t2b = S.box_t + 3 * (int64_t)n;
+  FOR_CHUNKS(S.A, L) {
+    const int32_t row = c * kChunk + L.lane;
+    if (row >= n) continue;
+    int32_t z, y, x;
+    box_coords(row, g, z, y, x);
+    double sa = 0.0, sb = 0.0;
+    for (int32_t d = -R; d <= R; d++) {
+      if (y + d < 0 || y + d >= g) continue;
+      sa += __ldcg(t1a + row + d * g);
+      if (two) sb += __ldcg(t1b + row + d * g);
+    }
+    __stcg(t2a + row, sa);
+    if (two) __stcg(t2b + row, sb);
+  }
+}
+
+// z-sums of t2 (array k = 0 or 1) for one row: the box sum B_row.
+__device__ __forceinline__ double box_z(const SysDesc& S, int32_t row, int32_t z, int k) {
+  const int32_t n = (int32_t)S.A.n, g = S.box_g, R = S.box_r;
+  const double* t2 = S.box_t + (2 + k) * (int64_t)n;
+  const int64_t plane = (int64_t)g * g;
+  double s = 0.0;
+  for (int32_t d = -R; d <= R; d++) {
+    if (z + d < 0 || z + d >= g) continue;
+    s += __ldcg(t2 + row + d * plane);
+  }
+  return s;
+}
+
+// Sources of the box stages for an FP64 pass (slot_a < 0: the pass needs no product).
+__device__ __forceinline__ void box_sources(const Ctl& C, const SysDesc& S, int& slot_a, int& slot_b) {
+  slot_a = slot_b = -1;
+  switch (C.pass) {
+    case P_SETUP1: if (!(S.x_zero != 0 && !C.fallback)) slot_a = V_X; break;
+    case P_SETUP2: slot_a = V_R; break;
+    case P_ITER: slot_a = (C.iter & 1) ? V_WB : V_WA; break;
+    case P_TRUE: slot_a = V_X; break;
+    case P_RR1: slot_a = V_X; if (!(C.iter == 0 || C.restart)) slot_b = V_P; break;
+    case P_RR2: slot_a = V_R; slot_b = V_S; break;
+    default: break;
+  }
+}
+
+// The FP64 passes with the box product (the other passes are shared with the SELL path).
+// Returns whether the pass produced partials.
+__device__ bool box_pass(const SysDesc& S, const Ctl& C, const Lanes& L, Dots<double>& d, bool paper) {
+  const int32_t n = (int32_t)S.A.n, g = S.box_g;
+  const double cd = S.box_cd, co = S.box_co, ch = S.box_co / S.box_cd;
+  const Blk<double, kNS64> v{S.v64};
+  switch (C.pass) {
+    case P_SETUP1:
+    case P_TRUE:
+    case P_RR1: {
+      const bool x_zero = C.pass == P_SETUP1 && S.x_zero != 0 && !C.fallback;
+      const bool rr = C.pass == P_RR1, p_zero = rr && (C.iter == 0 || C.restart);
+      FOR_CHUNKS(S.A, L) {
+        const int32_t row = c * kChunk + L.lane;
+        if (row >= n) continue;
+        int32_t z, y, x;
+        box_coords(row, g, z, y, x);
+        double* pc = v.chunk(c, L.lane);
+        const double bi = __ldg(S.b + row);
+        double ax = 0.0;
+        if (!x_zero) {
+          const double xi = ldcg(pc + V_X * kChunk);
+          ax = fma(co, box_z(S, row, z, 0) - xi, cd * xi);
+        }
+        const double ri = bi - ax;
+        if (C.pass == P_TRUE) { d.add(0, ri, ri); continue; }
+        const double id = ldcs(pc + V_INVD * kChunk);
+        stcs(pc + V_R * kChunk, ri);
+        stcs(pc + V_U * kChunk, id * ri);
+        if (rr) {
+          double ap = 0.0;
+          if (!p_zero) {
+            const double pi = ldcg(pc + V_P * kChunk);
+            ap = fma(co, box_z(S, row, z, 1) - pi, cd * pi);
+          }
+          stcs(pc + V_S * kChunk, ap);
+          stcs(pc + V_Q * kChunk, id * ap);
+        } else {
+          d.add(0, bi, bi);
+          d.add(1, ri, ri);
+        }
+      }
+      return !rr;
+    }
+    case P_SETUP2:
+    case P_RR2: {
+      const bool rr = C.pass == P_RR2;
+      const int wcs = rr && (C.iter & 1) ? V_WB : V_WA;
+      FOR_CHUNKS(S.A, L) {
+        const int32_t row = c * kChunk + L.lane;
+        if (row >= n) continue;
+        int32_t z, y, x;
+        box_coords(row, g, z, y, x);
+        double* pc = v.chunk(c, L.lane);
+        const double ri = ldcg(pc + V_R * kChunk), ui = ldcs(pc + V_U * kChunk);
+        const double wi = fma(ch, box_z(S, row, z, 0) - ri, ri);
+        stcs(pc + wcs * kChunk, wi);
+        if (rr) {
+          const double si = ldcg(pc + V_S * kChunk);
+          stcs(pc + V_Z * kChunk, fma(ch, box_z(S, row, z, 1) - si, si));
+        }
+        d.add(0, ri, ui);
+        d.add(1, wi, ui);
+        if (paper) d.add(2, ui, ui); else d.add(2, ri, ri);
+      }
+      return true;
+    }
+    case P_ITER: {
+      const bool first = C.first != 0, with_rr = C.want_rr != 0;
+      const double alpha = C.alpha, beta = C.beta;
+      const int wcs = (C.iter & 1) ? V_WB : V_WA;
+      const int wns = (C.iter & 1) ? V_WA : V_WB;
+      FOR_CHUNKS(S.A, L) {
+        const int32_t row = c * kChunk + L.lane;
+        if (row >= n) continue;
+        int32_t z, y, x;
+        box_coords(row, g, z, y, x);
+        double* pc = v.chunk(c, L.lane);
+        const double wi = ldcg(pc + wcs * kChunk);
+        // n_i = (A M^-1 w)_i = w_i + (co / cd) (B(w)_i - w_i)
+        const double ni = fma(ch, box_z(S, row, z, 0) - wi, wi);
+        const double id = ldcs(pc + V_INVD * kChunk), ui = ldcs(pc + V_U * kChunk);
+        const double mi = id * wi;
+        const double zi = first ? ni : fma(beta, ldcs(pc + V_Z * kChunk), ni);
+        const double qi = first ? mi : fma(beta, ldcs(pc + V_Q * kChunk), mi);
+        const double si = first ? wi : fma(beta, ldcs(pc + V_S * kChunk), wi);
+        const double pi = first ? ui : fma(beta, ldcs(pc + V_P * kChunk), ui);
+        const double xi = fma(alpha, pi, ldcs(pc + V_X * kChunk));
+        const double ri = fma(-alpha, si, ldcs(pc + V_R * kChunk));
+        const double un = fma(-alpha, qi, ui);
+        const double wnn = fma(-alpha, zi, wi);
+        stcs(pc + V_Z * kChunk, zi);
+        stcs(pc + V_Q * kChunk, qi);
+        stcs(pc + V_S * kChunk, si);
+        stcs(pc + V_P * kChunk, pi);
+        stcs(pc + V_X * kChunk, xi);
+        stcs(pc + V_R * kChunk, ri);
+        stcs(pc + V_U * kChunk, un);
+        stcs(pc + wns * kChunk, wnn);
+        d.add(0, ri, un);
+        d.add(1, wnn, un);
+        if (with_rr) { if (paper) d.add(2, un, un); else d.add(2, ri, ri); }
+      }
+      return true;
+    }
+    default:
+      return false;
+  }
+}
+
 // ------------------------------------------------------------------------- driver --
 
 // Shared state of run_system.  The grid path keeps the per-warp-tree block reduction and a
@@ -1499,6 +1704,19 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
         case P_ZERO_X: pass_zero_x<kNSS, VS_X>(S, L); partials = false; break;
         default: partials = false; break;
       }
+      if (partials) write_block_partials<kPacked>(d.get(0), d.get(1), d.get(2), slot, sh.sm);
+    } else if (!fp32 && S.box_g > 0 && (pass == P_SETUP1 || pass == P_SETUP2 || pass == P_ITER ||
+                                          pass == P_TRUE || pass == P_RR1 || pass == P_RR2)) {
+      int sa, sb;
+      box_sources(C, S, sa, sb);
+      if (sa >= 0) {
+        box_stage_x(S, L, sa, sb);
+        if (!g.sync()) { if (threadIdx.x == 0) { C.status = PPCG_ERR_TIMEOUT; C.state = S_DONE; } break; }
+        box_stage_y(S, L, sb >= 0);
+        if (!g.sync()) { if (threadIdx.x == 0) { C.status = PPCG_ERR_TIMEOUT; C.state = S_DONE; } break; }
+      }
+      Dots<double> d;
+      partials = box_pass(S, C, L, d, paper);
       if (partials) write_block_partials<kPacked>(d.get(0), d.get(1), d.get(2), slot, sh.sm);
     } else if (!fp32) {
       Dots<double> d;

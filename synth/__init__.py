@@ -15,6 +15,7 @@ from .matrices import (
     rgg_laplacian,
     box125,
     box125_nnz,
+    box_stencil,
     hadamard_spd,
     batch_mix,
     serving_mix,
@@ -26,5 +27,5 @@ from .matrices import (
 __all__ = [
     "mix64", "u64_stream", "uniform", "uniform_pm1", "normal",
     "CSR", "poisson2d", "poisson3d", "varcoeff2d", "varcoeff3d", "rgg_laplacian",
-    "box125", "box125_nnz", "hadamard_spd", "batch_mix", "serving_mix", "rhs_uniform", "xtrue_uniform", "build_spec",
+    "box125", "box125_nnz", "box_stencil", "hadamard_spd", "batch_mix", "serving_mix", "rhs_uniform", "xtrue_uniform", "build_spec",
 ]

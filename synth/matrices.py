@@ -146,8 +146,16 @@ def box125(n, slab=8):
     diag 124, off-diag -1 (irreducibly diagonally dominant, so SPD).  Built `slab`
     z-planes at a time straight into arrays of the final size (n = 185 has 776M nonzeros),
     so the peak host memory is the CSR itself plus one slab of candidates."""
-    offs = np.array([(dz, dy, dx) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)])
-    nnz = box125_nnz(n)
+    return box_stencil(n, 2, 124.0, -1.0, slab=slab, name=f"box125_{n}")
+
+
+def box_stencil(n, R, cd, co, slab=8, name=None):
+    """Constant-coefficient box stencil on an n^3 grid: cd on the diagonal, co for every
+    other cell within Chebyshev distance R (truncated at the boundary); rows in grid order,
+    x fastest.  SPD when cd > 0 and cd >= ((2R+1)^3 - 1) |co| with co < 0."""
+    offs = np.array([(dz, dy, dx) for dz in range(-R, R + 1) for dy in range(-R, R + 1) for dx in range(-R, R + 1)])
+    i = np.arange(n)
+    nnz = int((np.minimum(i, R) + np.minimum(n - 1 - i, R) + 1).sum()) ** 3
     N = n ** 3
     row_ptr = np.zeros(N + 1, dtype=np.int64)
     col = np.empty(nnz, dtype=np.int32)
@@ -164,7 +172,7 @@ def box125(n, slab=8):
         ok = (nz_ >= 0) & (nz_ < n) & (ny_ >= 0) & (ny_ < n) & (nx_ >= 0) & (nx_ < n)
         # with every coordinate inside [0, n) the (dz, dy, dx) order is ascending column order
         cols = ((nz_ * n + ny_) * n + nx_)[ok]
-        vals = np.where(np.broadcast_to(is_diag[None, :], ok.shape), 124.0, -1.0)[ok]
+        vals = np.where(np.broadcast_to(is_diag[None, :], ok.shape), cd, co)[ok]
         r0 = z0 * n * n
         np.cumsum(ok.sum(axis=1), out=row_ptr[r0 + 1:r0 + 1 + ok.shape[0]])
         row_ptr[r0 + 1:r0 + 1 + ok.shape[0]] += pos
@@ -172,7 +180,7 @@ def box125(n, slab=8):
         val[pos:pos + vals.size] = vals
         pos += cols.size
     assert pos == nnz
-    return CSR(N, row_ptr, col, val, f"box125_{n}")
+    return CSR(N, row_ptr, col, val, name or f"box{2 * R + 1}_{n}")
 
 
 def rgg_laplacian(npts, radius, shift, seed, chunk=1 << 22):

@@ -334,6 +334,79 @@ def test_onchip_in_batch_bitwise_equals_solo():
         assert np.array_equal(xb.cpu().numpy(), x0)
 
 
+# ------------------------------------------- matrix-free box stencil (Table II family, f3) --
+
+BOX = dict(format=3, path=1)
+
+
+def box_problem(name):
+    if name == "box125_24":              # R = 2, 13,824 rows: 432 chunks, grid rows of 24
+        a = synth.box125(24)
+        return a, synth.rhs_uniform(a.n, 11)
+    if name == "box27_33":               # R = 1, 35,937 rows, a ragged last chunk
+        a = synth.box_stencil(33, 1, 26.5, -1.0)
+        return a, synth.rhs_uniform(a.n, 12)
+    if name == "box343_12":              # R = 3
+        a = synth.box_stencil(12, 3, 400.0, -1.0)
+        return a, synth.rhs_uniform(a.n, 13)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name,k", [("box125_24", 12), ("box27_33", 25), ("box343_12", 8)])
+def test_box_fixed_k_parity(name, k):
+    a, b = box_problem(name)
+    ref = oracle.pipecg(a, b, tol=0.0, maxit=k)
+    x, info = gpu(a, b, tol=0.0, maxit=k, **BOX)
+    assert info.bytes_per_iter == pytest.approx(21 * 8 * a.n)      # the matrix-free plan
+    assert info.iters == k and rel(x, ref["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["box125_24", "box27_33", "box343_12"])
+def test_box_full_solve_parity(name):
+    a, b = box_problem(name)
+    ref = oracle.pipecg(a, b, tol=1e-8, maxit=5000)
+    x, info = gpu(a, b, tol=1e-8, maxit=5000, **BOX)
+    assert info.status == pp().OK and abs(info.iters - ref["result"]["iters"]) <= 2
+    t = np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)
+    assert t <= 1e-8 and abs(t - info.rel_res_true) <= 1e-6 * t
+
+
+def test_box_modes_detection_and_rejects():
+    m = pp()
+    a, b = box_problem("box125_24")
+    # AUTO detects the stencil on the grid path and gives the same iterates as FMT_BOX
+    xa, ia = gpu(a, b, tol=1e-8, maxit=5000, path=1)
+    xb, ib = gpu(a, b, tol=1e-8, maxit=5000, **BOX)
+    assert ia.iters == ib.iters and np.array_equal(xa, xb)
+    # FMT_SELL keeps the matrix: different plan, same answer within the parity bars
+    xs, is_ = gpu(a, b, tol=1e-8, maxit=5000, format=2, path=1)
+    assert abs(is_.iters - ib.iters) <= 2
+    # residual replacement, paper norm, nonzero x0
+    ref = oracle.pipecg(a, b, tol=0.0, maxit=30, rr_period=7)
+    x, info = gpu(a, b, tol=0.0, maxit=30, rr_period=7, **BOX)
+    assert info.rr_count == ref["result"]["rr_count"] and rel(x, ref["x"]) <= 1e-10
+    bp = a.to_scipy() @ np.full(a.n, 1.0 / np.sqrt(a.n))
+    refp = oracle.pipecg(a, bp, tol=1e-5, maxit=10000, norm=oracle.NORM_PAPER_U_ABS)
+    x, info = gpu(a, bp, tol=1e-5, maxit=10000, norm=m.NORM_PAPER_U_ABS, **BOX)
+    assert info.status == m.OK and abs(info.iters - refp["result"]["iters"]) <= 2
+    x0 = synth.xtrue_uniform(a.n, 3)
+    refx = oracle.pipecg(a, b, x0=x0, tol=0.0, maxit=10)
+    x, info = gpu(a, b, x0=x0, tol=0.0, maxit=10, **BOX)
+    assert rel(x, refx["x"]) <= 1e-10
+    # not a constant box stencil, or not FP64 Alg. 2, or not the grid path: refused
+    v = synth.varcoeff3d(24, seed=2)
+    for mat, kw in ((v, dict(path=1)), (a, dict(path=1, precision=m.FP32_RU)), (a, dict(path=1, variant=1)),
+                    (a, dict(path=2))):
+        with pytest.raises(m.PPCGError) as e:
+            m.Solver.from_csr(mat, format=3, **kw)
+        assert e.value.status == m.ERR_ARG
+    # a perturbed value breaks the detection: AUTO keeps the SELL matrix
+    bad = synth.CSR(a.n, a.row_ptr.copy(), a.col.copy(), a.val.copy())
+    bad.val[len(bad.val) // 2] *= 1.0 + 1e-15
+    _, info = gpu(bad, b, tol=1e-8, maxit=1, path=1)
+    assert info.bytes_per_iter != pytest.approx(21 * 8 * a.n)
+
+
 # ----------------------------------------------------- Jacobi-scaled variant (next row f1) --
 
 SCALED = dict(variant=1)

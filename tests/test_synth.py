@@ -74,6 +74,17 @@ def test_box125_matches_brute_force(n, slab):
     assert np.all(np.diff(a.col[a.row_ptr[0]:a.row_ptr[1]]) > 0)
 
 
+@pytest.mark.parametrize("n,R", [(4, 1), (5, 1), (7, 3)])
+def test_box_stencil_matches_brute_force(n, R):
+    a = synth.box_stencil(n, R, 2.0 * (2 * R + 1) ** 3, -0.5)
+    idx = np.arange(n ** 3)
+    zyx = np.stack([idx // (n * n), (idx // n) % n, idx % n], axis=1)
+    cheb = np.abs(zyx[:, None, :] - zyx[None, :, :]).max(axis=2)
+    expect = np.where(cheb <= R, -0.5, 0.0)
+    np.fill_diagonal(expect, 2.0 * (2 * R + 1) ** 3)
+    assert np.array_equal(a.dense(), expect)
+
+
 def test_box125_reproduces_table2():
     for name, N, nnz in _rows("table2_poisson125.txt"):
         n = round(int(N) ** (1 / 3))
