@@ -124,6 +124,24 @@ def test_fp32_ru_hard_system_finishes_in_fp64_accuracy():
     assert np.linalg.norm(bn - a.to_scipy() @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(bn)
 
 
+def test_fp32_ru_falls_back_when_fp32_cannot_progress():
+    """A 1-D Laplacian chain of 8,000 rows (kappa ~ 2.6e7 > 1/eps32): FP32 corrections carry no
+    correct digits, so the recursion claims progress that the FP64 residual of the reliable
+    updates does not show; after three such updates the solve switches to the FP64 iteration
+    and still meets the FP64 residual bar."""
+    m = pp()
+    import scipy.sparse as sp
+    n = 8000
+    c = sp.diags([-np.ones(n - 1), 2.0 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1], format="csr")
+    a = synth.CSR(n, c.indptr.astype(np.int64), c.indices.astype(np.int32), c.data.astype(np.float64))
+    b = synth.rhs_uniform(n, 21)
+    s = m.Solver.from_csr(a, precision=m.FP32_RU, path=m.PATH_GRID)
+    x, info = s.solve(dev(b), tol=1e-8, maxit=200000)
+    assert info.status == m.OK, info
+    assert info.fp64_fallback == 1
+    assert np.linalg.norm(b - a.to_scipy() @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(b)
+
+
 def test_fp32_ru_edge_cases():
     m = pp()
     a = synth.poisson2d(40)
