@@ -257,10 +257,14 @@ namespace {
 
 // Work list of a launch of one cluster running system 0: device array {0, 0, 1} read as
 // list = {0} (element 0) and list_ptr = {0, 1} (elements 1-2).
+// (One array per device, created on first use and kept for the process.)
 const int32_t* single_work_list() {
-  static int32_t* d_list = nullptr;
   static std::mutex mu;
+  static std::unordered_map<int, int32_t*> per;
+  int dev = 0;
+  cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(mu);
+  int32_t*& d_list = per[dev];
   if (!d_list) {
     const int32_t host[3] = {0, 0, 1};
     if (cudaMalloc(&d_list, sizeof(host)) != cudaSuccess ||

@@ -14,6 +14,9 @@
 // with w double-buffered (other CTAs still gather the old w), and alpha/beta (lines 5-9)
 // formed after the barrier from the partials in a fixed order.
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "internal.h"
 
@@ -2188,10 +2191,10 @@ __global__ void k_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, in
 int grid_shape_count() { return kNumGridShapes; }
 int grid_threads(int shape) { return kGridShapes[shape].threads; }
 
+cudaError_t ensure_smem_attr(const void* fn, size_t bytes);
+
 static void set_smem_attr(const GridShape& gs) {
-  if (gs.smem > 0 && cudaFuncSetAttribute((const void*)gs.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, gs.smem) !=
-                         cudaSuccess)
-    cudaGetLastError();
+  if (gs.smem > 0 && ensure_smem_attr((const void*)gs.fn, (size_t)gs.smem) != cudaSuccess) cudaGetLastError();
 }
 
 int grid_blocks_for_device(int device, int shape) {
@@ -2230,17 +2233,27 @@ cudaError_t launch_grid(const SysDesc* d_desc, int shape, int grid, int budget, 
   return cudaLaunchCooperativeKernel((void*)gs.fn, dim3(grid), dim3(gs.threads), args, gs.smem, st);
 }
 
+// Raise a kernel's dynamic shared memory limit to at least `bytes` on the current device
+// (the attribute is per device; callers may run on several devices and host threads).
+cudaError_t ensure_smem_attr(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = done[{dev, fn}];
+  if (bytes <= have) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
+
 cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
                             int nclusters, int budget, cudaStream_t st, bool spread) {
   // spread: request enough dynamic shared memory that no two CTAs share an SM, so a lone
   // cluster gets the FP64 pipes of 8 SMs instead of being packed onto two.
-  static bool attr_set = false;
   const int spread_smem = 120 * 1024;
-  if (spread && !attr_set) {
-    if (cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, spread_smem) != cudaSuccess)
-      cudaGetLastError();
-    attr_set = true;
-  }
+  if (spread && ensure_smem_attr((const void*)k_cluster, spread_smem) != cudaSuccess) cudaGetLastError();
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kClusterSize * nclusters);
   cfg.blockDim = dim3(kClusterThreads);
@@ -2270,12 +2283,8 @@ size_t onchip_smem_limit(int device) {
 
 cudaError_t launch_onchip(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
                           int nclusters, int budget, size_t smem, cudaStream_t st) {
-  static size_t attr = 0;
-  if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_onchip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = smem;
-  }
+  cudaError_t e = ensure_smem_attr((const void*)k_onchip, smem);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kClusterSize * nclusters);
   cfg.blockDim = dim3(kOnchipThreads);
