@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <unordered_map>
 #include <queue>
 #include <vector>
@@ -29,7 +30,23 @@ cudaMemPool_t g_pools[64] = {nullptr};
 std::vector<Stage*> g_stage_free;     // pinned info stages, reused across handles
 }  // namespace
 
+// Host-side fault injection for tests: with PPCG_FAIL_DEVICE_ALLOC=k set, the k-th device
+// allocation counted from the moment the variable took its current value fails as out of
+// memory (once).  No GPU fault is involved: the allocation is simply not made.
+static bool injected_alloc_failure() {
+  static std::mutex mu;
+  static std::string last;
+  static long count = 0;
+  const char* e = getenv("PPCG_FAIL_DEVICE_ALLOC");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!e || !*e) { last.clear(); return false; }
+  if (last != e) { last = e; count = 0; }
+  const long k = atol(e);
+  return k > 0 && ++count == k;
+}
+
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st) {
+  if (injected_alloc_failure()) { *p = nullptr; return cudaErrorMemoryAllocation; }
   int dev = 0;
   cudaGetDevice(&dev);
   cudaMemPool_t pool = nullptr;

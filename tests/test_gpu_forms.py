@@ -261,6 +261,44 @@ def test_server_results_same_alone_and_in_mix(precision):
     assert np.array_equal(xs.cpu().numpy(), alone[0][1])
 
 
+def test_injected_allocation_failures_are_reported_and_recovered(monkeypatch):
+    """Host-side fault injection (no GPU fault): every device allocation of ppcg_create is
+    made to fail in turn; each attempt returns PPCG_ERR_OOM without crashing or leaking into
+    later calls, and a clean create + solve afterwards meets the parity bar.  The server
+    reports an injected failure as that request's status and serves the next request."""
+    m = pp()
+    a = synth.varcoeff3d(30, seed=4)
+    b = synth.rhs_uniform(a.n, 4)
+    failures = 0
+    for k in range(1, 40):
+        monkeypatch.setenv("PPCG_FAIL_DEVICE_ALLOC", str(k))
+        try:
+            s = m.Solver.from_csr(a, precision=m.FP32_RU, path=m.PATH_GRID)
+        except m.PPCGError as e:
+            assert e.status == m.ERR_OOM, str(e)
+            failures += 1
+            continue
+        s.close()
+        break
+    assert failures >= 5                      # create makes several device allocations
+    monkeypatch.delenv("PPCG_FAIL_DEVICE_ALLOC")
+    ref = oracle.pipecg(a, b, tol=1e-8, maxit=5000)
+    x, info = m.Solver.from_csr(a, path=m.PATH_GRID).solve(dev(b), tol=1e-8, maxit=5000)
+    assert info.status == m.OK and abs(info.iters - ref["result"]["iters"]) <= 2
+    # server: the admitter's allocation fails for one request only
+    srv = m.Server(epoch_iters=64)
+    monkeypatch.setenv("PPCG_FAIL_DEVICE_ALLOC", "1")
+    t_bad = srv.submit(a, b, tol=1e-8, maxit=5000)
+    res = _wait(srv, [t_bad], {t_bad: a.n})
+    monkeypatch.delenv("PPCG_FAIL_DEVICE_ALLOC")
+    assert res[t_bad][0] == m.ERR_OOM
+    t_ok = srv.submit(a, b, tol=1e-8, maxit=5000)
+    res = _wait(srv, [t_ok], {t_ok: a.n})
+    assert res[t_ok][0] == m.OK
+    assert srv.stats()["hbm_in_use"] == 0
+    srv.close()
+
+
 def test_server_admission_by_budget_and_errors():
     m = pp()
     systems = _batch_systems()[:5]
