@@ -375,6 +375,7 @@ const char* ppcg_last_error(void) { return g_err; }
 ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64_t* row_ptr,
                         const int32_t* col, const double* val, const ppcg_opts* opts,
                         cudaStream_t stream) {
+  NvtxRange nvtx_range("ppcg_create");
   g_err[0] = 0;
   if (!handle) { set_error("ppcg_create: handle is NULL"); return PPCG_ERR_ARG; }
   *handle = nullptr;
@@ -566,6 +567,7 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
 
 ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double* x, double tol,
                        int32_t maxit, cudaStream_t st, ppcg_info* info) {
+  NvtxRange nvtx_range("ppcg_solve");
   g_err[0] = 0;
   if (!h) { set_error("ppcg_solve: NULL handle"); return PPCG_ERR_ARG; }
   if (!(tol >= 0.0) || maxit < 0 || (h->n > 0 && (!b || !x))) {
@@ -604,6 +606,7 @@ ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double*
 ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double* const* b,
                              const double* const* x0, double* const* x, const double* tol,
                              const int32_t* maxit, cudaStream_t st, ppcg_info* infos) {
+  NvtxRange nvtx_range("ppcg_batch_solve");
   g_err[0] = 0;
   if (count < 0 || (count > 0 && (!hs || !b || !x || !tol || !maxit))) {
     set_error("ppcg_batch_solve: bad arguments");

@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <vector>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/ppcg.h"
 
@@ -146,6 +147,15 @@ bool detect_box_stencil(int64_t n, int64_t nnz, const int64_t* d_rp, const int32
                         cudaStream_t st, int32_t* g, int32_t* r, double* cd, double* co);
 
 void set_error(const char* fmt, ...);
+
+// NVTX range over a host-side scope (create, enqueue of a solve or batch, server admission
+// and epochs), for timeline profilers; header-only NVTX 3, no cost when no tool listens.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Device memory of handles comes from a library-owned stream-ordered pool per device (no
 // device-wide synchronisation on allocation or release; freed blocks stay in the pool).

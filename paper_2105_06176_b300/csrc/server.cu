@@ -111,6 +111,7 @@ void admit_loop(ppcg_srv* S) {
       S->in_use += req->footprint;
       S->running++;
     }
+    NvtxRange nvtx_range("ppcg_server_admit");
     ppcg_handle h = nullptr;
     // Served solves take the cluster path (epochs of many solves in one launch) or the grid
     // path; the on-chip path holds 8 SMs' shared memory per solve and is left to ppcg_solve.
@@ -155,6 +156,7 @@ void admit_loop(ppcg_srv* S) {
 }
 
 bool run_cluster_epoch(ppcg_srv* S, const std::vector<Slot*>& slots) {
+  NvtxRange nvtx_range("ppcg_server_epoch");
   const int m = (int)slots.size();
   if (m == 0) return true;
   std::vector<SysDesc> descs(m);
