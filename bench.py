@@ -145,6 +145,17 @@ def dist_setup():
     return ws, rank, local
 
 
+def reduce_over_ranks(dist, device, times, counts):
+    """Whole-job figures of a multi-rank run: the maximum over ranks of each time and the sum
+    over ranks of each count (every rank calls it with lists of the same length)."""
+    import torch
+    t = torch.tensor(times, dtype=torch.float64, device=device)
+    c = torch.tensor(counts, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return t.tolist(), c.tolist()
+
+
 def cpu_oracle_rate(a, b, k_lo=2, k_hi=8):
     """Oracle (plain single-thread C, FP64) iterations/s on the same system: the time of
     k_hi - k_lo iterations, from two runs that share setup and final-residual costs."""
@@ -456,7 +467,7 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     import oracle
-    a = synth.varcoeff3d(GRID_N, SEED)
+    a = synth.varcoeff3d(args.grid, SEED)
     b = synth.rhs_uniform(a.n, SEED)
     oracle.lib()
     k = 3
@@ -473,9 +484,9 @@ def run_reference(args, ws, rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload(GRID_N, a.n, a.nnz), "sample": f"{k} iterations per step incl. setup and final residual"},
+            "config": {"workload": workload(args.grid, a.n, a.nnz), "sample": f"{k} iterations per step incl. setup and final residual"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{k} iterations of the 256^3 system per step, including setup "
+                             "sample": f"{k} iterations of the {args.grid}^3 system per step, including setup "
                                        f"(3 SpMV) and the final residual, single-thread plain C"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -577,11 +588,7 @@ def main():
     assert all(i.status == pp.OK for i in infos), [i.status for i in infos]
     step_s = [s.elapsed_time(e) * 1e-3 for s, e in step_ev]
     if pg:
-        t = torch.tensor([dt, float(iters)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-        pg.all_reduce(t, op=pg.ReduceOp.SUM)
-        dt_max, iters_all = tmax[0].item(), t[1].item()
+        (dt_max,), (iters_all,) = reduce_over_ranks(pg, "cuda", [dt], [float(iters)])
     else:
         dt_max, iters_all = dt, float(iters)
     value = iters_all / dt_max
@@ -599,12 +606,10 @@ def main():
         e_iters += info.iters
     e_dt = time.perf_counter() - t0
     barrier()
-    e2e = {"value": e_iters * ws / e_dt if not pg else None, "unit": UNIT,
-           "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+    e2e = {"value": e_iters / e_dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
     if pg:
-        t = torch.tensor([e_dt], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e["value"] = e_iters * ws / t.item()
+        (e_dt_max,), (e_iters_all,) = reduce_over_ranks(pg, "cuda", [e_dt], [float(e_iters)])
+        e2e["value"] = e_iters_all / e_dt_max
 
     # roofline of the solve kernel (one launch = one step)
     peaks, peak_kind = measured_peaks()
