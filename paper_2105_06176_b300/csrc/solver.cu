@@ -1198,8 +1198,57 @@ __device__ __forceinline__ bool scalars(Ctl& c, int it) {
   return true;
 }
 
+// The common step of the FP64 iteration -- S_AFTER_ITER, then S_TOP continuing with the
+// next P_ITER -- on registers: the same operations in the same order as the general state
+// machine below, committed only when every check of S_TOP lets the iteration continue;
+// otherwise nothing is written and the general path takes the step.  (The control step is
+// a serial chain run by one thread per CTA on every iteration; with the control block in
+// shared memory each of its field accesses is a dependent round trip.)
+__device__ __forceinline__ bool control_fast(Ctl& c, const SysDesc& S, int iter_end) {
+  if (c.state != S_AFTER_ITER) return false;
+  const int iter = c.iter + 1;
+  const double gamma_prev = c.gamma, alpha_prev = c.alpha;
+  const double gamma = c.red[0], delta = c.red[1];
+  const int rr_valid = c.want_rr;
+  const double norm = rr_valid ? sqrt(c.red[2]) : HUGE_VAL;
+  const double bnorm = c.bnorm, tol = S.tol;
+  const bool paper = S.norm == PPCG_NORM_PAPER_U_ABS;
+  auto may = [&](double slack) {
+    if (!(gamma >= 0.0)) return true;
+    if (paper) return gamma / S.dmax <= slack * tol * tol;
+    const double t = tol * bnorm;
+    return gamma * S.dmin <= slack * t * t;
+  };
+  if (iter >= iter_end) return false;
+  if (S.rr_period > 0 && iter % S.rr_period == 0 && c.last_rr_iter != iter) return false;
+  if (!rr_valid && may(1.001)) return false;
+  if (paper ? (norm <= tol) : (norm <= tol * bnorm)) return false;
+  if (iter >= S.maxit) return false;
+  if (!isfinite(gamma) || !isfinite(delta)) return false;
+  const double beta = gamma / gamma_prev;
+  const double den = delta - beta * gamma / alpha_prev;
+  if (!(gamma > 0.0) || !(den > 0.0)) return false;
+  const double alpha = gamma / den;
+  const int want = may(64.0) ? 1 : 0;
+  c.gamma_prev = gamma_prev;
+  c.alpha_prev = alpha_prev;
+  c.iter = iter;
+  c.restart = 0;
+  c.gamma = gamma;
+  c.delta = delta;
+  c.norm = norm;
+  c.rr_valid = rr_valid;
+  c.beta = beta;
+  c.alpha = alpha;
+  c.first = 0;
+  c.want_rr = want;
+  c.pass = P_ITER;
+  return true;
+}
+
 // Thread 0 of every CTA: choose the next pass from the reduced partials of the last one.
 __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
+  if (control_fast(c, S, iter_end)) return;
   for (;;) {
     switch (c.state) {
       // ---- FP64 pipelined PCG
