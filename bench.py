@@ -354,9 +354,14 @@ def measure_rgg(pp, torch, npts=4_000_000, seed=3):
         runs[name] = (x.clone(), info, e0.elapsed_time(e1) * 1e-3)
         s.close()
     ref = runs["fp64_1e-10"][0]
+    peaks, _ = measured_peaks()
     for name, (x, info, t) in runs.items():
+        # algorithmic bytes (B_alg of the iteration's precision, SELL padding not counted)
+        gbs = info.bytes_per_iter * info.iters / t / 1e9
         out[name] = {"s": t, "iters": info.iters, "outer": info.outer_iters, "status": pp.status_name(info.status),
-                     "rel_res_true": info.rel_res_true,
+                     "rel_res_true": info.rel_res_true, "iters_per_s": info.iters / t,
+                     "bytes_per_iter": info.bytes_per_iter, "achieved_gbs": gbs,
+                     "frac_of_measured_hbm": gbs / peaks["hbm_gbs"],
                      "err_vs_fp64_1e-10": (torch.linalg.norm(x - ref) / torch.linalg.norm(ref)).item()}
     out["fp32_ru_speedup_vs_fp64_1e-8"] = runs["fp64_1e-8"][2] / runs["fp32_ru_1e-8"][2]
     out["fp32_ir_speedup_vs_fp64_1e-8"] = runs["fp64_1e-8"][2] / runs["fp32_ir_1e-8"][2]
