@@ -462,9 +462,20 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   // memory; AUTO takes it whenever it fits (it removes every L2 round trip from an
   // iteration, the latency that bounds small systems).
   int path = h->opts.path;
-  h->onchip_smem = onchip_smem_bytes(h->A.nchunks, h->sell.onchip_slots);
-  const bool onchip_ok = h->opts.precision == PPCG_FP64 && h->opts.variant == PPCG_VARIANT_ALG2 &&
-                         h->onchip_smem <= onchip_smem_limit(h->device) && h->sell.onchip_slots < INT32_MAX;
+  bool onchip_ok = false;
+  if (h->opts.precision == PPCG_FP64 && h->opts.variant == PPCG_VARIANT_ALG2 &&
+      (path == PPCG_PATH_AUTO || path == PPCG_PATH_ONCHIP)) {
+    // 16 CTAs per cluster spread the FP64 work of an iteration over twice the SMs (the pass
+    // is FP64-pipe bound on chip); it pays once every CTA has a few chunks.  8 otherwise, or
+    // when the device cannot place a 16-CTA cluster with this much shared memory.
+    const size_t limit = onchip_smem_limit(h->device);
+    const size_t s8 = onchip_smem_bytes(h->A.nchunks, h->sell.onchip_slots, 8);
+    const size_t s16 = onchip_smem_bytes(h->A.nchunks, h->sell.onchip_slots16, 16);
+    const bool ok16 = s16 <= limit && h->sell.onchip_slots16 < INT32_MAX && onchip_cluster_fits(16, s16);
+    const bool ok8 = s8 <= limit && h->sell.onchip_slots < INT32_MAX && onchip_cluster_fits(8, s8);
+    if (ok16 && (h->A.nchunks >= 64 || !ok8)) { h->onchip_nc = 16; h->onchip_smem = s16; onchip_ok = true; }
+    else if (ok8) { h->onchip_nc = 8; h->onchip_smem = s8; onchip_ok = true; }
+  }
   if (path == PPCG_PATH_ONCHIP && !onchip_ok) {
     free_all(h);
     delete h;
@@ -548,7 +559,8 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   d.max_restarts = h->opts.max_restarts < 0 ? 0 : h->opts.max_restarts;
   d.variant = h->opts.variant;
   d.inner_tol = h->opts.inner_tol;
-  d.onchip_slots = (int32_t)std::min<int64_t>(h->sell.onchip_slots, INT32_MAX);
+  d.onchip_slots = (int32_t)std::min<int64_t>(h->onchip_nc == 16 ? h->sell.onchip_slots16 : h->sell.onchip_slots,
+                                               INT32_MAX);
   d.box_g = h->box_g;
   d.box_r = h->box_r;
   d.box_cd = h->box_cd;
@@ -586,7 +598,7 @@ ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double*
   } else if (h->path == PPCG_PATH_ONCHIP) {
     const int32_t* d_list = single_work_list();
     if (!d_list) { set_error("ppcg_solve: could not allocate the cluster work list"); return PPCG_ERR_OOM; }
-    e = launch_onchip(h->d_desc, d_list, d_list + 1, 1, 0, h->onchip_smem, st);
+    e = launch_onchip(h->d_desc, d_list, d_list + 1, 1, 0, h->onchip_smem, h->onchip_nc, st);
   } else {
     const int32_t* d_list = single_work_list();
     if (!d_list) { set_error("ppcg_solve: could not allocate the cluster work list"); return PPCG_ERR_OOM; }
@@ -631,8 +643,8 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
     prepare_control(h, tol[i], maxit[i], st);
     (h->path == PPCG_PATH_CLUSTER ? cl : h->path == PPCG_PATH_ONCHIP ? oc : gr).push_back(i);
   }
-  // On-chip systems: one launch of clusters (one system per cluster at a time, longest
-  // first) on a side stream, overlapping the cluster-path launch below.
+  // On-chip systems: one launch of clusters per cluster size (one system per cluster at a
+  // time, longest first) on a side stream, overlapping the cluster-path launch below.
   cudaEvent_t oc_done = nullptr;
   if (!oc.empty()) {
     cudaStream_t side = nullptr;
@@ -643,44 +655,53 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
     }
     cudaEventRecord(fork, st);
     cudaStreamWaitEvent(side, fork, 0);
-    const int m = (int)oc.size();
-    std::vector<SysDesc> descs(m);
-    size_t smem = 0;
-    std::vector<int> order(m);
-    for (int k = 0; k < m; k++) {
-      descs[k] = hs[oc[k]]->desc;
-      smem = std::max(smem, hs[oc[k]]->onchip_smem);
-      order[k] = k;
-    }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hs[oc[0]]->device);
-    const int nclusters = std::max(1, std::min(m, sms / kClusterSize));
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int c) { return hs[oc[a]]->sell.nslots > hs[oc[c]]->sell.nslots; });
-    std::vector<std::vector<int>> lists(nclusters);
-    std::vector<double> load(nclusters, 0.0);
-    for (int k : order) {
-      const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-      lists[c].push_back(k);
-      load[c] += (double)hs[oc[k]]->sell.nslots + 32.0 * (double)hs[oc[k]]->n;
+    cudaError_t e = cudaSuccess;
+    for (int nc : {16, 8}) {
+      std::vector<int> grp;
+      for (int i : oc)
+        if (hs[i]->onchip_nc == nc) grp.push_back(i);
+      if (grp.empty() || e != cudaSuccess) continue;
+      const int m = (int)grp.size();
+      std::vector<SysDesc> descs(m);
+      size_t smem = 0;
+      std::vector<int> order(m);
+      for (int k = 0; k < m; k++) {
+        descs[k] = hs[grp[k]]->desc;
+        smem = std::max(smem, hs[grp[k]]->onchip_smem);
+        order[k] = k;
+      }
+      const int nclusters = std::max(1, std::min(m, sms / nc));
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int a, int c) { return hs[grp[a]]->sell.nslots > hs[grp[c]]->sell.nslots; });
+      std::vector<std::vector<int>> lists(nclusters);
+      std::vector<double> load(nclusters, 0.0);
+      for (int k : order) {
+        const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lists[c].push_back(k);
+        load[c] += (double)hs[grp[k]]->sell.nslots + 32.0 * (double)hs[grp[k]]->n;
+      }
+      std::vector<int32_t> flat, ptr(1, 0);
+      for (auto& l : lists) { for (int k : l) flat.push_back(k); ptr.push_back((int32_t)flat.size()); }
+      std::vector<int32_t> packed(ptr);
+      packed.insert(packed.end(), flat.begin(), flat.end());
+      SysDesc* d_descs = nullptr;
+      int32_t* d_lists = nullptr;
+      if (cudaMallocAsync((void**)&d_descs, m * sizeof(SysDesc), side) != cudaSuccess ||
+          cudaMallocAsync((void**)&d_lists, packed.size() * sizeof(int32_t), side) != cudaSuccess) {
+        cudaGetLastError();
+        cudaEventRecord(oc_done, side);
+        cudaStreamWaitEvent(st, oc_done, 0);
+        set_error("ppcg_batch_solve: out of device memory for the schedule");
+        return PPCG_ERR_OOM;
+      }
+      cudaMemcpyAsync(d_descs, descs.data(), m * sizeof(SysDesc), cudaMemcpyHostToDevice, side);
+      cudaMemcpyAsync(d_lists, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice, side);
+      e = launch_onchip(d_descs, d_lists + ptr.size(), d_lists, nclusters, 0, smem, nc, side);
+      cudaFreeAsync(d_descs, side);
+      cudaFreeAsync(d_lists, side);
     }
-    std::vector<int32_t> flat, ptr(1, 0);
-    for (auto& l : lists) { for (int k : l) flat.push_back(k); ptr.push_back((int32_t)flat.size()); }
-    std::vector<int32_t> packed(ptr);
-    packed.insert(packed.end(), flat.begin(), flat.end());
-    SysDesc* d_descs = nullptr;
-    int32_t* d_lists = nullptr;
-    if (cudaMallocAsync((void**)&d_descs, m * sizeof(SysDesc), side) != cudaSuccess ||
-        cudaMallocAsync((void**)&d_lists, packed.size() * sizeof(int32_t), side) != cudaSuccess) {
-      cudaGetLastError();
-      set_error("ppcg_batch_solve: out of device memory for the schedule");
-      return PPCG_ERR_OOM;
-    }
-    cudaMemcpyAsync(d_descs, descs.data(), m * sizeof(SysDesc), cudaMemcpyHostToDevice, side);
-    cudaMemcpyAsync(d_lists, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice, side);
-    cudaError_t e = launch_onchip(d_descs, d_lists + ptr.size(), d_lists, nclusters, 0, smem, side);
-    cudaFreeAsync(d_descs, side);
-    cudaFreeAsync(d_lists, side);
     cudaEventRecord(oc_done, side);
     if (e != cudaSuccess) {
       cudaGetLastError();

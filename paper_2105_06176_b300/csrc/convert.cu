@@ -354,9 +354,12 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   out->nchunks = nchunks;
   out->nslots = nslots;
   {
-    int64_t per[kClusterSize] = {0};
-    for (int64_t c = 0; c < nchunks; c++) per[c % kClusterSize] += cptr[c + 1] - cptr[c];
-    out->onchip_slots = *std::max_element(per, per + kClusterSize);
+    int64_t per[16] = {0};
+    for (int64_t c = 0; c < nchunks; c++) per[c % 16] += cptr[c + 1] - cptr[c];
+    out->onchip_slots16 = *std::max_element(per, per + 16);
+    int64_t per8[8];
+    for (int r = 0; r < 8; r++) per8[r] = per[r] + per[r + 8];   // c % 8 == r  <=>  c % 16 in {r, r + 8}
+    out->onchip_slots = *std::max_element(per8, per8 + 8);
   }
   out->sigma = (int32_t)sigma;
   out->padding = nnz > n ? (double)(nslots - (nnz - n)) / (double)(nnz - n) : 0.0;

@@ -56,6 +56,7 @@ struct ppcg_ctx {
   std::vector<void*> allocs;
   int32_t path = PPCG_PATH_GRID;
   size_t onchip_smem = 0;   // dynamic shared memory per CTA of the on-chip path
+  int onchip_nc = 8;        // CTAs per on-chip cluster (8 or 16)
   int32_t box_g = 0, box_r = 0;      // matrix-free box stencil (box_g > 0)
   double box_cd = 0.0, box_co = 0.0;
   int shape = 0;       // grid-path launch shape (index into the kernel variants)

@@ -116,10 +116,12 @@ struct SysDesc {
 cudaError_t launch_grid(const SysDesc* d_desc, int shape, int grid, int budget, cudaStream_t st);
 cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
                             int nclusters, int budget, cudaStream_t st, bool spread = false);
+// On-chip path, clusters of nc = 8 or 16 CTAs (16: non-portable, where the device allows).
 cudaError_t launch_onchip(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
-                          int nclusters, int budget, size_t smem, cudaStream_t st);
-size_t onchip_smem_bytes(int64_t nchunks, int64_t slots);   // dynamic shared memory per CTA
-size_t onchip_smem_limit(int device);                       // largest the device allows
+                          int nclusters, int budget, size_t smem, int nc, cudaStream_t st);
+size_t onchip_smem_bytes(int64_t nchunks, int64_t slots, int nc);   // dynamic shared memory per CTA
+size_t onchip_smem_limit(int device);                               // largest the device allows
+bool onchip_cluster_fits(int nc, size_t smem);                      // can one such cluster run
 int grid_shape_count();
 int grid_threads(int shape);
 int grid_blocks_for_device(int device, int shape);
@@ -135,6 +137,7 @@ struct SellBuild {
   double seconds = 0.0;   // conversion wall time
   double dmin = 0.0, dmax = 0.0;   // extreme diagonal entries
   int64_t onchip_slots = 0;        // SELL slots of the fullest CTA when chunk c goes to CTA c % 8
+  int64_t onchip_slots16 = 0;      // the same for clusters of 16 CTAs
 };
 ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col,
                                 const double* d_val, int32_t sigma_req, bool want_fp32, bool sym_scale,

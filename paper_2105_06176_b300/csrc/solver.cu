@@ -88,6 +88,11 @@ __device__ __forceinline__ uint32_t cluster_rank() {
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
   return r;
 }
+__device__ __forceinline__ uint32_t cluster_nranks() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
 __device__ __forceinline__ void cluster_barrier() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -1904,9 +1909,10 @@ __global__ void __launch_bounds__(kClusterThreads, 4) k_cluster(const SysDesc* d
 }
 
 // ---------------------------------------------------------- on-chip small systems --
-// A system whose vectors and matrix fit in the shared memory of one 8-CTA cluster runs
-// entirely on chip: chunk c lives in CTA c % 8 as local chunk c / 8 (its FP64 vector tile
-// and its SELL slots), gathers of other CTAs' rows are distributed-shared-memory loads, and
+// A system whose vectors and matrix fit in the shared memory of one cluster of NC = 8 or 16
+// CTAs (the launch's cluster size) runs entirely on chip: chunk c lives in CTA c % NC as
+// local chunk c / NC (its FP64 vector tile and its SELL slots), gathers of other CTAs' rows
+// are distributed-shared-memory loads, and
 // the block partials are exchanged through shared memory as well.  No pass touches HBM or
 // L2 except for b and the diagonal (setup, true residual, replacement).  The same
 // control() drives it, so the iteration, its stopping rules, restarts and replacements are
@@ -1917,14 +1923,15 @@ constexpr int kOnchipThreads = 256;
 
 
 // Gather of one slot of the distributed vector tiles: row j is lane j % 32 of chunk j / 32,
-// held by CTA (j / 32) % 8 as its local chunk j / 256.
+// held by CTA (j / 32) % NC as its local chunk (j / 32) / NC (NC = 1 << lg).
 struct GatherDS {
   uint32_t tile;   // shared-memory address of the tile array (the same in every CTA)
   int slot;
+  uint32_t lg;     // log2 of the cluster size
   __device__ __forceinline__ double operator()(int32_t j) const {
     const uint32_t cj = (uint32_t)j >> 5;
-    const uint32_t off = (((cj >> 3) * (uint32_t)kNS64 + (uint32_t)slot) * kChunk + ((uint32_t)j & 31u)) * 8u;
-    return ld_dsmem(tile + off, cj & 7u);
+    const uint32_t off = (((cj >> lg) * (uint32_t)kNS64 + (uint32_t)slot) * kChunk + ((uint32_t)j & 31u)) * 8u;
+    return ld_dsmem(tile + off, cj & ((1u << lg) - 1u));
   }
 };
 
@@ -1970,6 +1977,7 @@ struct Onchip {
   int32_t* lptr;         // [nloc + 1] slot offset of each local chunk
   uint32_t tile_addr;
   int32_t nloc, rank, nchunks, n;
+  int32_t nc, lg;        // cluster size and its log2
 };
 
 #define FOR_LOCAL(O) for (int32_t lc = (int32_t)(threadIdx.x >> 5); lc < (O).nloc; lc += kOnchipThreads / 32)
@@ -1986,9 +1994,9 @@ __device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dot
       // rr1: u = M^-1 r, s = A p, q = M^-1 s.
       const bool x_zero = C.pass == P_SETUP1 && S.x_zero != 0 && !C.fallback;
       const bool rr = C.pass == P_RR1, p_zero = rr && (C.iter == 0 || C.restart);
-      const GatherDS gx{O.tile_addr, V_X}, gp{O.tile_addr, V_P};
+      const GatherDS gx{O.tile_addr, V_X, (uint32_t)O.lg}, gp{O.tile_addr, V_P, (uint32_t)O.lg};
       FOR_LOCAL(O) {
-        const int32_t c = lc * kClusterSize + O.rank;
+        const int32_t c = lc * O.nc + O.rank;
         if (c >= O.nchunks) continue;
         const int32_t row = c * kChunk + lane;
         const bool in = row < O.n;
@@ -2025,9 +2033,9 @@ __device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dot
       // w = Ahat r (= A u); rr2 also z = Ahat s (= A q); partials (r,u) (w,u) norm.
       const bool rr = C.pass == P_RR2;
       const int wcs = rr && (C.iter & 1) ? V_WB : V_WA;
-      const GatherDS gr{O.tile_addr, V_R}, gs{O.tile_addr, V_S};
+      const GatherDS gr{O.tile_addr, V_R, (uint32_t)O.lg}, gs{O.tile_addr, V_S, (uint32_t)O.lg};
       FOR_LOCAL(O) {
-        const int32_t c = lc * kClusterSize + O.rank;
+        const int32_t c = lc * O.nc + O.rank;
         if (c >= O.nchunks) continue;
         const bool in = c * kChunk + lane < O.n;
         double* t = O.tile + (int64_t)lc * kNS64 * kChunk + lane;
@@ -2052,9 +2060,9 @@ __device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dot
       const double alpha = C.alpha, beta = C.beta;
       const int wcs = (C.iter & 1) ? V_WB : V_WA;
       const int wns = (C.iter & 1) ? V_WA : V_WB;
-      const GatherDS gw{O.tile_addr, wcs};
+      const GatherDS gw{O.tile_addr, wcs, (uint32_t)O.lg};
       FOR_LOCAL(O) {
-        const int32_t c = lc * kClusterSize + O.rank;
+        const int32_t c = lc * O.nc + O.rank;
         if (c >= O.nchunks) continue;
         const bool in = c * kChunk + lane < O.n;
         double* t = O.tile + (int64_t)lc * kNS64 * kChunk + lane;
@@ -2091,7 +2099,7 @@ __device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dot
     }
     case P_NORM: {
       FOR_LOCAL(O) {
-        const int32_t c = lc * kClusterSize + O.rank;
+        const int32_t c = lc * O.nc + O.rank;
         if (c >= O.nchunks || c * kChunk + lane >= O.n) continue;
         const double v = O.tile[((int64_t)lc * kNS64 + (paper ? V_U : V_R)) * kChunk + lane];
         d.add(2, v, v);
@@ -2100,7 +2108,7 @@ __device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dot
     }
     case P_ZERO_X: {
       FOR_LOCAL(O) {
-        const int32_t c = lc * kClusterSize + O.rank;
+        const int32_t c = lc * O.nc + O.rank;
         if (c < O.nchunks && c * kChunk + lane < O.n) O.tile[((int64_t)lc * kNS64 + V_X) * kChunk + lane] = 0.0;
       }
       return false;
@@ -2115,7 +2123,7 @@ __device__ void onchip_tiles(const SysDesc& S, const Onchip& O, bool to_smem) {
   const int64_t per = (int64_t)kNS64 * kChunk;
   for (int64_t k = threadIdx.x; k < (int64_t)O.nloc * per; k += blockDim.x) {
     const int64_t lc = k / per, e = k % per;
-    const int64_t c = lc * kClusterSize + O.rank;
+    const int64_t c = lc * O.nc + O.rank;
     if (c >= O.nchunks) continue;
     double* g = S.v64 + c * per + e;
     if (to_smem) O.tile[k] = __ldcg(g); else __stcg(g, O.tile[k]);
@@ -2147,7 +2155,9 @@ __global__ void __launch_bounds__(kOnchipThreads, 1) k_onchip(const SysDesc* des
     O.nchunks = (int32_t)S.A.nchunks;
     O.n = (int32_t)S.A.n;
     O.rank = (int32_t)rank;
-    O.nloc = (O.nchunks + kClusterSize - 1) / kClusterSize;
+    O.nc = (int32_t)cluster_nranks();
+    O.lg = O.nc == 16 ? 4 : 3;
+    O.nloc = (O.nchunks + O.nc - 1) / O.nc;
     O.tile = reinterpret_cast<double*>(dyn);
     O.val = O.tile + (int64_t)O.nloc * kNS64 * kChunk;
     O.col = reinterpret_cast<int32_t*>(O.val + S.onchip_slots);
@@ -2158,14 +2168,14 @@ __global__ void __launch_bounds__(kOnchipThreads, 1) k_onchip(const SysDesc* des
       int32_t off = 0;
       for (int32_t lc = 0; lc < O.nloc; lc++) {
         O.lptr[lc] = off;
-        const int64_t c = (int64_t)lc * kClusterSize + rank;
+        const int64_t c = (int64_t)lc * O.nc + rank;
         if (c < O.nchunks) off += (int32_t)(__ldg(S.A.cptr + c + 1) - __ldg(S.A.cptr + c));
       }
       O.lptr[O.nloc] = off;
     }
     __syncthreads();
     for (int32_t lc = (int32_t)(threadIdx.x >> 5); lc < O.nloc; lc += kOnchipThreads / 32) {
-      const int64_t c = (int64_t)lc * kClusterSize + rank;
+      const int64_t c = (int64_t)lc * O.nc + rank;
       if (c >= O.nchunks) continue;
       const int64_t g0 = __ldg(S.A.cptr + c);
       const int cnt = O.lptr[lc + 1] - O.lptr[lc];
@@ -2193,17 +2203,16 @@ __global__ void __launch_bounds__(kOnchipThreads, 1) k_onchip(const SysDesc* des
       __syncthreads();
       cluster_barrier();
       if (partials && threadIdx.x < 32) {
-        // lane q < 8 reads rank q's partials; a fixed shuffle tree sums them (deterministic)
+        // lane q < NC reads rank q's partials; a fixed shuffle tree sums them (deterministic)
         const int lane = threadIdx.x;
         const uint32_t base = smem_u32(&sh.part[C.parity][0]);
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        if (lane < kClusterSize) {
+        if (lane < O.nc) {
           s0 = ld_dsmem(base, lane);
           s1 = ld_dsmem(base + 8, lane);
           s2 = ld_dsmem(base + 16, lane);
         }
-#pragma unroll
-        for (int o = kClusterSize / 2; o > 0; o >>= 1) {
+        for (int o = O.nc / 2; o > 0; o >>= 1) {
           s0 += __shfl_down_sync(kFull, s0, o);
           s1 += __shfl_down_sync(kFull, s1, o);
           s2 += __shfl_down_sync(kFull, s2, o);
@@ -2318,8 +2327,8 @@ cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const
   return cudaLaunchKernelEx(&cfg, k_cluster, d_descs, d_list, d_list_ptr, budget);
 }
 
-size_t onchip_smem_bytes(int64_t nchunks, int64_t slots) {
-  const int64_t nloc = (nchunks + kClusterSize - 1) / kClusterSize;
+size_t onchip_smem_bytes(int64_t nchunks, int64_t slots, int nc) {
+  const int64_t nloc = (nchunks + nc - 1) / nc;
   return (size_t)(nloc * kNS64 * kChunk * 8 + slots * 12 + (nloc + 1) * 4);
 }
 
@@ -2330,18 +2339,57 @@ size_t onchip_smem_limit(int device) {
   return optin > (int)stat ? (size_t)optin - stat : 0;
 }
 
+// The 16-CTA cluster is beyond the portable size: the kernel must opt in (once per device).
+static cudaError_t allow_cluster16() {
+  static std::mutex mu;
+  static std::map<int, cudaError_t> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find(dev);
+  if (it != done.end()) return it->second;
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_onchip, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) cudaGetLastError();
+  done[dev] = e;
+  return e;
+}
+
+bool onchip_cluster_fits(int nc, size_t smem) {
+  if (nc == 16 && allow_cluster16() != cudaSuccess) return false;
+  if (ensure_smem_attr((const void*)k_onchip, smem) != cudaSuccess) { cudaGetLastError(); return false; }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nc);
+  cfg.blockDim = dim3(kOnchipThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = nc;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (void*)k_onchip, &cfg) != cudaSuccess) { cudaGetLastError(); return false; }
+  return n >= 1;
+}
+
 cudaError_t launch_onchip(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
-                          int nclusters, int budget, size_t smem, cudaStream_t st) {
+                          int nclusters, int budget, size_t smem, int nc, cudaStream_t st) {
+  if (nc != 8 && nc != 16) return cudaErrorInvalidValue;
+  if (nc == 16) {
+    cudaError_t e = allow_cluster16();
+    if (e != cudaSuccess) return e;
+  }
   cudaError_t e = ensure_smem_attr((const void*)k_onchip, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kClusterSize * nclusters);
+  cfg.gridDim = dim3(nc * nclusters);
   cfg.blockDim = dim3(kOnchipThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kClusterSize;
+  at[0].val.clusterDim.x = nc;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
