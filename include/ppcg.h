@@ -147,7 +147,11 @@ typedef struct {
   double rel_res_recursive;  /* stopping norm at exit, divided by ||b|| (REL_R) or absolute (PAPER_U_ABS) */
   double rel_res_true;       /* ||b - A x||_2 / ||b||_2 at exit, FP64 (0 when b = 0) */
   double seconds;            /* device time of the solve (globaltimer), setup and final residual included */
-  double bytes_per_iter;     /* algorithmic bytes of one iteration: (v+4) nnz + 4 (N+1) + 17 v N */
+  double bytes_per_iter;     /* algorithmic bytes of one iteration, v = 8 (FP64) or 4 (FP32 modes):
+                                (v+4) nnz + 4 (N+1) + 17 v N (matrix values and columns, row
+                                pointers, 17 vector streams); Jacobi-scaled: (v+4)(nnz - N) +
+                                4 (N+1) + 13 v N; matrix-free box stencil: 21 v N (17 vector
+                                streams and two stage arrays).  SELL padding is not counted. */
   double bnorm;              /* ||b||_2 */
   int32_t fp64_fallback;     /* FP32_IR: 1 when a refinement step failed to halve the FP64 residual and
                                 the solve finished with the FP64 iteration from the previous x;
