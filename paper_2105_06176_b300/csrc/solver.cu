@@ -1209,7 +1209,41 @@ __device__ __forceinline__ bool scalars(Ctl& c, int it) {
 // otherwise nothing is written and the general path takes the step.  (The control step is
 // a serial chain run by one thread per CTA on every iteration; with the control block in
 // shared memory each of its field accesses is a dependent round trip.)
+// The same for the FP32_RU iteration step (S_U_AFTER_ITER, then S_U_TOP continuing).
+__device__ __forceinline__ bool control_fast_ru(Ctl& c, const SysDesc& S, int iter_end) {
+  const int iter = c.iter + 1, inner = c.inner_iter + 1;
+  const double gamma_prev = c.gamma, alpha_prev = c.alpha;
+  const double gamma = c.red[0], delta = c.red[1];
+  const double norm = sqrt(c.red[2]);
+  const double rmax = fmax(c.rmax, norm);
+  if (iter >= iter_end) return false;
+  if (!isfinite(gamma) || !isfinite(delta) || !isfinite(norm)) return false;
+  if (c.last_rr_iter != iter) {
+    const bool periodic = S.rr_period > 0 && iter - c.last_rr_iter >= S.rr_period;
+    if (periodic || norm <= S.inner_tol * rmax || norm <= S.tol * c.bnorm || iter >= S.maxit) return false;
+  }
+  const double beta = gamma / gamma_prev;
+  const double den = delta - beta * gamma / alpha_prev;
+  if (!(gamma > 0.0) || !(den > 0.0)) return false;
+  const double alpha = gamma / den;
+  c.gamma_prev = gamma_prev;
+  c.alpha_prev = alpha_prev;
+  c.iter = iter;
+  c.inner_iter = inner;
+  c.restart = 0;
+  c.gamma = gamma;
+  c.delta = delta;
+  c.norm = norm;
+  c.rmax = rmax;
+  c.beta = beta;
+  c.alpha = alpha;
+  c.first = 0;
+  c.pass = P_ITER;
+  return true;
+}
+
 __device__ __forceinline__ bool control_fast(Ctl& c, const SysDesc& S, int iter_end) {
+  if (c.state == S_U_AFTER_ITER) return control_fast_ru(c, S, iter_end);
   if (c.state != S_AFTER_ITER) return false;
   const int iter = c.iter + 1;
   const double gamma_prev = c.gamma, alpha_prev = c.alpha;
