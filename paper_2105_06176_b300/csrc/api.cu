@@ -710,7 +710,10 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
       return PPCG_ERR_CUDA;
     }
   }
-  // Cluster-path systems: one persistent launch; longest-first schedule over the clusters.
+  // Cluster-path systems: one persistent launch; the clusters take systems longest first
+  // from a shared counter (list scheduling: an estimate that is off for some systems --
+  // iteration counts differ between families of the same size -- only reorders the queue).
+  // Estimate: padded slots x sqrt(n), the growth of CG's iteration count on 2-D stencils.
   if (!cl.empty()) {
     const int m = (int)cl.size();
     std::vector<SysDesc> descs(m);
@@ -718,38 +721,26 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
     for (int k = 0; k < m; k++) {
       descs[k] = hs[cl[k]]->desc;
       const double n = (double)hs[cl[k]]->n;
-      cost[k] = (double)hs[cl[k]]->sell.nslots * std::pow(n, 0.4);
+      cost[k] = ((double)hs[cl[k]]->sell.nslots + 32.0 * n) * std::sqrt(n);
     }
-    int nclusters = std::min(m, max_active_clusters(hs[cl[0]]->device));
-    std::vector<int> order(m);
+    const int nclusters = std::min(m, max_active_clusters(hs[cl[0]]->device));
+    std::vector<int32_t> order(m);
     for (int k = 0; k < m; k++) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-    std::vector<std::vector<int>> lists(nclusters);
-    std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> pq;
-    for (int c = 0; c < nclusters; c++) pq.push({0.0, c});
-    for (int k : order) {
-      auto top = pq.top();
-      pq.pop();
-      lists[top.second].push_back(k);
-      pq.push({top.first + cost[k], top.second});
-    }
-    std::vector<int32_t> flat, ptr(1, 0);
-    for (auto& l : lists) { for (int k : l) flat.push_back(k); ptr.push_back((int32_t)flat.size()); }
-    std::vector<int32_t> packed(ptr);
-    packed.insert(packed.end(), flat.begin(), flat.end());
     SysDesc* d_descs = nullptr;
-    int32_t* d_lists = nullptr;
+    int32_t* d_order = nullptr;
     if (cudaMallocAsync((void**)&d_descs, m * sizeof(SysDesc), st) != cudaSuccess ||
-        cudaMallocAsync((void**)&d_lists, packed.size() * sizeof(int32_t), st) != cudaSuccess) {
+        cudaMallocAsync((void**)&d_order, (m + 1) * sizeof(int32_t), st) != cudaSuccess) {
       cudaGetLastError();
       set_error("ppcg_batch_solve: out of device memory for the schedule");
       return PPCG_ERR_OOM;
     }
     cudaMemcpyAsync(d_descs, descs.data(), m * sizeof(SysDesc), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(d_lists, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-    cudaError_t e = launch_clusters(d_descs, d_lists + ptr.size(), d_lists, nclusters, 0, st);
+    cudaMemcpyAsync(d_order, order.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(d_order + m, 0, sizeof(int32_t), st);   // the take counter
+    cudaError_t e = launch_clusters(d_descs, d_order, nullptr, nclusters, 0, st, false, d_order + m, m);
     cudaFreeAsync(d_descs, st);
-    cudaFreeAsync(d_lists, st);
+    cudaFreeAsync(d_order, st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error("ppcg_batch_solve: cluster launch failed: %s", cudaGetErrorString(e));

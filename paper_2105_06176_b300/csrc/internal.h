@@ -114,8 +114,10 @@ struct SysDesc {
 
 // Launchers (solver.cu)
 cudaError_t launch_grid(const SysDesc* d_desc, int shape, int grid, int budget, cudaStream_t st);
+// d_next != nullptr: dynamic schedule over d_list[0..m) (see k_cluster); *d_next must be 0.
 cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
-                            int nclusters, int budget, cudaStream_t st, bool spread = false);
+                            int nclusters, int budget, cudaStream_t st, bool spread = false,
+                            int32_t* d_next = nullptr, int32_t m = 0);
 // On-chip path, clusters of nc = 8 or 16 CTAs (16: non-portable, where the device allows).
 cudaError_t launch_onchip(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
                           int nclusters, int budget, size_t smem, int nc, cudaStream_t st);

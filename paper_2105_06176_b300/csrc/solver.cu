@@ -1931,15 +1931,41 @@ const GridShape kGridShapes[] = {
 };
 constexpr int kNumGridShapes = (int)(sizeof(kGridShapes) / sizeof(kGridShapes[0]));
 
+// Cluster path.  Static schedule (next == nullptr): cluster c runs list[list_ptr[c] ..
+// list_ptr[c + 1]).  Dynamic schedule: every cluster takes the next entry of list (ordered
+// longest first) from the counter *next until m entries are taken -- list scheduling, which
+// absorbs the errors of any cost estimate.  A system's result does not depend on the
+// cluster that runs it.
 __global__ void __launch_bounds__(kClusterThreads, 4) k_cluster(const SysDesc* descs, const int32_t* list,
-                                                             const int32_t* list_ptr, int budget) {
+                                                             const int32_t* list_ptr, int budget,
+                                                             int32_t* next, int32_t m) {
   __shared__ SharedT<kSmCluster> sh;
+  __shared__ int32_t sh_take;
   ClusterGroup g;
   unsigned cid;
   unsigned phases = 0;
   asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
-  for (int k = list_ptr[cid]; k < list_ptr[cid + 1]; k++)
+  if (!next) {
+    for (int k = list_ptr[cid]; k < list_ptr[cid + 1]; k++)
+      run_system<false>(g, descs + list[k], budget, sh, nullptr, nullptr, phases);
+    return;
+  }
+  const uint32_t rank = cluster_rank();
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) sh_take = atomicAdd(next, 1);
+    __syncthreads();
+    cluster_barrier();   // rank 0's entry is visible to the cluster
+    int32_t k;
+    {
+      uint32_t remote;
+      asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_addr(&sh_take)), "r"(0u));
+      asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(k) : "r"(remote));
+    }
+    __syncthreads();
+    cluster_barrier();   // everyone has read it before rank 0 takes the next one
+    if (k >= m) break;
     run_system<false>(g, descs + list[k], budget, sh, nullptr, nullptr, phases);
+  }
 }
 
 // ---------------------------------------------------------- on-chip small systems --
@@ -2341,7 +2367,7 @@ cudaError_t ensure_smem_attr(const void* fn, size_t bytes) {
 }
 
 cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
-                            int nclusters, int budget, cudaStream_t st, bool spread) {
+                            int nclusters, int budget, cudaStream_t st, bool spread, int32_t* d_next, int32_t m) {
   // spread: request enough dynamic shared memory that no two CTAs share an SM, so a lone
   // cluster gets the FP64 pipes of 8 SMs instead of being packed onto two.
   const int spread_smem = 120 * 1024;
@@ -2358,7 +2384,7 @@ cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_cluster, d_descs, d_list, d_list_ptr, budget);
+  return cudaLaunchKernelEx(&cfg, k_cluster, d_descs, d_list, d_list_ptr, budget, d_next, m);
 }
 
 size_t onchip_smem_bytes(int64_t nchunks, int64_t slots, int nc) {
