@@ -710,37 +710,55 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
       return PPCG_ERR_CUDA;
     }
   }
-  // Cluster-path systems: one persistent launch; the clusters take systems longest first
-  // from a shared counter (list scheduling: an estimate that is off for some systems --
-  // iteration counts differ between families of the same size -- only reorders the queue).
-  // Estimate: padded slots x sqrt(n), the growth of CG's iteration count on 2-D stencils.
+  // Cluster-path systems: one persistent launch, systems ordered longest first by an
+  // estimate.  Up to two systems per cluster: a static longest-processing-time assignment
+  // (each cluster's first system is one of the longest, the rest fill the least loaded
+  // clusters), which leaves the critical longest solves the least contended.  More: the
+  // clusters take systems from a shared counter (list scheduling, which absorbs the
+  // estimate's errors; 1,024 systems: 1.78 -> 1.19 s).  Results do not depend on either.
   if (!cl.empty()) {
     const int m = (int)cl.size();
     std::vector<SysDesc> descs(m);
     std::vector<double> cost(m);
     for (int k = 0; k < m; k++) {
       descs[k] = hs[cl[k]]->desc;
-      const double n = (double)hs[cl[k]]->n;
-      cost[k] = ((double)hs[cl[k]]->sell.nslots + 32.0 * n) * std::sqrt(n);
+      cost[k] = cluster_solve_cost(hs[cl[k]], 0);
     }
     const int nclusters = std::min(m, max_active_clusters(hs[cl[0]]->device));
     std::vector<int32_t> order(m);
     for (int k = 0; k < m; k++) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    const bool dynamic = m > 2 * nclusters;
+    std::vector<int32_t> packed;   // dynamic: order, counter; static: list_ptr, lists
+    if (dynamic) {
+      packed = order;
+      packed.push_back(0);
+    } else {
+      std::vector<std::vector<int>> lists(nclusters);
+      std::vector<double> load(nclusters, 0.0);
+      for (int k : order) {
+        const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lists[c].push_back(k);
+        load[c] += cost[k];
+      }
+      packed.push_back(0);
+      for (auto& l : lists) packed.push_back(packed.back() + (int32_t)l.size());
+      for (auto& l : lists) packed.insert(packed.end(), l.begin(), l.end());
+    }
     SysDesc* d_descs = nullptr;
-    int32_t* d_order = nullptr;
+    int32_t* d_lists = nullptr;
     if (cudaMallocAsync((void**)&d_descs, m * sizeof(SysDesc), st) != cudaSuccess ||
-        cudaMallocAsync((void**)&d_order, (m + 1) * sizeof(int32_t), st) != cudaSuccess) {
+        cudaMallocAsync((void**)&d_lists, packed.size() * sizeof(int32_t), st) != cudaSuccess) {
       cudaGetLastError();
       set_error("ppcg_batch_solve: out of device memory for the schedule");
       return PPCG_ERR_OOM;
     }
     cudaMemcpyAsync(d_descs, descs.data(), m * sizeof(SysDesc), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(d_order, order.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(d_order + m, 0, sizeof(int32_t), st);   // the take counter
-    cudaError_t e = launch_clusters(d_descs, d_order, nullptr, nclusters, 0, st, false, d_order + m, m);
+    cudaMemcpyAsync(d_lists, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    cudaError_t e = dynamic ? launch_clusters(d_descs, d_lists, nullptr, nclusters, 0, st, false, d_lists + m, m)
+                            : launch_clusters(d_descs, d_lists + nclusters + 1, d_lists, nclusters, 0, st);
     cudaFreeAsync(d_descs, st);
-    cudaFreeAsync(d_order, st);
+    cudaFreeAsync(d_lists, st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error("ppcg_batch_solve: cluster launch failed: %s", cudaGetErrorString(e));

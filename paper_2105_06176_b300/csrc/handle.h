@@ -1,5 +1,6 @@
 // Solver handle internals shared by the ABI layer (api.cu) and the server (server.cu).
 #pragma once
+#include <cmath>
 #include <cstring>
 #include <utility>
 #include <vector>
@@ -89,5 +90,19 @@ void prepare_control(ppcg_ctx* h, double tol, int32_t maxit, cudaStream_t st);
 // Device bytes a handle of this size will allocate (estimate used for admission).
 size_t footprint_bytes(int64_t n, int64_t nnz, int32_t precision);
 bool is_device_ptr(const void* p);
+
+// Estimated device time of a cluster-path solve (iterations = 0: the whole solve), used only
+// to order the clusters' work queue.  Iterations grow like the grid side, n^(1/2) for 2-D
+// stencils (about 4 off-diagonals per row) and n^(1/3) for 3-D ones and geometric graphs;
+// an iteration costs a fixed ~8 us of control and barriers plus its bytes at ~100 GB/s (a
+// cluster's share of HBM when the GPU is full).
+inline double cluster_solve_cost(const ppcg_ctx* h, double iterations) {
+  const double n = (double)(h->n > 0 ? h->n : 1);
+  const double offdiag = (double)(h->nnz - h->n) / n;
+  const double it = iterations > 0 ? iterations : 4.3 * std::pow(n, offdiag <= 4.5 ? 0.5 : 1.0 / 3.0);
+  const double v = h->opts.precision == PPCG_FP64 ? 8.0 : 4.0;
+  const double bytes = (double)h->sell.nslots * (v + 4.0) + 17.0 * v * n;
+  return it * (8e-6 + bytes / 1e11);
+}
 
 }  // namespace ppcg

@@ -168,28 +168,32 @@ bool run_cluster_epoch(ppcg_srv* S, const std::vector<Slot*>& slots) {
     const double n = (double)std::max<int64_t>(slots[k]->h->n, 1);
     const double it = std::min(64.0 * S->epoch_iters, std::max(2.0, S->epoch_iters * 131072.0 / n));
     descs[k].budget = (int32_t)it;
-    cost[k] = (double)slots[k]->h->sell.nslots * it;
+    cost[k] = cluster_solve_cost(slots[k]->h, it);
   }
-  int nclusters = std::min(m, max_active_clusters(S->device));
-  std::vector<int> order(m);
+  // Longest first: a static longest-processing-time assignment while there are at most two
+  // solves per cluster, else the clusters take solves from a shared counter (as in
+  // ppcg_batch_solve).
+  const int nclusters = std::min(m, max_active_clusters(S->device));
+  std::vector<int32_t> order(m);
   for (int k = 0; k < m; k++) order[k] = k;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-  std::vector<std::vector<int>> lists(nclusters);
-  std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> pq;
-  for (int c = 0; c < nclusters; c++) pq.push({0.0, c});
-  for (int k : order) {
-    auto top = pq.top();
-    pq.pop();
-    lists[top.second].push_back(k);
-    pq.push({top.first + cost[k], top.second});
+  const bool dynamic = m > 2 * nclusters;
+  std::vector<int32_t> packed;   // dynamic: order, counter; static: list_ptr, lists
+  if (dynamic) {
+    packed = order;
+    packed.push_back(0);
+  } else {
+    std::vector<std::vector<int>> lists(nclusters);
+    std::vector<double> load(nclusters, 0.0);
+    for (int k : order) {
+      const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      lists[c].push_back(k);
+      load[c] += cost[k];
+    }
+    packed.push_back(0);
+    for (auto& l : lists) packed.push_back(packed.back() + (int32_t)l.size());
+    for (auto& l : lists) packed.insert(packed.end(), l.begin(), l.end());
   }
-  std::vector<int32_t> packed(1, 0), flat;
-  for (auto& l : lists) {
-    for (int k : l) flat.push_back(k);
-    packed.push_back((int32_t)flat.size());
-  }
-  const size_t nptr = packed.size();
-  packed.insert(packed.end(), flat.begin(), flat.end());
   if ((size_t)m > S->cap || packed.size() > 2 * S->cap + 2) {
     cudaFree(S->d_descs);
     cudaFree(S->d_lists);
@@ -203,8 +207,12 @@ bool run_cluster_epoch(ppcg_srv* S, const std::vector<Slot*>& slots) {
   }
   cudaMemcpyAsync(S->d_descs, descs.data(), m * sizeof(SysDesc), cudaMemcpyHostToDevice, S->s_exec);
   cudaMemcpyAsync(S->d_lists, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice, S->s_exec);
-  return launch_clusters(S->d_descs, S->d_lists + nptr, S->d_lists, nclusters, S->epoch_iters, S->s_exec) ==
-         cudaSuccess;
+  const cudaError_t e =
+      dynamic ? launch_clusters(S->d_descs, S->d_lists, nullptr, nclusters, S->epoch_iters, S->s_exec, false,
+                                S->d_lists + m, m)
+              : launch_clusters(S->d_descs, S->d_lists + nclusters + 1, S->d_lists, nclusters, S->epoch_iters,
+                                S->s_exec);
+  return e == cudaSuccess;
 }
 
 void exec_loop(ppcg_srv* S) {
