@@ -8,7 +8,6 @@
 #include <mutex>
 #include <string>
 #include <unordered_map>
-#include <queue>
 #include <vector>
 
 #include "handle.h"

@@ -194,6 +194,23 @@ def test_batch_bitwise_equals_solo(precision):
             assert abs(it0 - oracle.pipecg(a, b, tol=1e-8, maxit=20000)["result"]["iters"]) <= 2
 
 
+def test_batch_dynamic_schedule_bitwise_equals_solo():
+    """More than two systems per cluster: the clusters take systems from a shared counter, in
+    an order that depends on timing; every result is still bitwise the solo result."""
+    m = pp()
+    specs = synth.batch_mix(400, 23, lo=1e3, hi=6e3)
+    systems = [synth.build_spec(sp) for sp in specs]
+    solvers = [m.Solver.from_csr(a, path=m.PATH_CLUSTER) for a, _ in systems]
+    bs = [dev(b) for _, b in systems]
+    xs = [torch.empty_like(b) for b in bs]
+    infos = m.batch_solve(solvers, bs, xs, tol=1e-8, maxit=20000)
+    for k in range(0, len(systems), 37):
+        x0, i0 = solvers[k].solve(bs[k], tol=1e-8, maxit=20000)
+        assert infos[k].status == i0.status == m.OK and infos[k].iters == i0.iters
+        assert np.array_equal(xs[k].cpu().numpy(), x0.cpu().numpy())
+    assert all(i.status == m.OK for i in infos)
+
+
 def test_batch_fixed_k_parity():
     m = pp()
     systems = _batch_systems()[:6]
