@@ -1150,10 +1150,9 @@ __device__ void write_block_partials(double a0, double a1, double a2, double* sl
 }
 
 // Sum the group's P partial slots in a fixed order; every CTA obtains identical bits.
-__device__ void group_reduce(const double* part, int P, double* out, double* sm) {
+__device__ void group_reduce(const double* part, int P, double* out) {
   // warp v (v < 3) sums value v over the P partial slots (lane-strided, then a shuffle
   // tree): three warps' worth of FP64 adds, the other warps idle.  Fixed order.
-  (void)sm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp < 3) {
     double v = 0.0;
@@ -1881,7 +1880,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
     }
     if (partials) {
       if constexpr (G::kCluster) cluster_reduce(sh.part[C.parity], C.red);
-      else group_reduce(S.part + (size_t)C.parity * P * 4, P, C.red, sh.sm);
+      else group_reduce(S.part + (size_t)C.parity * P * 4, P, C.red);
       if (threadIdx.x == 0) C.parity ^= 1;
     }
   }
