@@ -7,8 +7,8 @@
  * Architectures", arXiv 2105.06176, Sec. III-B, with the Jacobi preconditioner
  * M = diag(A) and the CSR input format of Sec. V-A.  Every iteration runs on the GPU:
  * one fused pass computes n = A M^-1 w for its rows and updates z, q, s, p, x, r, u, w
- * (lines 10-17 and 21-22 of the algorithm), emitting block partials of gamma = (r, u),
- * delta = (w, u) and the stopping norm (lines 18-20); alpha and beta (lines 5-9) are
+ * (the algorithm's vector updates, preconditioner and SpMV), emitting block partials of
+ * gamma = (r, u), delta = (w, u) and the stopping norm; alpha and beta are
  * formed on the device, so the host never waits inside a solve.
  *
  * Conventions shared by every call:

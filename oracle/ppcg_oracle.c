@@ -24,7 +24,7 @@
  *     (residual replacement, not in the paper) and the iteration continues.
  *   - rr_period > 0 additionally replaces residuals every rr_period iterations.
  *   - jacobi_elim (a variant, not the paper's literal algorithm): with a diagonal M the
- *     recurrences of lines 11 and 16 reproduce q = M^-1 s and u = M^-1 r exactly in exact
+ *     recurrences of q and u in the update block reproduce q = M^-1 s and u = M^-1 r in exact
  *     arithmetic, so the variant computes q and u from s and r after their updates instead.
  *   - Restart on breakdown (not in the paper): when the alpha denominator is not positive
  *     after the first iteration -- which pipelined PCG meets near its attainable accuracy --
@@ -159,16 +159,16 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
     goto done;
   }
 
-  /* line 1: r0 = b - A x0; u0 = M^-1 r0; w0 = A u0 */
+  /* setup: r0 = b - A x0; u0 = M^-1 r0; w0 = A u0 */
   oracle_spmv(n, rp, ci, v, x, tmp);
   for (int64_t i = 0; i < n; i++) r[i] = b[i] - tmp[i];
   apply_jacobi(n, d, r, u);
   oracle_spmv(n, rp, ci, v, u, w);
-  /* line 2: gamma0 = (r0, u0); delta = (w0, u0); norm0 */
+  /* setup: gamma0 = (r0, u0); delta = (w0, u0); norm0 */
   gamma = dot(sum_mode, n, r, u);
   delta = dot(sum_mode, n, w, u);
   norm = norm_mode ? sqrt(dot(sum_mode, n, u, u)) : sqrt(dot(sum_mode, n, r, r));
-  /* line 3: m0 = M^-1 w0; n0 = A m0 */
+  /* setup: m0 = M^-1 w0; n0 = A m0 */
   apply_jacobi(n, d, w, m);
   oracle_spmv(n, rp, ci, v, m, nv);
 
@@ -207,7 +207,7 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
     }
     if (it >= maxit) { status = OR_ERR_NOT_CONVERGED; break; }
     if (!isfinite(gamma) || !isfinite(delta)) { status = OR_ERR_NONFINITE; break; }
-    /* lines 5-9: scalars */
+    /* scalars: beta, alpha */
     if (it > 0 && !restart) {
       beta = gamma / gamma_prev;
       double den = delta - beta * gamma / alpha_prev;
@@ -240,7 +240,7 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
     restart = 0;
     if (alpha_hist) alpha_hist[it] = alpha;
     if (beta_hist) beta_hist[it] = beta;
-    /* lines 10-17: z, q, s, p, then x, r, u, w */
+    /* vector updates: z, q, s, p, then x, r, u, w */
     for (int64_t i = 0; i < n; i++) {
       z[i] = nv[i] + beta * z[i];
       s[i] = w[i] + beta * s[i];
@@ -251,13 +251,13 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
       u[i] = jacobi_elim ? r[i] / d[i] : u[i] - alpha * q[i];
       w[i] = w[i] - alpha * z[i];
     }
-    /* lines 18-20: gamma_{i+1}, delta, norm_{i+1} */
+    /* dot products: gamma_{i+1}, delta, norm_{i+1} */
     gamma_prev = gamma;
     alpha_prev = alpha;
     gamma = dot(sum_mode, n, r, u);
     delta = dot(sum_mode, n, w, u);
     norm = norm_mode ? sqrt(dot(sum_mode, n, u, u)) : sqrt(dot(sum_mode, n, r, r));
-    /* lines 21-22: m = M^-1 w; n = A m */
+    /* preconditioner and SpMV: m = M^-1 w; n = A m */
     apply_jacobi(n, d, w, m);
     oracle_spmv(n, rp, ci, v, m, nv);
   }
@@ -307,11 +307,11 @@ int oracle_pcg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
     status = OR_OK;
     goto done;
   }
-  /* line 1: r0 = b - A x0; u0 = M^-1 r0 */
+  /* setup: r0 = b - A x0; u0 = M^-1 r0 */
   oracle_spmv(n, rp, ci, v, x, tmp);
   for (int64_t i = 0; i < n; i++) r[i] = b[i] - tmp[i];
   apply_jacobi(n, d, r, u);
-  /* line 2: gamma0 = (u0, r0); norm0 */
+  /* setup: gamma0 = (u0, r0); norm0 */
   gamma = dot(sum_mode, n, u, r);
   norm = norm_mode ? sqrt(dot(sum_mode, n, u, u)) : sqrt(dot(sum_mode, n, r, r));
   status = OR_ERR_NOT_CONVERGED;
@@ -321,11 +321,11 @@ int oracle_pcg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
     if (it >= maxit) break;
     if (!isfinite(gamma)) { status = OR_ERR_NONFINITE; break; }
     if (!(gamma > 0.0)) { status = OR_ERR_BREAKDOWN; break; }
-    /* lines 4-8 */
+    /* beta */
     beta = it > 0 ? gamma / gamma_prev : 0.0;
-    /* line 9: p_i = u_i + beta p_{i-1} */
+    /* search direction: p_i = u_i + beta p_{i-1} */
     for (int64_t i = 0; i < n; i++) p[i] = u[i] + beta * p[i];
-    /* lines 10-12: s = A p; delta = (s, p); alpha = gamma / delta */
+    /* s = A p; delta = (s, p); alpha = gamma / delta */
     oracle_spmv(n, rp, ci, v, p, s);
     delta = dot(sum_mode, n, s, p);
     if (!isfinite(delta)) { status = OR_ERR_NONFINITE; break; }
@@ -333,13 +333,13 @@ int oracle_pcg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
     alpha = gamma / delta;
     if (alpha_hist) alpha_hist[it] = alpha;
     if (beta_hist) beta_hist[it] = beta;
-    /* lines 13-15 */
+    /* x, r and u = M^-1 r */
     for (int64_t i = 0; i < n; i++) {
       x[i] = x[i] + alpha * p[i];
       r[i] = r[i] - alpha * s[i];
     }
     apply_jacobi(n, d, r, u);
-    /* lines 16-17 */
+    /* gamma_{i+1} = (u, r), stopping norm */
     gamma_prev = gamma;
     gamma = dot(sum_mode, n, u, r);
     norm = norm_mode ? sqrt(dot(sum_mode, n, u, u)) : sqrt(dot(sum_mode, n, r, r));

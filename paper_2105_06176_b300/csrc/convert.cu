@@ -3,7 +3,7 @@
 //
 // The solver keeps the matrix column-scaled, Ahat = A D^-1 (or, for the Jacobi-scaled
 // variant, symmetrically scaled, D^-1/2 A D^-1/2, with the same unit diagonal), so that the preconditioner
-// apply and the SpMV of Alg. 2 lines 21-22 (m = M^-1 w; n = A m) become one product
+// apply and the SpMV of Alg. 2 (m = M^-1 w; n = A m) become one product
 // n = Ahat w with no per-iteration multiply by D^-1 inside the gather.  The scaling divides
 // (a_ij / a_jj), so every diagonal entry of Ahat is exactly 1.0: the SELL arrays hold the
 // off-diagonal entries only and the kernels add the diagonal term (w_i, or a_ii v_i for

@@ -93,9 +93,10 @@ __device__ __forceinline__ double na_row(const int64_t* rp, const int32_t* col, 
   return acc;
 }
 
-// One cluster of 8 CTAs runs the whole solve: setup (Alg. 2 lines 1-3), then one fused
-// phase per iteration (lines 10-22) with alpha/beta (lines 5-9) formed in every CTA from
-// the same partials, a cluster barrier between phases, and the final true residual.
+// One cluster of 8 CTAs runs the whole solve: the setup of Alg. 2, then one fused phase per
+// iteration (vector updates, dot products, preconditioner and SpMV) with alpha/beta formed in
+// every CTA from the same partials, a cluster barrier between phases, and the final true
+// residual.
 __global__ void __cluster_dims__(kNaCluster, 1, 1) __launch_bounds__(kNaThreads)
 k_solve_noalloc(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                 const double* __restrict__ val, const double* __restrict__ b, const double* x0,
@@ -148,7 +149,7 @@ k_solve_noalloc(int64_t n, const int64_t* __restrict__ rp, const int32_t* __rest
   if (red[0] != 0.0) { status = PPCG_ERR_NOT_SPD; done = true; }
 
   if (!done) {
-    // line 1 (first half): r0 = b - A x0; u0 = M^-1 r0; partial (b, b)
+    // setup, first half: r0 = b - A x0; u0 = M^-1 r0; partial (b, b)
     double pb = 0.0;
     for (int64_t i = t0; i < n; i += T) {
       double ri = b[i] - na_row(rp, col, val, x, i);
@@ -169,7 +170,7 @@ k_solve_noalloc(int64_t n, const int64_t* __restrict__ rp, const int32_t* __rest
     }
   }
   if (!done) {
-    // lines 1-2: w0 = A u0; gamma0 = (r0, u0); delta = (w0, u0); ||r0||
+    // setup: w0 = A u0; gamma0 = (r0, u0); delta = (w0, u0); ||r0||
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     for (int64_t i = t0; i < n; i += T) {
       double wi = na_row(rp, col, val, u, i);
@@ -203,7 +204,7 @@ k_solve_noalloc(int64_t n, const int64_t* __restrict__ rp, const int32_t* __rest
     double* wn = wv[(it + 1) & 1];
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     for (int64_t i = t0; i < n; i += T) {
-      // lines 21-22 of the previous step, fused: n_i = (A M^-1 w)_i
+      // preconditioner and SpMV of the previous step, fused: n_i = (A M^-1 w)_i
       double ni = 0.0;
       for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
         int32_t c = col[k];

@@ -7,12 +7,12 @@
 // One "pass" is one sweep over the system's rows in SELL-C-sigma order (one warp per
 // 32-row chunk, one lane per row); passes are separated by a group barrier.  The hot pass,
 // P_ITER, is the whole iteration of Alg. 2 for its rows:
-//     n_i  = A M^-1 w_i  = Ahat w_i                    (lines 21-22 of the previous step)
-//     z = n + beta z;  q = m + beta q;  s = w + beta s;  p = u + beta p     (lines 10-13)
-//     x += alpha p;    r -= alpha s;    u -= alpha q;    w -= alpha z       (lines 14-17)
-//     block partials of (r,u), (w,u) and the stopping norm                  (lines 18-20)
-// with w double-buffered (other CTAs still gather the old w), and alpha/beta (lines 5-9)
-// formed after the barrier from the partials in a fixed order.
+//     n_i  = A M^-1 w_i  = Ahat w_i           (preconditioner and SpMV of the previous step)
+//     z = n + beta z;  q = m + beta q;  s = w + beta s;  p = u + beta p     (vector updates)
+//     x += alpha p;    r -= alpha s;    u -= alpha q;    w -= alpha z
+//     block partials of (r,u), (w,u) and the stopping norm                  (dot products)
+// with w double-buffered (other CTAs still gather the old w), and alpha/beta formed after
+// the barrier from the partials in a fixed order.
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -389,7 +389,7 @@ __device__ __forceinline__ View<float, kNS32> view32(const SysDesc& S) {
 
 // -------------------------------------------------------------------------- passes --
 
-// P_SETUP1 (FP64), Alg. 2 line 1: r0 = b - A x0 ; u0 = M^-1 r0.  Partials (b,b), (r,r).
+// P_SETUP1 (FP64), Alg. 2 setup: r0 = b - A x0 ; u0 = M^-1 r0.  Partials (b,b), (r,r).
 __device__ __forceinline__ void pass_setup1(const SysDesc& S, const Lanes& L, Dots<double>& d, bool x_zero) {
   const DevMatrix& A = S.A;
   const Blk<double, kNS64> v{S.v64};
@@ -417,7 +417,7 @@ __device__ __forceinline__ void pass_setup1(const SysDesc& S, const Lanes& L, Do
   }
 }
 
-// P_SETUP2, Alg. 2 lines 1-2: w0 = A u0 (= Ahat r0) ; partials (r,u), (w,u), norm.
+// P_SETUP2, Alg. 2 setup: w0 = A u0 (= Ahat r0) ; partials (r,u), (w,u), norm.
 template <typename T, int NS>
 __device__ __forceinline__ void pass_setup2(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, Dots<T>& d,
                                             bool paper_norm) {
@@ -1187,7 +1187,7 @@ __device__ __forceinline__ bool may_pass(const Ctl& c, const SysDesc& S, double 
   return c.gamma * S.dmin <= slack * t * t;
 }
 
-// Alg. 2 lines 5-9.  Returns false (and sets status) on breakdown.
+// The scalars of Alg. 2 (beta, then alpha).  Returns false on breakdown.
 __device__ __forceinline__ bool scalars(Ctl& c, int it) {
   if (it > 0) {
     c.beta = c.gamma / c.gamma_prev;
