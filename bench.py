@@ -158,18 +158,29 @@ def reduce_over_ranks(dist, device, times, counts):
 
 def cpu_oracle_rate(a, b, k_lo=2, k_hi=8):
     """Oracle (plain single-thread C, FP64) iterations/s on the same system: the time of
-    k_hi - k_lo iterations, from two runs that share setup and final-residual costs."""
+    k_hi - k_lo iterations, from two runs that share setup and final-residual costs.  The
+    same source built with OpenMP (row loops on every host core, dot products sequential,
+    bitwise-identical iterates) is timed the same way and reported beside it."""
     import oracle
-    t0 = time.perf_counter()
-    oracle.pipecg(a, b, tol=0.0, maxit=k_lo)
-    t1 = time.perf_counter()
-    oracle.pipecg(a, b, tol=0.0, maxit=k_hi)
-    t2 = time.perf_counter()
-    per = max((t2 - t1) - (t1 - t0), 1e-9) / (k_hi - k_lo)
-    return {"value": 1.0 / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+
+    def rate(openmp):
+        oracle.lib(openmp)
+        t0 = time.perf_counter()
+        oracle.pipecg(a, b, tol=0.0, maxit=k_lo, openmp=openmp)
+        t1 = time.perf_counter()
+        oracle.pipecg(a, b, tol=0.0, maxit=k_hi, openmp=openmp)
+        t2 = time.perf_counter()
+        return 1.0 / (max((t2 - t1) - (t1 - t0), 1e-9) / (k_hi - k_lo)), t2 - t0
+
+    v1, s1 = rate(False)
+    vo, so = rate(True)
+    return {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{k_hi - k_lo} iterations of the 256^3 system (difference of {k_hi}- and {k_lo}-iteration "
                       f"runs), single-thread plain C, {os.cpu_count()} host cores present",
-            "seconds": t2 - t0}
+            "seconds": s1,
+            "openmp": {"value": vo, "unit": UNIT, "cores": oracle.threads(openmp=True), "kind": "oracle",
+                       "sample": "the same iterations, the same source built with -fopenmp (row loops "
+                                 "threaded, dot products sequential)", "seconds": so}}
 
 
 def _events():

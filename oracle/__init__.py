@@ -20,6 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ppcg_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 OK, ERR_ARG, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_NONFINITE = 0, -1, -2, -3, -4, -5
 NORM_REL_R, NORM_PAPER_U_ABS = 0, 1
@@ -37,25 +38,30 @@ class Result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
-def build(force=False):
-    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-    os.replace(tmp, _LIB)
-    return _LIB
+def build(force=False, openmp=False):
+    """Compile the oracle with gcc (no FMA contraction, no fast-math).  openmp: the same
+    source with -fopenmp (row loops over all host cores, bitwise-identical results), used
+    only to time the oracle on every core."""
+    out = _LIB_OMP if openmp else _LIB
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math"]
+                          + (["-fopenmp"] if openmp else [])
+                          + ["-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, out)
+    return out
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build())
+def lib(openmp=False):
+    if openmp not in _libs:
+        _lib = ctypes.CDLL(build(openmp=openmp))
         P = ctypes.c_void_p
+        _lib.oracle_threads.argtypes = []
+        _lib.oracle_threads.restype = ctypes.c_int
         _lib.oracle_spmv.argtypes = [ctypes.c_int64, P, P, P, P, P]
         _lib.oracle_spmv.restype = None
         _lib.oracle_pipecg.argtypes = [ctypes.c_int64, P, P, P, P, P, P, ctypes.c_double,
@@ -66,7 +72,13 @@ def lib():
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                     P, P, P, P, ctypes.POINTER(Result)]
         _lib.oracle_pcg.restype = ctypes.c_int
-    return _lib
+        _libs[openmp] = _lib
+    return _libs[openmp]
+
+
+def threads(openmp=False):
+    """Host threads the oracle's row loops use (1 for the plain build)."""
+    return lib(openmp).oracle_threads()
 
 
 def _ptr(a):
@@ -80,19 +92,20 @@ def _csr_args(a):
     return rp, ci, v
 
 
-def spmv(a, x):
-    """y = A x (CSR order, sequential)."""
+def spmv(a, x, openmp=False):
+    """y = A x (CSR order; rows over all host cores with openmp)."""
     rp, ci, v = _csr_args(a)
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty(a.n)
-    lib().oracle_spmv(a.n, _ptr(rp), _ptr(ci), _ptr(v), _ptr(x), _ptr(y))
+    lib(openmp).oracle_spmv(a.n, _ptr(rp), _ptr(ci), _ptr(v), _ptr(x), _ptr(y))
     return y
 
 
 def pipecg(a, b, x0=None, tol=1e-8, maxit=10000, norm=NORM_REL_R, rr_period=0, max_restarts=8,
-           jacobi_elim=False, sum_mode=0, history=False, state=False):
+           jacobi_elim=False, sum_mode=0, history=False, state=False, openmp=False):
     """Algorithm 2 (with restart on breakdown, up to max_restarts times).  jacobi_elim: the
-    variant with q = M^-1 s and u = M^-1 r in place of their recurrences.
+    variant with q = M^-1 s and u = M^-1 r in place of their recurrences.  openmp: the
+    OpenMP build of the same source (bitwise-identical results).
     Returns dict(x, result, [alpha, beta, res], [state])."""
     rp, ci, v = _csr_args(a)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -103,7 +116,7 @@ def pipecg(a, b, x0=None, tol=1e-8, maxit=10000, norm=NORM_REL_R, rr_period=0, m
     rh = np.full(maxit + 1, np.nan) if history else None
     st = np.empty(10 * a.n) if state else None
     res = Result()
-    lib().oracle_pipecg(a.n, _ptr(rp), _ptr(ci), _ptr(v), _ptr(b), _ptr(x0), _ptr(x), tol,
+    lib(openmp).oracle_pipecg(a.n, _ptr(rp), _ptr(ci), _ptr(v), _ptr(b), _ptr(x0), _ptr(x), tol,
                         maxit, norm, rr_period, max_restarts, int(bool(jacobi_elim)), sum_mode, _ptr(ah),
                         _ptr(bh), _ptr(rh),
                         _ptr(st), ctypes.byref(res))
@@ -117,7 +130,7 @@ def pipecg(a, b, x0=None, tol=1e-8, maxit=10000, norm=NORM_REL_R, rr_period=0, m
 
 
 def pcg(a, b, x0=None, tol=1e-8, maxit=10000, norm=NORM_REL_R, sum_mode=0, history=False,
-        state=False):
+        state=False, openmp=False):
     """Algorithm 1.  Returns dict(x, result, [alpha, beta, res], [state: x r u p])."""
     rp, ci, v = _csr_args(a)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -128,7 +141,7 @@ def pcg(a, b, x0=None, tol=1e-8, maxit=10000, norm=NORM_REL_R, sum_mode=0, histo
     rh = np.full(maxit + 1, np.nan) if history else None
     st = np.empty(4 * a.n) if state else None
     res = Result()
-    lib().oracle_pcg(a.n, _ptr(rp), _ptr(ci), _ptr(v), _ptr(b), _ptr(x0), _ptr(x), tol, maxit,
+    lib(openmp).oracle_pcg(a.n, _ptr(rp), _ptr(ci), _ptr(v), _ptr(b), _ptr(x0), _ptr(x), tol, maxit,
                      norm, sum_mode, _ptr(ah), _ptr(bh), _ptr(rh), _ptr(st), ctypes.byref(res))
     out = {"x": x, "result": res.as_dict()}
     if history:

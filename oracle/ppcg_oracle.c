@@ -13,6 +13,12 @@
  * -O2 -ffp-contract=off so every product and sum is rounded separately, in the order
  * written here.
  *
+ * Loops whose rows are independent (SpMV rows, Jacobi application, vector updates) carry
+ * OpenMP pragmas.  A plain build ignores them; a build with -fopenmp spreads those rows over
+ * the host cores with each row's arithmetic unchanged, and the dot products stay sequential
+ * in index order, so both builds return bitwise-identical results.  The OpenMP build exists
+ * only to time the same source on all host cores.
+ *
  * Readings where the paper is silent or loose (each is repeated in the design notes):
  *   - alpha_{i-1} in the alpha update of Algorithm 2 is the previous iteration's alpha;
  *     the un-subscripted delta is the value of the latest (w, u) dot product.
@@ -41,6 +47,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define OR_OK 0
 #define OR_ERR_ARG (-1)
 #define OR_ERR_NOT_SPD (-2)
@@ -59,11 +69,21 @@ typedef struct {
   double gamma, delta;
 } oracle_result;
 
+/* Host threads the row loops use: 1 for the plain build. */
+int oracle_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* ---- building blocks ---------------------------------------------------------------- */
 
 /* y = A x, one row at a time, terms added in CSR order. */
 void oracle_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
                  const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; i++) {
     double acc = 0.0;
     for (int64_t k = rp[i]; k < rp[i + 1]; k++) acc += v[k] * x[ci[k]];
@@ -103,12 +123,14 @@ static int jacobi_diag(int64_t n, const int64_t* rp, const int32_t* ci, const do
 
 /* y = M^-1 x with M = diag(A): y_i = x_i / a_ii. */
 static void apply_jacobi(int64_t n, const double* d, const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; i++) y[i] = x[i] / d[i];
 }
 
 static double true_residual(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
                             const double* b, const double* x, double* tmp, int sum_mode) {
   oracle_spmv(n, rp, ci, v, x, tmp);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; i++) tmp[i] = b[i] - tmp[i];
   return sqrt(dot(sum_mode, n, tmp, tmp));
 }
@@ -161,6 +183,7 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
 
   /* setup: r0 = b - A x0; u0 = M^-1 r0; w0 = A u0 */
   oracle_spmv(n, rp, ci, v, x, tmp);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; i++) r[i] = b[i] - tmp[i];
   apply_jacobi(n, d, r, u);
   oracle_spmv(n, rp, ci, v, u, w);
@@ -190,6 +213,7 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
     if (replace) {
       /* r = b - A x, u = M^-1 r, w = A u, s = A p, q = M^-1 s, z = A q, m = M^-1 w, n = A m */
       oracle_spmv(n, rp, ci, v, x, tmp);
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; i++) r[i] = b[i] - tmp[i];
       apply_jacobi(n, d, r, u);
       oracle_spmv(n, rp, ci, v, u, w);
@@ -217,6 +241,7 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
         restarts++;
         for (int64_t i = 0; i < n; i++) { p[i] = 0.0; s[i] = 0.0; q[i] = 0.0; z[i] = 0.0; }
         oracle_spmv(n, rp, ci, v, x, tmp);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; i++) r[i] = b[i] - tmp[i];
         apply_jacobi(n, d, r, u);
         oracle_spmv(n, rp, ci, v, u, w);
@@ -241,6 +266,7 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
     if (alpha_hist) alpha_hist[it] = alpha;
     if (beta_hist) beta_hist[it] = beta;
     /* vector updates: z, q, s, p, then x, r, u, w */
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
       z[i] = nv[i] + beta * z[i];
       s[i] = w[i] + beta * s[i];
@@ -309,6 +335,7 @@ int oracle_pcg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
   }
   /* setup: r0 = b - A x0; u0 = M^-1 r0 */
   oracle_spmv(n, rp, ci, v, x, tmp);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; i++) r[i] = b[i] - tmp[i];
   apply_jacobi(n, d, r, u);
   /* setup: gamma0 = (u0, r0); norm0 */
@@ -324,6 +351,7 @@ int oracle_pcg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
     /* beta */
     beta = it > 0 ? gamma / gamma_prev : 0.0;
     /* search direction: p_i = u_i + beta p_{i-1} */
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) p[i] = u[i] + beta * p[i];
     /* s = A p; delta = (s, p); alpha = gamma / delta */
     oracle_spmv(n, rp, ci, v, p, s);
@@ -334,6 +362,7 @@ int oracle_pcg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
     if (alpha_hist) alpha_hist[it] = alpha;
     if (beta_hist) beta_hist[it] = beta;
     /* x, r and u = M^-1 r */
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
       x[i] = x[i] + alpha * p[i];
       r[i] = r[i] - alpha * s[i];

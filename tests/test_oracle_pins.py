@@ -371,3 +371,25 @@ def test_jacobi_elimination_variant():
     f2 = oracle.pipecg(a, b, tol=1e-8, maxit=5000, jacobi_elim=True)
     assert f2["result"]["status"] == oracle.OK
     assert abs(f1["result"]["iters"] - f2["result"]["iters"]) <= 2
+
+
+def test_openmp_build_is_bitwise_identical():
+    """The OpenMP build of the oracle (timed as the all-core CPU baseline) spreads only rows
+    over threads and keeps the dot products sequential, so it must return the plain build's
+    iterates bit for bit: Algorithm 2 with residual replacement, the Jacobi-eliminated
+    variant, and Algorithm 1."""
+    a = synth.varcoeff3d(20, 5)
+    b = synth.rhs_uniform(a.n, 5)
+    for kw in ({"rr_period": 7}, {"jacobi_elim": True}, {"norm": oracle.NORM_PAPER_U_ABS, "tol": 1e-9}):
+        kw = {"tol": 1e-10, "maxit": 400, **kw}
+        plain = oracle.pipecg(a, b, history=True, state=True, **kw)
+        omp = oracle.pipecg(a, b, history=True, state=True, openmp=True, **kw)
+        assert plain["result"] == omp["result"]
+        assert np.array_equal(plain["alpha"], omp["alpha"]) and np.array_equal(plain["beta"], omp["beta"])
+        for k in oracle.STATE_NAMES:
+            assert np.array_equal(plain["state"][k], omp["state"][k]), k
+    p1 = oracle.pcg(a, b, tol=1e-10, history=True)
+    p2 = oracle.pcg(a, b, tol=1e-10, history=True, openmp=True)
+    assert p1["result"] == p2["result"] and np.array_equal(p1["x"], p2["x"])
+    assert np.array_equal(oracle.spmv(a, b), oracle.spmv(a, b, openmp=True))
+    assert oracle.threads() == 1 and oracle.threads(openmp=True) >= 1
