@@ -488,9 +488,12 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   if (path != PPCG_PATH_GRID) box = false;
   if (!box) h->box_g = 0;
   if (path == PPCG_PATH_GRID) {
-    h->shape = 0;
-    if (const char* e = getenv("PPCG_GRID_SHAPE")) h->shape = atoi(e);   // launch-shape tuning knob
-    if (h->shape < 0 || h->shape >= grid_shape_count()) h->shape = 0;
+    // launch-shape tuning knob: an index among the plan's own kernels (SELL or box)
+    const int nshapes = box ? grid_box_shape_count() : grid_shape_count();
+    int k = 0;
+    if (const char* e = getenv("PPCG_GRID_SHAPE")) k = atoi(e);
+    if (k < 0 || k >= nshapes) k = 0;
+    h->shape = box ? grid_box_shape_first() + k : k;
     // One CTA per SM at most for small systems: enough warps for one 32-row chunk each,
     // so the grid barrier spans only the CTAs that have rows to work on.
     const int full = grid_blocks_for_device(h->device, h->shape);

@@ -124,7 +124,9 @@ cudaError_t launch_onchip(const SysDesc* d_descs, const int32_t* d_list, const i
 size_t onchip_smem_bytes(int64_t nchunks, int64_t slots, int nc);   // dynamic shared memory per CTA
 size_t onchip_smem_limit(int device);                               // largest the device allows
 bool onchip_cluster_fits(int nc, size_t smem);                      // can one such cluster run
-int grid_shape_count();
+int grid_shape_count();        // SELL/CSR plans: shapes [0, grid_shape_count())
+int grid_box_shape_first();    // matrix-free box plans: shapes first + [0, count)
+int grid_box_shape_count();
 int grid_threads(int shape);
 int grid_blocks_for_device(int device, int shape);
 int max_active_clusters(int device);

@@ -1523,11 +1523,39 @@ __device__ __forceinline__ void box_coords(int32_t row, int32_t g, int32_t& z, i
   y = zy - z * g;
 }
 
+// Window sum along one axis: the sum of f(row + d * stride) over the offsets d in [-R, R]
+// that stay on the grid (0 <= c + d < g, c the row's coordinate on that axis), added in
+// ascending d with the first term taken as is -- no 0.0 start, so a window of w terms costs
+// w - 1 FP64 adds, the pipe that bounds these passes.  The interior of the R = 2 family
+// (Table II) is unrolled; every form adds the same terms in the same order.
+template <class F>
+__device__ __forceinline__ double axis_sum(const F& f, int32_t row, int32_t c, int32_t g, int32_t R,
+                                           int64_t stride) {
+  if (R == 2 && c >= 2 && c + 2 < g) {
+    const double a0 = f(row - 2 * stride), a1 = f(row - stride), a2 = f(row), a3 = f(row + stride),
+                 a4 = f(row + 2 * stride);
+    return (((a0 + a1) + a2) + a3) + a4;
+  }
+  const int32_t lo = max(-R, -c), hi = min(R, g - 1 - c);
+  double s = f(row + lo * stride);
+  for (int32_t d = lo + 1; d <= hi; d++) s += f(row + d * stride);
+  return s;
+}
+
+struct LoadCg {
+  const double* p;
+  __device__ __forceinline__ double operator()(int64_t j) const { return __ldcg(p + j); }
+};
+struct LoadSlot {
+  GatherSlot<double, kNS64> g;
+  __device__ __forceinline__ double operator()(int64_t j) const { return g((int32_t)j); }
+};
+
 // Stage X for one or two FP64-block slots (slot_b < 0: one).
 __device__ void box_stage_x(const SysDesc& S, const Lanes& L, int slot_a, int slot_b) {
   const int32_t n = (int32_t)S.A.n, g = S.box_g, R = S.box_r;
-  const GatherSlot<double, kNS64> va{S.v64 + slot_a * kChunk};
-  const GatherSlot<double, kNS64> vb{S.v64 + (slot_b < 0 ? slot_a : slot_b) * kChunk};
+  const LoadSlot va{{S.v64 + slot_a * kChunk}};
+  const LoadSlot vb{{S.v64 + (slot_b < 0 ? slot_a : slot_b) * kChunk}};
   double* t1a = S.box_t;
   double* t1b = S.box_t + n;
   FOR_CHUNKS(S.A, L) {
@@ -1535,22 +1563,16 @@ __device__ void box_stage_x(const SysDesc& S, const Lanes& L, int slot_a, int sl
     if (row >= n) continue;
     int32_t z, y, x;
     box_coords(row, g, z, y, x);
-    double sa = 0.0, sb = 0.0;
-    for (int32_t d = -R; d <= R; d++) {
-      if (x + d < 0 || x + d >= g) continue;
-      sa += va(row + d);
-      if (slot_b >= 0) sb += vb(row + d);
-    }
-    __stcg(t1a + row, sa);
-    if (slot_b >= 0) __stcg(t1b + row, sb);
+    __stcg(t1a + row, axis_sum(va, row, x, g, R, 1));
+    if (slot_b >= 0) __stcg(t1b + row, axis_sum(vb, row, x, g, R, 1));
   }
 }
 
 // Stage Y: t2 = y-sums of t1 (one or two arrays).
 __device__ void box_stage_y(const SysDesc& S, const Lanes& L, bool two) {
   const int32_t n = (int32_t)S.A.n, g = S.box_g, R = S.box_r;
-  const double* t1a = S.box_t;
-  const double* t1b = S.box_t + n;
+  const LoadCg t1a{S.box_t};
+  const LoadCg t1b{S.box_t + n};
   double* t2a = S.box_t + 2 * (int64_t)n;
   double* t2b = S.box_t + 3 * (int64_t)n;
   FOR_CHUNKS(S.A, L) {
@@ -1558,28 +1580,16 @@ __device__ void box_stage_y(const SysDesc& S, const Lanes& L, bool two) {
     if (row >= n) continue;
     int32_t z, y, x;
     box_coords(row, g, z, y, x);
-    double sa = 0.0, sb = 0.0;
-    for (int32_t d = -R; d <= R; d++) {
-      if (y + d < 0 || y + d >= g) continue;
-      sa += __ldcg(t1a + row + d * g);
-      if (two) sb += __ldcg(t1b + row + d * g);
-    }
-    __stcg(t2a + row, sa);
-    if (two) __stcg(t2b + row, sb);
+    __stcg(t2a + row, axis_sum(t1a, row, y, g, R, g));
+    if (two) __stcg(t2b + row, axis_sum(t1b, row, y, g, R, g));
   }
 }
 
 // z-sums of t2 (array k = 0 or 1) for one row: the box sum B_row.
 __device__ __forceinline__ double box_z(const SysDesc& S, int32_t row, int32_t z, int k) {
   const int32_t n = (int32_t)S.A.n, g = S.box_g, R = S.box_r;
-  const double* t2 = S.box_t + (2 + k) * (int64_t)n;
-  const int64_t plane = (int64_t)g * g;
-  double s = 0.0;
-  for (int32_t d = -R; d <= R; d++) {
-    if (z + d < 0 || z + d >= g) continue;
-    s += __ldcg(t2 + row + d * plane);
-  }
-  return s;
+  const LoadCg t2{S.box_t + (2 + k) * (int64_t)n};
+  return axis_sum(t2, row, z, g, R, (int64_t)g * g);
 }
 
 // Sources of the box stages for an FP64 pass (slot_a < 0: the pass needs no product).
@@ -1743,7 +1753,10 @@ __device__ __forceinline__ void cluster_reduce(const double* part, double* out) 
 }
 constexpr int kSmGrid = 3 * 32, kSmCluster = 3 * 32 * (kClusterThreads / 32);
 
-template <bool STAGED, class G, class Shared>
+// BOX: the kernel carries the matrix-free box passes (a plan with box_g > 0 runs only on
+// such a kernel, every other plan only on the others, so the SELL kernels' register
+// allocation does not carry the box code); a mismatch ends the solve with PPCG_ERR_ARG.
+template <bool STAGED, bool BOX = false, class G, class Shared>
 __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsigned char* stage_mem,
                            uint64_t* stage_bars, unsigned& phases) {
   __syncthreads();   // previous system's readers of sh are done
@@ -1755,6 +1768,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
     for (int i = 0; i < (int)(sizeof(Ctl) / 8); i++) dst[i] = __ldcg(src + i);
     if (sh.C.t_start == 0) sh.C.t_start = globaltimer();
     sh.C.exit_now = 0;
+    if ((sh.S.box_g > 0) != BOX) { sh.C.status = PPCG_ERR_ARG; sh.C.state = S_DONE; }
   }
   __syncthreads();
   const SysDesc& S = sh.S;
@@ -1795,7 +1809,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
         default: partials = false; break;
       }
       if (partials) write_block_partials<kPacked>(d.get(0), d.get(1), d.get(2), slot, sh.sm);
-    } else if (!fp32 && S.box_g > 0 && (pass == P_SETUP1 || pass == P_SETUP2 || pass == P_ITER ||
+    } else if (BOX && !fp32 && (pass == P_SETUP1 || pass == P_SETUP2 || pass == P_ITER ||
                                           pass == P_TRUE || pass == P_RR1 || pass == P_RR2)) {
       int sa, sb;
       box_sources(C, S, sa, sb);
@@ -1896,7 +1910,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
   }
 }
 
-template <int THREADS, int MINB, bool STAGED>
+template <int THREADS, int MINB, bool STAGED, bool BOX = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_grid(const SysDesc* d, int budget) {
   __shared__ SharedT<kSmGrid> sh;
   __shared__ uint64_t bars[2 * (THREADS / 32)];
@@ -1911,12 +1925,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_grid(const SysDesc* d, int bu
     __syncthreads();
   }
   GridGroup g{d->bar, d->err, (long long)d->spin_limit_ns, 0u};
-  run_system<STAGED>(g, d, budget, sh, stage_mem, bars, phases);
+  run_system<STAGED, BOX>(g, d, budget, sh, stage_mem, bars, phases);
 }
 
 // Launch shapes of the grid path: (threads per CTA, minimum CTAs per SM for the register
 // budget, bulk-copy staging).  Index 0 is the default (fastest measured on the 256^3
-// stencil); the others trade registers, resident warps and staging.
+// stencil); the others trade registers, resident warps and staging.  From kFirstBoxShape on:
+// the kernels of matrix-free box-stencil plans.
 struct GridShape {
   void (*fn)(const SysDesc*, int);
   int threads;
@@ -1927,8 +1942,11 @@ const GridShape kGridShapes[] = {
     {k_grid<512, 1, false>, 512, 0}, {k_grid<384, 2, false>, 384, 0}, {k_grid<128, 6, false>, 128, 0},
     {k_grid<512, 1, true>, 512, 16 * kWarpStageBytes}, {k_grid<256, 2, true>, 256, 8 * kWarpStageBytes},
     {k_grid<384, 1, true>, 384, 12 * kWarpStageBytes},
+    {k_grid<512, 2, false, true>, 512, 0}, {k_grid<256, 4, false, true>, 256, 0},
+    {k_grid<1024, 1, false, true>, 1024, 0},
 };
 constexpr int kNumGridShapes = (int)(sizeof(kGridShapes) / sizeof(kGridShapes[0]));
+constexpr int kFirstBoxShape = 9;
 
 // Cluster path.  Static schedule (next == nullptr): cluster c runs list[list_ptr[c] ..
 // list_ptr[c + 1]).  Dynamic schedule: every cluster takes the next entry of list (ordered
@@ -2305,7 +2323,9 @@ __global__ void k_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, in
 
 }  // namespace
 
-int grid_shape_count() { return kNumGridShapes; }
+int grid_shape_count() { return kFirstBoxShape; }
+int grid_box_shape_first() { return kFirstBoxShape; }
+int grid_box_shape_count() { return kNumGridShapes - kFirstBoxShape; }
 int grid_threads(int shape) { return kGridShapes[shape].threads; }
 
 cudaError_t ensure_smem_attr(const void* fn, size_t bytes);

@@ -361,6 +361,18 @@ def test_box_fixed_k_parity(name, k):
     assert info.iters == k and rel(x, ref["x"]) <= 1e-10
 
 
+@pytest.mark.parametrize("shape", [1, 2])
+def test_box_launch_shapes(shape, monkeypatch):
+    """The other launch shapes of the box kernel (256 and 1024 threads per CTA; the tuning
+    knob indexes the box plan's own kernels) meet the same fixed-k bar."""
+    monkeypatch.setenv("PPCG_GRID_SHAPE", str(shape))
+    a, b = box_problem("box125_24")
+    ref = oracle.pipecg(a, b, tol=0.0, maxit=12)
+    x, info = gpu(a, b, tol=0.0, maxit=12, **BOX)
+    assert info.status == pp().ERR_NOT_CONVERGED
+    assert info.iters == 12 and rel(x, ref["x"]) <= 1e-10
+
+
 @pytest.mark.parametrize("name", ["box125_24", "box27_33", "box343_12"])
 def test_box_full_solve_parity(name):
     a, b = box_problem(name)
