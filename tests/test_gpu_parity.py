@@ -463,3 +463,40 @@ def test_scaled_variant_modes():
     assert i2.status == pp().OK and abs(i2.iters - r2["result"]["iters"]) <= 2
     with pytest.raises(pp().PPCGError):
         pp().Solver.from_csr(a, precision=pp().FP32_IR, **SCALED)
+
+
+# ------------------------------------------------------- every grid-path kernel shape --
+
+# PPCG_GRID_SHAPE picks the launch shape of a SELL plan's grid kernel (threads per CTA,
+# register budget, bulk-copy staging of the vector tiles for shapes 6-8); every shape must
+# meet the bars of every form.
+@pytest.mark.parametrize("shape", range(9))
+def test_fp64_launch_shapes(shape, monkeypatch):
+    monkeypatch.setenv("PPCG_GRID_SHAPE", str(shape))
+    a, b = problem("varcoeff3d_31")
+    ref = oracle.pipecg(a, b, tol=0.0, maxit=20)
+    x, info = gpu(a, b, tol=0.0, maxit=20, path=1)
+    assert info.status == pp().ERR_NOT_CONVERGED and info.iters == 20
+    assert rel(x, ref["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("shape", [0, 1, 6])
+def test_scaled_launch_shapes(shape, monkeypatch):
+    monkeypatch.setenv("PPCG_GRID_SHAPE", str(shape))
+    a, b = problem("varcoeff3d_31")
+    x, info = gpu(a, b, tol=0.0, maxit=20, path=1, variant=1)
+    assert info.iters == 20
+    assert rel(x, oracle.pipecg(a, b, tol=0.0, maxit=20, jacobi_elim=True)["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("shape", [0, 1, 6])
+@pytest.mark.parametrize("precision", [1, 2], ids=["fp32_ir", "fp32_ru"])
+def test_mixed_launch_shapes(shape, precision, monkeypatch):
+    monkeypatch.setenv("PPCG_GRID_SHAPE", str(shape))
+    a, b = problem("varcoeff3d_31")
+    x, info = gpu(a, b, tol=1e-8, maxit=20000, path=1, precision=precision)
+    assert info.status == pp().OK
+    t = np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)
+    assert t <= 1e-8
+    x64 = oracle.pipecg(a, b, tol=1e-10, maxit=20000)["x"]
+    assert rel(x, x64) <= 1e-4
