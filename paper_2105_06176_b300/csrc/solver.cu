@@ -1512,9 +1512,11 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
 // Stage X writes t1 = the x-sums of v, stage Y writes t2 = the y-sums of t1, and the
 // consuming pass adds the z-sums of t2.  Rows are in grid order (x fastest), so each stage
 // reads its 2R+1 neighbours at fixed row offsets (1, g, g^2): for a warp, contiguous 32-row
-// runs.  Per product and row: 6R FP64 adds and 4 intermediate streams instead of (2R+1)^3-1
-// FMAs and the matrix stream.  Then (A v)_i = cd v_i + co (B_i - v_i) and
-// (A D^-1 v)_i = v_i + (co / cd) (B_i - v_i).
+// runs.  Stage Y and the iteration pass march along their axis with a running window sum
+// (box_march), so per product and row the sums cost 2R + 4 FP64 adds (interior rows, plus
+// a direct window at each segment start) and 4 intermediate streams instead of
+// (2R+1)^3 - 1 FMAs and the matrix stream.  The FP64 pipe, not HBM, bounds these passes.
+// Then (A v)_i = cd v_i + co (B_i - v_i) and (A D^-1 v)_i = v_i + (co / cd) (B_i - v_i).
 
 __device__ __forceinline__ void box_coords(int32_t row, int32_t g, int32_t& z, int32_t& y, int32_t& x) {
   const int32_t zy = row / g;
@@ -1568,20 +1570,61 @@ __device__ void box_stage_x(const SysDesc& S, const Lanes& L, int slot_a, int sl
   }
 }
 
-// Stage Y: t2 = y-sums of t1 (one or two arrays).
+// Marching split of a stage along y or z: work items (in-plane position, segment), the
+// segment a run of `len` consecutive positions along the axis.  The first position of a
+// segment takes its window directly (axis_sum); each next one updates the running window
+// sum by the entering and the leaving term -- 2 FP64 adds per row instead of 2R.  Segments
+// are at least 8 long (fewer items than threads on small grids) and otherwise as many as
+// the group's threads can take at once.  Item t: segment t / g^2, in-plane index t % g^2
+// with x fastest, so the lanes of a warp hold consecutive rows.
+struct BoxMarch {
+  int32_t nseg, len;
+};
+__device__ __forceinline__ BoxMarch box_march(int32_t g, int32_t threads) {
+  const int32_t plane = g * g;
+  int32_t nseg = min((g + 7) / 8, threads / plane);
+  if (nseg < 1) nseg = 1;
+  const int32_t len = (g + nseg - 1) / nseg;
+  return {(g + len - 1) / len, len};
+}
+
+// The running window sum along an axis (stride `st` rows) moved from position p - 1 to p:
+// add the entering term (p + R on the grid), subtract the leaving one (p - R - 1).
+__device__ __forceinline__ double window_step(const double* t, int64_t row, int32_t p, int32_t g, int32_t R,
+                                              int64_t st, double s) {
+  if (p + R < g) s += __ldcg(t + row + R * st);
+  if (p - R - 1 >= 0) s -= __ldcg(t + row - (R + 1) * st);
+  return s;
+}
+
+// Stage Y: t2 = y-sums of t1 (one or two arrays), marching along y.
 __device__ void box_stage_y(const SysDesc& S, const Lanes& L, bool two) {
   const int32_t n = (int32_t)S.A.n, g = S.box_g, R = S.box_r;
-  const LoadCg t1a{S.box_t};
-  const LoadCg t1b{S.box_t + n};
+  const double* t1a = S.box_t;
+  const double* t1b = S.box_t + n;
   double* t2a = S.box_t + 2 * (int64_t)n;
   double* t2b = S.box_t + 3 * (int64_t)n;
-  FOR_CHUNKS(S.A, L) {
-    const int32_t row = c * kChunk + L.lane;
-    if (row >= n) continue;
-    int32_t z, y, x;
-    box_coords(row, g, z, y, x);
-    __stcg(t2a + row, axis_sum(t1a, row, y, g, R, g));
-    if (two) __stcg(t2b + row, axis_sum(t1b, row, y, g, R, g));
+  const int32_t plane = g * g;
+  const BoxMarch m = box_march(g, L.W * 32);
+  const int32_t items = m.nseg * plane;
+  for (int64_t t = (int64_t)L.gw * 32 + L.lane; t < items; t += (int64_t)L.W * 32) {
+    const int32_t seg = (int32_t)(t / plane), rem = (int32_t)(t - (int64_t)seg * plane);
+    const int32_t z = rem / g, x = rem - z * g;
+    const int32_t y0 = seg * m.len, y1 = min(g, y0 + m.len);
+    int64_t row = (int64_t)z * plane + (int64_t)y0 * g + x;
+    double sa = axis_sum(LoadCg{t1a}, row, y0, g, R, g);
+    double sb = two ? axis_sum(LoadCg{t1b}, row, y0, g, R, g) : 0.0;
+    __stcg(t2a + row, sa);
+    if (two) __stcg(t2b + row, sb);
+    for (int32_t y = y0 + 1; y < y1; y++) {
+      row += g;
+      sa = window_step(t1a, row, y, g, R, g, sa);
+      __stcg(t2a + row, sa);
+      if (two) {
+        sb = window_step(t1b, row, y, g, R, g, sb);
+        __stcg(t2b + row, sb);
+      }
+    }
   }
 }
 
@@ -1678,36 +1721,47 @@ __device__ bool box_pass(const SysDesc& S, const Ctl& C, const Lanes& L, Dots<do
       const double alpha = C.alpha, beta = C.beta;
       const int wcs = (C.iter & 1) ? V_WB : V_WA;
       const int wns = (C.iter & 1) ? V_WA : V_WB;
-      FOR_CHUNKS(S.A, L) {
-        const int32_t row = c * kChunk + L.lane;
-        if (row >= n) continue;
-        int32_t z, y, x;
-        box_coords(row, g, z, y, x);
-        double* pc = v.chunk(c, L.lane);
-        const double wi = ldcg(pc + wcs * kChunk);
-        // n_i = (A M^-1 w)_i = w_i + (co / cd) (B(w)_i - w_i)
-        const double ni = fma(ch, box_z(S, row, z, 0) - wi, wi);
-        const double id = ldcs(pc + V_INVD * kChunk), ui = ldcs(pc + V_U * kChunk);
-        const double mi = id * wi;
-        const double zi = first ? ni : fma(beta, ldcs(pc + V_Z * kChunk), ni);
-        const double qi = first ? mi : fma(beta, ldcs(pc + V_Q * kChunk), mi);
-        const double si = first ? wi : fma(beta, ldcs(pc + V_S * kChunk), wi);
-        const double pi = first ? ui : fma(beta, ldcs(pc + V_P * kChunk), ui);
-        const double xi = fma(alpha, pi, ldcs(pc + V_X * kChunk));
-        const double ri = fma(-alpha, si, ldcs(pc + V_R * kChunk));
-        const double un = fma(-alpha, qi, ui);
-        const double wnn = fma(-alpha, zi, wi);
-        stcs(pc + V_Z * kChunk, zi);
-        stcs(pc + V_Q * kChunk, qi);
-        stcs(pc + V_S * kChunk, si);
-        stcs(pc + V_P * kChunk, pi);
-        stcs(pc + V_X * kChunk, xi);
-        stcs(pc + V_R * kChunk, ri);
-        stcs(pc + V_U * kChunk, un);
-        stcs(pc + wns * kChunk, wnn);
-        d.add(0, ri, un);
-        d.add(1, wnn, un);
-        if (with_rr) { if (paper) d.add(2, un, un); else d.add(2, ri, ri); }
+      // Rows in marching order along z (see box_march): the z-window of t2 is carried from
+      // one row to the next of the segment.
+      const int32_t R = S.box_r, plane = g * g;
+      const double* t2 = S.box_t + 2 * (int64_t)n;
+      const BoxMarch m = box_march(g, L.W * 32);
+      const int32_t items = m.nseg * plane;
+      for (int64_t t = (int64_t)L.gw * 32 + L.lane; t < items; t += (int64_t)L.W * 32) {
+        const int32_t seg = (int32_t)(t / plane), rem = (int32_t)(t - (int64_t)seg * plane);
+        const int32_t z0 = seg * m.len, z1 = min(g, z0 + m.len);
+        int32_t row = z0 * plane + rem;
+        double bs = axis_sum(LoadCg{t2}, row, z0, g, R, plane);
+        for (int32_t z = z0;;) {
+          double* pc = v.chunk(row / kChunk, row % kChunk);
+          const double wi = ldcg(pc + wcs * kChunk);
+          // n_i = (A M^-1 w)_i = w_i + (co / cd) (B(w)_i - w_i)
+          const double ni = fma(ch, bs - wi, wi);
+          const double id = ldcs(pc + V_INVD * kChunk), ui = ldcs(pc + V_U * kChunk);
+          const double mi = id * wi;
+          const double zi = first ? ni : fma(beta, ldcs(pc + V_Z * kChunk), ni);
+          const double qi = first ? mi : fma(beta, ldcs(pc + V_Q * kChunk), mi);
+          const double si = first ? wi : fma(beta, ldcs(pc + V_S * kChunk), wi);
+          const double pi = first ? ui : fma(beta, ldcs(pc + V_P * kChunk), ui);
+          const double xi = fma(alpha, pi, ldcs(pc + V_X * kChunk));
+          const double ri = fma(-alpha, si, ldcs(pc + V_R * kChunk));
+          const double un = fma(-alpha, qi, ui);
+          const double wnn = fma(-alpha, zi, wi);
+          stcs(pc + V_Z * kChunk, zi);
+          stcs(pc + V_Q * kChunk, qi);
+          stcs(pc + V_S * kChunk, si);
+          stcs(pc + V_P * kChunk, pi);
+          stcs(pc + V_X * kChunk, xi);
+          stcs(pc + V_R * kChunk, ri);
+          stcs(pc + V_U * kChunk, un);
+          stcs(pc + wns * kChunk, wnn);
+          d.add(0, ri, un);
+          d.add(1, wnn, un);
+          if (with_rr) { if (paper) d.add(2, un, un); else d.add(2, ri, ri); }
+          if (++z >= z1) break;
+          row += plane;
+          bs = window_step(t2, row, z, g, R, plane, bs);
+        }
       }
       return true;
     }
