@@ -465,6 +465,17 @@ def measure_box125(pp, torch, sizes=(165, 170, 181, 185), seed=9):
                  "rel_res_true": info.rel_res_true, "create_s": t_create, "bytes_per_iter": balg,
                  "achieved_gbs": balg * info.iters / t / 1e9}
             r["frac_of_measured_hbm"] = r["achieved_gbs"] / peaks["hbm_gbs"]
+            if fmt == pp.FMT_BOX:
+                # The matrix-free passes are bound by the FP64 pipe: per interior row and
+                # iteration 2R adds for the x-sums, 2 + 2 for the marching y- and z-sums and
+                # 13 for the update and the two dots (the optional norm dot not counted).
+                # Peak: the nominal 1.25 TFLOP/s FP64 rate counts an FMA as two flops, so the
+                # pipe retires 0.625 T FP64 operations per second (an add or a multiply
+                # takes an FMA's slot).
+                ops = (2 * 2 + 4 + 13) * a.n
+                r["fp64_ops_per_iter"] = ops
+                r["fp64_tops"] = ops * info.iters / t / 1e12
+                r["frac_of_fp64_pipe_nominal"] = r["fp64_tops"] / 0.625
             if name == "fp64":
                 x64 = x.clone()
             else:
@@ -528,6 +539,8 @@ def main():
                          "paper: the paper's stopping rule and exact solution on every config; "
                          "box125: Table II's 125-point family; latency: the 64^2 solve latency")
     ap.add_argument("--batch-count", type=int, default=1024)
+    ap.add_argument("--box-sizes", type=int, nargs="+", default=[165, 170, 181, 185],
+                    help="grid sides of the box125 mode (default: Table II's four)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -540,7 +553,7 @@ def main():
         if args.mode == "rgg":
             res = {"mode": "rgg", "rgg": measure_rgg(pp, torch)}
         elif args.mode == "box125":
-            res = {"mode": "box125", "box125": measure_box125(pp, torch)}
+            res = {"mode": "box125", "box125": measure_box125(pp, torch, sizes=tuple(args.box_sizes))}
         elif args.mode == "paper":
             res = {"mode": "paper", "paper": measure_paper(pp, torch, args.batch_count)}
         elif args.mode == "latency":
