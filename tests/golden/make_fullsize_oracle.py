@@ -15,7 +15,8 @@ Records:
     kernel and not the rounding order.
   * RGG Laplacian, 4,000,000 points (seed 3, expected degree 14, shift 1e-3), b seed 3, rel
     tol 1e-8 and 1e-10: iterations; and the fixed k chosen the same way.
-  * The 1024-system ragged batch (batch_mix(1024, 11)), rel tol 1e-8: iterations per system.
+  * The 1024-system ragged batch (batch_mix(1024, 11)), rel tol 1e-8: iterations and
+    residual replacements per system.
 
 Run from the repository root:  python tests/golden/make_fullsize_oracle.py   (about ten
 minutes on eight cores).
@@ -40,7 +41,7 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fullsize_oracle.
 def _batch_one(spec):
     a, b = synth.build_spec(tuple(spec))
     r = oracle.pipecg(a, b, tol=1e-8, maxit=20000)["result"]
-    return {"n": a.n, "iters": r["iters"], "status": r["status"],
+    return {"n": a.n, "iters": r["iters"], "status": r["status"], "rr_count": r["rr_count"],
             "rel_res_true": r["res_true"] / r["bnorm"]}
 
 
