@@ -78,6 +78,7 @@ struct Ctl {
   int32_t stalls, ru_due;       // FP32_RU: reliable updates in a row without progress; this one was due
   double rmax;                  // FP32_RU: largest recursive norm since the last reliable update
   double gamma, gamma_prev, delta, alpha, alpha_prev, beta, norm;
+  double inv_gamma, inv_alpha;  // 1 / gamma and 1 / alpha of the last scalars step
   double bnorm, rn, rn_prev, res_true, inner_norm0, inner_target, rr_norm_prev;
   unsigned long long t_start, t_end;
   double red[4];                           // reduced partials of the last pass

@@ -1187,17 +1187,38 @@ __device__ __forceinline__ bool may_pass(const Ctl& c, const SysDesc& S, double 
   return c.gamma * S.dmin <= slack * t * t;
 }
 
+// alpha = gamma / den, with 1 / alpha and 1 / gamma for the next step, from one FP64
+// division: r = 1 / (gamma den) gives 1 / den = gamma r and 1 / gamma = den r.  A division is
+// a long dependent chain for the single thread that runs the control step, and the step is
+// on every iteration's critical path, so the next step's beta = gamma / gamma_prev and
+// beta gamma / alpha_prev become products with these inverses.  Where gamma den is near the
+// ends of the FP64 range the three quotients are taken directly.
+__device__ __forceinline__ void alpha_and_inverses(double gamma, double den, double& alpha, double& inv_alpha,
+                                                   double& inv_gamma) {
+  const double p = gamma * den;
+  if (p > 1e-290 && p < 1e290) {
+    const double r = 1.0 / p;
+    alpha = gamma * (gamma * r);
+    inv_gamma = den * r;
+    inv_alpha = den * inv_gamma;
+  } else {
+    alpha = gamma / den;
+    inv_alpha = den / gamma;
+    inv_gamma = 1.0 / gamma;
+  }
+}
+
 // The scalars of Alg. 2 (beta, then alpha).  Returns false on breakdown.
 __device__ __forceinline__ bool scalars(Ctl& c, int it) {
   if (it > 0) {
-    c.beta = c.gamma / c.gamma_prev;
-    double den = c.delta - c.beta * c.gamma / c.alpha_prev;
+    c.beta = c.gamma * c.inv_gamma;                    // gamma / gamma_prev
+    double den = c.delta - (c.beta * c.gamma) * c.inv_alpha;   // delta - beta gamma / alpha_prev
     if (!(c.gamma > 0.0) || !(den > 0.0)) return false;
-    c.alpha = c.gamma / den;
+    alpha_and_inverses(c.gamma, den, c.alpha, c.inv_alpha, c.inv_gamma);
   } else {
     c.beta = 0.0;
     if (!(c.gamma > 0.0) || !(c.delta > 0.0)) return false;
-    c.alpha = c.gamma / c.delta;
+    alpha_and_inverses(c.gamma, c.delta, c.alpha, c.inv_alpha, c.inv_gamma);
   }
   return true;
 }
@@ -1221,10 +1242,13 @@ __device__ __forceinline__ bool control_fast_ru(Ctl& c, const SysDesc& S, int it
     const bool periodic = S.rr_period > 0 && iter - c.last_rr_iter >= S.rr_period;
     if (periodic || norm <= S.inner_tol * rmax || norm <= S.tol * c.bnorm || iter >= S.maxit) return false;
   }
-  const double beta = gamma / gamma_prev;
-  const double den = delta - beta * gamma / alpha_prev;
+  const double beta = gamma * c.inv_gamma;
+  const double den = delta - (beta * gamma) * c.inv_alpha;
   if (!(gamma > 0.0) || !(den > 0.0)) return false;
-  const double alpha = gamma / den;
+  double alpha, inv_alpha, inv_gamma;
+  alpha_and_inverses(gamma, den, alpha, inv_alpha, inv_gamma);
+  c.inv_alpha = inv_alpha;
+  c.inv_gamma = inv_gamma;
   c.gamma_prev = gamma_prev;
   c.alpha_prev = alpha_prev;
   c.iter = iter;
@@ -1263,11 +1287,14 @@ __device__ __forceinline__ bool control_fast(Ctl& c, const SysDesc& S, int iter_
   if (paper ? (norm <= tol) : (norm <= tol * bnorm)) return false;
   if (iter >= S.maxit) return false;
   if (!isfinite(gamma) || !isfinite(delta)) return false;
-  const double beta = gamma / gamma_prev;
-  const double den = delta - beta * gamma / alpha_prev;
+  const double beta = gamma * c.inv_gamma;
+  const double den = delta - (beta * gamma) * c.inv_alpha;
   if (!(gamma > 0.0) || !(den > 0.0)) return false;
-  const double alpha = gamma / den;
+  double alpha, inv_alpha, inv_gamma;
+  alpha_and_inverses(gamma, den, alpha, inv_alpha, inv_gamma);
   const int want = may(64.0) ? 1 : 0;
+  c.inv_alpha = inv_alpha;
+  c.inv_gamma = inv_gamma;
   c.gamma_prev = gamma_prev;
   c.alpha_prev = alpha_prev;
   c.iter = iter;
