@@ -186,13 +186,28 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
  *   b [n]  host or device, read only.  b = 0 gives x = 0, 0 iterations, PPCG_OK (REL_R).
  *   x0 [n] host or device initial guess, or NULL for zero.  May alias x.
  *   x [n]  host or device output.  Written on every outcome except argument errors.
- *   info   host pointer or NULL; valid after the stream is synchronised.
+ *   info   host pointer or NULL; valid after the stream is synchronised.  A non-NULL info is
+ *          filled by a host function enqueued on the stream, which holds the stream for tens
+ *          to hundreds of microseconds; with NULL the solve's record is only copied into the
+ *          handle's pinned staging buffer, and ppcg_last_info reads it after the sync.
  * Returns PPCG_OK when the work was enqueued (numerical status goes to info->status), or
  * PPCG_ERR_ARG / PPCG_ERR_OOM / PPCG_ERR_CUDA immediately.
  * With host b/x the call copies through device staging buffers on the stream.
  */
 ppcg_status ppcg_solve(ppcg_handle handle, const double* b, const double* x0, double* x,
                        double tol, int32_t maxit, cudaStream_t stream, ppcg_info* info);
+
+/*
+ * The result record of the handle's most recent solve (ppcg_solve or ppcg_batch_solve), read
+ * from the pinned staging buffer that solve's stream-ordered copies wrote: call it after that
+ * stream has been synchronised (it makes no CUDA call and does not wait).  For solves
+ * enqueued with info == NULL this is how the caller gets the status, iteration count and
+ * residuals without the stream-held host function.
+ *   info   host pointer, written with the same fields ppcg_solve's info would hold.
+ * Returns PPCG_OK, or PPCG_ERR_ARG for a NULL handle or info or a handle that has not
+ * solved yet.
+ */
+ppcg_status ppcg_last_info(ppcg_handle handle, ppcg_info* info);
 
 /*
  * Solve count independent systems, each with its own handle, in as few launches as the

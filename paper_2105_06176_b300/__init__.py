@@ -35,7 +35,7 @@ _NAMES = {OK: "OK", PENDING: "PENDING", ERR_ARG: "ERR_ARG", ERR_NOT_SPD: "ERR_NO
 
 # Every symbol include/ppcg.h declares.
 EXPORTED_SYMBOLS = (
-    "ppcg_opts_default", "ppcg_create", "ppcg_solve", "ppcg_batch_solve", "ppcg_destroy",
+    "ppcg_opts_default", "ppcg_create", "ppcg_solve", "ppcg_last_info", "ppcg_batch_solve", "ppcg_destroy",
     "ppcg_server_create", "ppcg_submit", "ppcg_poll", "ppcg_server_stats", "ppcg_server_destroy",
     "ppcg_last_error", "ppcg_selftest_barrier_timeout", "ppcg_solve_noalloc",
 )
@@ -91,6 +91,8 @@ def lib(build_if_missing=True):
     L.ppcg_create.restype = ctypes.c_int
     L.ppcg_solve.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_int32, P, ctypes.POINTER(Info)]
     L.ppcg_solve.restype = ctypes.c_int
+    L.ppcg_last_info.argtypes = [P, ctypes.POINTER(Info)]
+    L.ppcg_last_info.restype = ctypes.c_int
     L.ppcg_batch_solve.argtypes = [ctypes.c_int32, P, P, P, P, P, P, P, P]
     L.ppcg_batch_solve.restype = ctypes.c_int
     L.ppcg_destroy.argtypes = [P]
@@ -185,22 +187,38 @@ class Solver:
                    np.ascontiguousarray(a.col, dtype=np.int32),
                    np.ascontiguousarray(a.val, dtype=np.float64), **kw)
 
-    def solve(self, b, x0=None, x=None, tol=1e-8, maxit=10000, stream=None, sync=True):
+    def solve(self, b, x0=None, x=None, tol=1e-8, maxit=10000, stream=None, sync=True, host_fn_info=None):
         """Enqueue a solve.  b/x0/x: torch tensors (device or host) or numpy arrays.
-        Returns (x, info); info is valid once the stream is synchronised (sync=True does it)."""
+        Returns (x, info); info is valid once the stream is synchronised (sync=True does it).
+        host_fn_info (default: not sync) passes info to ppcg_solve, which fills it from a
+        host function on the stream; otherwise info is NULL there, and with sync=True the
+        record is read after the synchronisation (ppcg_last_info), with sync=False info is
+        None and last_info() reads it after the caller's synchronisation."""
         import torch
         if x is None:
             x = torch.empty(self.n, dtype=torch.float64, device=b.device if hasattr(b, "device") else "cuda")
-        info = Info()
+        if host_fn_info is None:
+            host_fn_info = not sync
+        info = Info() if host_fn_info else None
         s = _stream_ptr(stream)
         st = lib().ppcg_solve(self.handle, _ptr(b), _ptr(x0), _ptr(x), float(tol), int(maxit), s,
-                              ctypes.byref(info))
+                              ctypes.byref(info) if host_fn_info else None)
         if st != OK:
             raise PPCGError(st, "ppcg_solve")
         if sync:
             torch.cuda.synchronize()
+            if not host_fn_info:
+                info = self.last_info()
         self._last_info = info
         return x, info
+
+    def last_info(self):
+        """ppcg_last_info: the record of this handle's latest solve (after a stream sync)."""
+        info = Info()
+        st = lib().ppcg_last_info(self.handle, ctypes.byref(info))
+        if st != OK:
+            raise PPCGError(st, "ppcg_last_info")
+        return info
 
     def close(self):
         if getattr(self, "handle", None):

@@ -315,12 +315,18 @@ bool side_stream(int device, cudaStream_t* s, cudaEvent_t* fork, cudaEvent_t* jo
   return true;
 }
 
+// The solve's record (control block and launch error flag) into the handle's pinned stage.
+void enqueue_stage_copies(ppcg_ctx* h, cudaStream_t st) {
+  cudaMemcpyAsync(&h->stage->ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&h->stage->err, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  h->last_solve = 1;
+}
+
 void enqueue_info(std::vector<std::pair<ppcg_ctx*, ppcg_info*>>& items, cudaStream_t st) {
   auto* jobs = new std::vector<InfoJob>();
   for (auto& it : items) {
     ppcg_ctx* h = it.first;
-    cudaMemcpyAsync(&h->stage->ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&h->stage->err, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    enqueue_stage_copies(h, st);
     jobs->push_back({h->stage, it.second, h->bytes_per_iter, h->opts.norm, h->opts.precision});
   }
   if (cudaLaunchHostFunc(st, info_callback, jobs) != cudaSuccess) {
@@ -588,7 +594,7 @@ ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double*
     set_error("ppcg_solve: bad arguments (tol=%g maxit=%d)", tol, maxit);
     return PPCG_ERR_ARG;
   }
-  if (h->n == 0) { write_trivial_info(info, PPCG_OK); return PPCG_OK; }
+  if (h->n == 0) { write_trivial_info(info, PPCG_OK); h->last_solve = 2; return PPCG_OK; }
   h->stream = st;
   ppcg_status s = stage_inputs(h, b, x0, false, st);
   if (s != PPCG_OK) return s;
@@ -612,9 +618,23 @@ ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double*
     return PPCG_ERR_CUDA;
   }
   stage_outputs(h, x, st);
-  std::vector<std::pair<ppcg_ctx*, ppcg_info*>> items{{h, info}};
-  enqueue_info(items, st);
+  if (info) {
+    std::vector<std::pair<ppcg_ctx*, ppcg_info*>> items{{h, info}};
+    enqueue_info(items, st);
+  } else {
+    enqueue_stage_copies(h, st);
+  }
   return check_launch("ppcg_solve") ? PPCG_OK : PPCG_ERR_CUDA;
+}
+
+ppcg_status ppcg_last_info(ppcg_handle h, ppcg_info* info) {
+  g_err[0] = 0;
+  if (!h || !info) { set_error("ppcg_last_info: NULL handle or info"); return PPCG_ERR_ARG; }
+  if (h->last_solve == 2) { write_trivial_info(info, PPCG_OK); return PPCG_OK; }
+  if (h->last_solve != 1 || !h->stage) { set_error("ppcg_last_info: the handle has not solved yet"); return PPCG_ERR_ARG; }
+  const InfoJob j{h->stage, info, h->bytes_per_iter, h->opts.norm, h->opts.precision};
+  fill_info(*h->stage, j, info);
+  return PPCG_OK;
 }
 
 ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double* const* b,
@@ -781,7 +801,7 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
   if (oc_done) cudaStreamWaitEvent(st, oc_done, 0);
   std::vector<std::pair<ppcg_ctx*, ppcg_info*>> items;
   for (int i = 0; i < count; i++) {
-    if (hs[i]->n == 0) continue;
+    if (hs[i]->n == 0) { hs[i]->last_solve = 2; continue; }
     stage_outputs(hs[i], x[i], st);
     items.push_back({hs[i], infos ? &infos[i] : nullptr});
   }

@@ -343,3 +343,29 @@ def test_server_admission_by_budget_and_errors():
         srv.submit(huge, np.ones(huge.n))
     assert e.value.status == m.ERR_OOM
     srv.close()
+
+
+def test_last_info_matches_host_function_info():
+    """ppcg_last_info after a synchronised solve with info == NULL gives the record that
+    ppcg_solve's host function writes into a non-NULL info; before any solve it is refused."""
+    m = pp()
+    a = synth.varcoeff3d(24, seed=4)
+    b = dev(synth.rhs_uniform(a.n, 4))
+    for path in (m.PATH_ONCHIP, m.PATH_CLUSTER, m.PATH_GRID):
+        s = m.Solver.from_csr(a, path=path)
+        with pytest.raises(m.PPCGError):
+            s.last_info()
+        x1, i1 = s.solve(b, tol=1e-8, maxit=5000, sync=False)        # host-function info
+        torch.cuda.synchronize()
+        x2, i2 = s.solve(b, tol=1e-8, maxit=5000, sync=True)         # info read after the sync
+        assert i2.status == i1.status == m.OK
+        for f in ("iters", "outer_iters", "rr_count", "rel_res_recursive", "rel_res_true", "bnorm",
+                  "bytes_per_iter", "fp64_fallback"):
+            assert getattr(i1, f) == getattr(i2, f), f
+        assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+        x3, i3 = s.solve(b, tol=0.0, maxit=7, sync=False, host_fn_info=False)
+        assert i3 is None
+        torch.cuda.synchronize()
+        i4 = s.last_info()
+        assert i4.status == m.ERR_NOT_CONVERGED and i4.iters == 7
+        s.close()
