@@ -49,6 +49,11 @@ def test_library_loads_and_binding_matches(libpath):
     lib.ppcg_opts_default(ctypes.byref(o))     # host-only call
     assert o.precision == pp.FP64 and o.norm == pp.NORM_REL_R and o.inner_tol == 1e-2
     assert o.epoch_iters == 256 and o.cluster_max_rows == 16384
+    # host-only argument checks: no CUDA call is made before they fail
+    info = pp.Info()
+    assert lib.ppcg_last_info(None, ctypes.byref(info)) == pp.ERR_ARG
+    lib.ppcg_last_error.restype = ctypes.c_char_p
+    assert b"ppcg_last_info" in lib.ppcg_last_error()
 
 
 def test_struct_layouts_match_header(tmp_path):
