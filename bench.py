@@ -8,13 +8,17 @@ final true residual, all inside the library's persistent kernel.
 
 Printed (rank 0, one JSON line): iterations/s over all ranks (value), end-to-end
 iterations/s through host buffers (e2e), the roofline of the solve kernel against the
-measured HBM copy bandwidth, SM clocks sampled during the timed region, the FP32+IR vs
-FP64 time to 1e-8 on the same system, and the CPU oracle timed on a bounded sample.
+measured HBM copy bandwidth (with the DRAM traffic of the committed ncu capture), SM clocks
+sampled during the timed region, the FP32 forms (reliable updates; inner solves in FP64
+refinement) and the Jacobi-scaled variant against FP64 in time to 1e-8 on the same system,
+the 64^2 solve latency, a batch and a serving figure, and the CPU oracle (single-thread and
+OpenMP builds) timed on a bounded sample.
 
 Multi-GPU: replicas only.  Each rank solves its own copy; value = all ranks' iterations /
 the slowest rank's time ("scaling": "weak").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --mode batch|serve|rgg|paper|box125|latency   (one workload's figures)
 """
 import argparse
 import json
