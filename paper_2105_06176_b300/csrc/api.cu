@@ -264,7 +264,8 @@ void prepare_control(ppcg_ctx* h, double tol, int32_t maxit, cudaStream_t st) {
 size_t footprint_bytes(int64_t n, int64_t nnz, int32_t precision) {
   const bool fp32 = precision != PPCG_FP64;
   const double slots = 1.05 * (double)nnz + 32.0 * ((double)n / 32.0 + 1.0);
-  double bytes = slots * (fp32 ? 16.0 : 12.0) + (double)n * 8.0 * 6.0;   // matrix + cptr/diag/invd/b/tmp/perm
+  // matrix (values, columns and the one-byte column dictionary) + cptr/diag/invd/b/tmp/perm
+  double bytes = slots * (fp32 ? 17.0 : 13.0) + (double)n * 8.0 * 6.0;
   bytes += (double)n * 8.0 * 10.0 + (fp32 ? (double)n * 4.0 * 11.0 : 0.0);
   return (size_t)bytes + (1u << 20);
 }
@@ -500,6 +501,8 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
     if (const char* e = getenv("PPCG_GRID_SHAPE")) k = atoi(e);
     if (k < 0 || k >= nshapes) k = 0;
     h->shape = box ? grid_box_shape_first() + k : k;
+    // the column dictionary, where the matrix has one, on the default shape
+    if (!box && k == 0 && h->A.cidx) h->shape = grid_dict_shape();
     // One CTA per SM at most for small systems: enough warps for one 32-row chunk each,
     // so the grid barrier spans only the CTAs that have rows to work on.
     const int full = grid_blocks_for_device(h->device, h->shape);

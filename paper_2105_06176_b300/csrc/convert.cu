@@ -10,6 +10,9 @@
 // A v) exactly, as the first term of each row sum.
 #include <algorithm>
 #include <chrono>
+#include <climits>
+#include <cstdint>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -97,6 +100,57 @@ __global__ void k_fill(int64_t n, int64_t nchunks, const int64_t* __restrict__ r
     scol[slot] = (int32_t)(i < n ? i : n - 1);
     sval[slot] = 0.0;
     if (sval32) sval32[slot] = 0.0f;
+  }
+}
+
+// Column dictionary.  The distinct offsets col - row of the SELL slots are collected in an
+// open-addressing table of kDictTable entries (kDictEmpty marks a free entry); then every
+// slot gets the one-byte index of its offset.  Collection stops (overflow) once more than
+// kColDict offsets appear: unstructured matrices keep their 4-byte columns.
+constexpr int kDictTable = 1024;
+constexpr int32_t kDictEmpty = INT32_MIN;
+
+__device__ __forceinline__ int dict_probe(int32_t* table, int32_t key, bool insert, int32_t* count,
+                                          int32_t* overflow) {
+  const uint32_t h = (uint32_t)key * 2654435761u;
+  for (int probe = 0; probe < kDictTable; probe++) {
+    const int pos = (int)((h + (uint32_t)probe) & (kDictTable - 1));
+    const int32_t cur = ((volatile int32_t*)table)[pos];
+    if (cur == key) return pos;
+    if (cur != kDictEmpty) continue;
+    if (!insert || *(volatile int32_t*)overflow) return -1;
+    const int32_t prev = atomicCAS(table + pos, kDictEmpty, key);
+    if (prev == kDictEmpty) {
+      if (atomicAdd(count, 1) >= kColDict) atomicExch(overflow, 1);
+      return pos;
+    }
+    if (prev == key) return pos;
+  }
+  atomicExch(overflow, 1);
+  return -1;
+}
+
+// One thread per (chunk, lane), as k_fill: insert the offsets of the lane's slots (pass 0),
+// or write each slot's dictionary index (pass 1, after the table is final).
+__global__ void k_dict(int64_t nchunks, const int64_t* __restrict__ cptr, const int32_t* __restrict__ scol,
+                       int32_t* table, int32_t* count, int32_t* overflow, const uint8_t* __restrict__ pos2idx,
+                       uint8_t* __restrict__ cidx) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = t / kChunk;
+  const int lane = (int)(t % kChunk);
+  if (c >= nchunks) return;
+  const int64_t i = c * kChunk + lane;
+  const int64_t base = cptr[c];
+  const int len = (int)((cptr[c + 1] - base) / kChunk);
+  for (int j = 0; j < len; j++) {
+    const int64_t slot = base + (int64_t)j * kChunk + lane;
+    const int32_t key = (int32_t)((int64_t)scol[slot] - i);
+    if (!cidx) {
+      if (dict_probe(table, key, true, count, overflow) < 0) return;
+    } else {
+      const int pos = dict_probe(table, key, false, count, overflow);
+      cidx[slot] = pos < 0 ? 0 : pos2idx[pos];
+    }
   }
 }
 
@@ -228,6 +282,61 @@ bool detect_box_stencil(int64_t n, int64_t nnz, const int64_t* d_rp, const int32
   return true;
 }
 
+// Build A's column dictionary on the device; leaves A->cidx = nullptr (and returns 0) when
+// the matrix has more than kColDict distinct offsets or PPCG_COL_DICT=0 is set.  Returns the
+// dictionary size, or -1 when a device allocation failed.  Synchronises st.
+int build_col_dict(DevMatrix* A, std::vector<void*>& allocs, cudaStream_t st) {
+  A->cidx = nullptr;
+  A->coff = nullptr;
+  if (const char* e = getenv("PPCG_COL_DICT")) if (e[0] == '0') return 0;   // diagnostic knob
+  if (A->nslots == 0) return 0;
+  int32_t* d_tab = nullptr;   // table, count, overflow
+  if (pool_alloc((void**)&d_tab, (kDictTable + 2) * sizeof(int32_t), st) != cudaSuccess) { cudaGetLastError(); return -1; }
+  std::vector<int32_t> h(kDictTable + 2, kDictEmpty);
+  h[kDictTable] = 0;
+  h[kDictTable + 1] = 0;
+  cudaMemcpyAsync(d_tab, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  const int tb = 256;
+  const int64_t threads = A->nchunks * kChunk;
+  const unsigned blocks = (unsigned)((threads + tb - 1) / tb);
+  k_dict<<<blocks, tb, 0, st>>>(A->nchunks, A->cptr, A->col, d_tab, d_tab + kDictTable, d_tab + kDictTable + 1,
+                                nullptr, nullptr);
+  cudaMemcpyAsync(h.data(), d_tab, h.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  int size = 0;
+  bool oom = false;
+  uint8_t* d_cidx = nullptr;
+  int32_t* d_coff = nullptr;
+  uint8_t* d_pos2idx = nullptr;
+  if (cudaStreamSynchronize(st) == cudaSuccess && h[kDictTable + 1] == 0 && h[kDictTable] <= kColDict) {
+    std::vector<uint8_t> pos2idx(kDictTable, 0);
+    std::vector<int32_t> coff(kColDict, 0);
+    for (int pos = 0; pos < kDictTable; pos++)
+      if (h[pos] != kDictEmpty) { pos2idx[pos] = (uint8_t)size; coff[size++] = h[pos]; }
+    if (dalloc(&d_cidx, (size_t)A->nslots, allocs, st) == cudaSuccess &&
+        dalloc(&d_coff, (size_t)kColDict, allocs, st) == cudaSuccess &&
+        pool_alloc((void**)&d_pos2idx, kDictTable, st) == cudaSuccess) {
+      cudaMemcpyAsync(d_coff, coff.data(), kColDict * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(d_pos2idx, pos2idx.data(), kDictTable, cudaMemcpyHostToDevice, st);
+      k_dict<<<blocks, tb, 0, st>>>(A->nchunks, A->cptr, A->col, d_tab, d_tab + kDictTable,
+                                    d_tab + kDictTable + 1, d_pos2idx, d_cidx);
+      if (cudaStreamSynchronize(st) == cudaSuccess && cudaGetLastError() == cudaSuccess) {
+        A->cidx = d_cidx;
+        A->coff = d_coff;
+      } else {
+        size = 0;
+      }
+    } else {
+      size = 0;
+      oom = true;
+    }
+  }
+  cudaGetLastError();
+  if (d_pos2idx) pool_free(d_pos2idx, st);
+  pool_free(d_tab, st);
+  if (oom) return -1;
+  return A->cidx ? size : 0;
+}
+
 ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col,
                                 const double* d_val, int32_t sigma_req, bool want_fp32, bool sym_scale,
                                 cudaStream_t st, std::vector<void*>& allocs, SellBuild* out,
@@ -344,6 +453,8 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   A->nslots = nslots;
   A->cptr = d_cptr;
   A->col = d_scol;
+  A->cidx = nullptr;
+  A->coff = nullptr;
   A->val = d_sval;
   A->val32 = d_sval32;
   A->invd = d_sinvd;
@@ -360,6 +471,11 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
     int64_t per8[8];
     for (int r = 0; r < 8; r++) per8[r] = per[r] + per[r + 8];   // c % 8 == r  <=>  c % 16 in {r, r + 8}
     out->onchip_slots = *std::max_element(per8, per8 + 8);
+  }
+  out->col_dict = build_col_dict(A, allocs, st);
+  if (out->col_dict < 0) {
+    set_error("ppcg_create: out of device memory for the column dictionary");
+    return PPCG_ERR_OOM;
   }
   out->sigma = (int32_t)sigma;
   out->padding = nnz > n ? (double)(nslots - (nnz - n)) / (double)(nnz - n) : 0.0;

@@ -25,6 +25,12 @@ struct DevMatrix {
   int64_t nslots;
   const int64_t* cptr;   // [nchunks + 1] slot offset of each chunk (multiple of 32)
   const int32_t* col;    // [nslots] column-major within a chunk: slot(base + j*32 + lane)
+  // Column dictionary (nullptr when the matrix has more than kColDict distinct offsets):
+  // col[s] == row(s) + coff[cidx[s]], row(s) = chunk * 32 + lane of slot s.  Stencil-like
+  // matrices have a handful of distinct col - row offsets, so the iteration pass reads one
+  // byte per slot instead of four.
+  const uint8_t* cidx;   // [nslots]
+  const int32_t* coff;   // [kColDict]
   const double* val;     // [nslots] a_ij / a_jj
   const float* val32;    // [nslots] same rounded to FP32 (FP32 modes only)
   const double* invd;    // [n] 1 / a_ii
@@ -128,6 +134,7 @@ bool onchip_cluster_fits(int nc, size_t smem);                      // can one s
 int grid_shape_count();        // SELL/CSR plans: shapes [0, grid_shape_count())
 int grid_box_shape_first();    // matrix-free box plans: shapes first + [0, count)
 int grid_box_shape_count();
+int grid_dict_shape();         // the default SELL shape reading the column dictionary
 int grid_threads(int shape);
 int grid_blocks_for_device(int device, int shape);
 int max_active_clusters(int device);
@@ -135,6 +142,8 @@ cudaError_t launch_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, i
                                     int drop_rank, int64_t limit_ns, cudaStream_t st);
 
 // Conversion (convert.cu)
+constexpr int kColDict = 255;   // largest column dictionary (a one-byte index)
+
 struct SellBuild {
   int64_t nchunks = 0, nslots = 0;
   int32_t sigma = 1;
@@ -143,6 +152,7 @@ struct SellBuild {
   double dmin = 0.0, dmax = 0.0;   // extreme diagonal entries
   int64_t onchip_slots = 0;        // SELL slots of the fullest CTA when chunk c goes to CTA c % 8
   int64_t onchip_slots16 = 0;      // the same for clusters of 16 CTAs
+  int32_t col_dict = 0;            // distinct col - row offsets in the dictionary (0: none)
 };
 ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col,
                                 const double* d_val, int32_t sigma_req, bool want_fp32, bool sym_scale,

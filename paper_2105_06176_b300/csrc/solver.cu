@@ -238,11 +238,23 @@ template <typename T, int NS> struct GatherSlot {
   }
 };
 
+// Column of SELL slot s: the 4-byte column array, or the column dictionary (DevMatrix):
+// row + coff[cidx[s]], one byte read per slot.
+__device__ __forceinline__ int32_t slot_col(const int32_t* __restrict__ col, int64_t s) { return ld_stream(col + s); }
+struct ColDict {
+  const uint8_t* __restrict__ idx;
+  const int32_t* __restrict__ off;
+  int32_t row;
+};
+__device__ __forceinline__ int32_t slot_col(const ColDict& d, int64_t s) {
+  return d.row + __ldg(d.off + __ldcs(d.idx + s));
+}
+
 // acc + sum_j val[slot_j] * x(col[slot_j]) (* dsc[col] when SCALE) over the row's
 // off-diagonal slots base + j*32, j < len, in CSR order; acc enters holding the diagonal
-// term.
-template <typename T, bool SCALE, class G>
-__device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* __restrict__ val, const G& x,
+// term.  CS: the column source (const int32_t* or ColDict).
+template <typename T, bool SCALE, class G, class CS>
+__device__ __forceinline__ T row_dot(const CS& col, const T* __restrict__ val, const G& x,
                                      const T* __restrict__ dsc, int64_t base, int len, T acc) {
   int j = 0;
   for (; j + 8 <= len; j += 8) {
@@ -250,7 +262,7 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* _
     T a[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-      c[k] = ld_stream(col + base + (int64_t)(j + k) * kChunk);
+      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk);
       a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
 #pragma unroll
@@ -265,7 +277,7 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* _
 #pragma unroll
   for (int k = 0; k < 7; k++) {
     if (j + k < len) {
-      c[k] = ld_stream(col + base + (int64_t)(j + k) * kChunk);
+      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk);
       a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
   }
@@ -283,8 +295,8 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ col, const T* _
 // Two products over the same row in one sweep of its slots: acc1 += A x1, acc2 += A x2.
 // Each accumulator sees the same FMA sequence as a row_dot of its own, so results are
 // identical; the matrix slots are read once instead of twice.
-template <typename T, bool SCALE, class G1, class G2>
-__device__ __forceinline__ void row_dot2(const int32_t* __restrict__ col, const T* __restrict__ val, const G1& x1,
+template <typename T, bool SCALE, class G1, class G2, class CS>
+__device__ __forceinline__ void row_dot2(const CS& col, const T* __restrict__ val, const G1& x1,
                                          const G2& x2, const T* __restrict__ dsc, int64_t base, int len, T& acc1,
                                          T& acc2) {
   int j = 0;
@@ -293,7 +305,7 @@ __device__ __forceinline__ void row_dot2(const int32_t* __restrict__ col, const 
     T a[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-      c[k] = ld_stream(col + base + (int64_t)(j + k) * kChunk);
+      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk);
       a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
 #pragma unroll
@@ -309,7 +321,7 @@ __device__ __forceinline__ void row_dot2(const int32_t* __restrict__ col, const 
 #pragma unroll
   for (int k = 0; k < 7; k++) {
     if (j + k < len) {
-      c[k] = ld_stream(col + base + (int64_t)(j + k) * kChunk);
+      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk);
       a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
   }
@@ -332,7 +344,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 }
 template <typename T, int NS>
 __device__ __forceinline__ void prefetch_chunk(const int64_t* __restrict__ cptr, const int32_t* __restrict__ col,
-                                               const T* __restrict__ val, const T* blk, int32_t c, int lane) {
+                                               const uint8_t* __restrict__ cidx, const T* __restrict__ val,
+                                               const T* blk, int32_t c, int lane) {
   constexpr int kTileBytes = NS * kChunk * (int)sizeof(T);
   const char* tile = reinterpret_cast<const char*>(blk + (int64_t)c * NS * kChunk);
   for (int off = lane * 128; off < kTileBytes; off += 32 * 128) prefetch_l2(tile + off);
@@ -341,9 +354,9 @@ __device__ __forceinline__ void prefetch_chunk(const int64_t* __restrict__ cptr,
   // their matrix slots a chunk ahead from every warp would overflow L2 (the 125-point box:
   // 32 KB per chunk); only the vector tile is prefetched for them.
   if (b1 - b0 > 16 * kChunk) return;
-  const char* pc = reinterpret_cast<const char*>(col + b0);
+  const char* pc = cidx ? reinterpret_cast<const char*>(cidx + b0) : reinterpret_cast<const char*>(col + b0);
   const char* pv = reinterpret_cast<const char*>(val + b0);
-  const int nc = (int)((b1 - b0) * 4), nv = (int)((b1 - b0) * (int64_t)sizeof(T));
+  const int nc = (int)((b1 - b0) * (cidx ? 1 : 4)), nv = (int)((b1 - b0) * (int64_t)sizeof(T));
   for (int off = lane * 128; off < nc; off += 32 * 128) prefetch_l2(pc + off);
   for (int off = lane * 128; off < nv; off += 32 * 128) prefetch_l2(pv + off);
 }
@@ -442,7 +455,7 @@ __device__ __forceinline__ void pass_setup2(const DevMatrix& A, const View<T, NS
 
 // P_ITER: one full iteration of Alg. 2 for the group's rows (see the file comment).  The
 // row's own vector entries are loaded before the gather so their latency overlaps it.
-template <typename T, int NS, bool FIRST>
+template <typename T, int NS, bool FIRST, bool DICT = false>
 __device__ __forceinline__ void pass_iter(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, Dots<T>& d,
                                           T alpha, T beta, int k, bool paper_norm, bool with_rr = true) {
   const int wcs = (k & 1) ? V_WB : V_WA;
@@ -456,7 +469,7 @@ __device__ __forceinline__ void pass_iter(const DevMatrix& A, const View<T, NS>&
     // same occupancy), 433 -> 350 us per 256^3 iteration; the FP64 pass, already near the
     // HBM and FP64-pipe limits, ran 10-20% slower with it.
     if (PPCG_PREFETCH && sizeof(T) == 4 && c + L.W < (int32_t)A.nchunks)
-      prefetch_chunk<T, NS>(A.cptr, col, val, V.v.b, c + L.W, L.lane);
+      prefetch_chunk<T, NS>(A.cptr, col, DICT ? A.cidx : nullptr, val, V.v.b, c + L.W, L.lane);
     int64_t base; int len;
     chunk_slots(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
@@ -478,7 +491,9 @@ __device__ __forceinline__ void pass_iter(const DevMatrix& A, const View<T, NS>&
       }
     }
     // n_i = (A M^-1 w)_i = w_i + sum_{j != i} ahat_ij w_j
-    const T ni = row_dot<T, false>(col, val, gw, nullptr, base, len, wi);
+    T ni;
+    if constexpr (DICT) ni = row_dot<T, false>(ColDict{A.cidx, A.coff, row}, val, gw, nullptr, base, len, wi);
+    else ni = row_dot<T, false>(col, val, gw, nullptr, base, len, wi);
     if (in) {
       const T mi = id * wi;
       const T zi = FIRST ? ni : fma(beta, zo, ni);
@@ -683,7 +698,7 @@ __device__ __forceinline__ void pass_rr2(const DevMatrix& A, const View<T, NS>& 
   const GatherSlot<T, NS> gs{V.v.b + V_S * kChunk};
   FOR_CHUNKS(A, L) {
     if (PPCG_PREFETCH && sizeof(T) == 4 && c + L.W < (int32_t)A.nchunks)
-      prefetch_chunk<T, NS>(A.cptr, A.col, V.val, V.v.b, c + L.W, L.lane);
+      prefetch_chunk<T, NS>(A.cptr, A.col, nullptr, V.val, V.v.b, c + L.W, L.lane);
     int64_t base; int len;
     chunk_slots(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
@@ -1837,7 +1852,9 @@ constexpr int kSmGrid = 3 * 32, kSmCluster = 3 * 32 * (kClusterThreads / 32);
 // BOX: the kernel carries the matrix-free box passes (a plan with box_g > 0 runs only on
 // such a kernel, every other plan only on the others, so the SELL kernels' register
 // allocation does not carry the box code); a mismatch ends the solve with PPCG_ERR_ARG.
-template <bool STAGED, bool BOX = false, class G, class Shared>
+// DICT: the iteration passes read the column dictionary (a plan without one ends with
+// PPCG_ERR_ARG on such a kernel; kernels without DICT read the 4-byte columns).
+template <bool STAGED, bool BOX = false, bool DICT = false, class G, class Shared>
 __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsigned char* stage_mem,
                            uint64_t* stage_bars, unsigned& phases) {
   __syncthreads();   // previous system's readers of sh are done
@@ -1849,7 +1866,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
     for (int i = 0; i < (int)(sizeof(Ctl) / 8); i++) dst[i] = __ldcg(src + i);
     if (sh.C.t_start == 0) sh.C.t_start = globaltimer();
     sh.C.exit_now = 0;
-    if ((sh.S.box_g > 0) != BOX) { sh.C.status = PPCG_ERR_ARG; sh.C.state = S_DONE; }
+    if ((sh.S.box_g > 0) != BOX || (DICT && !sh.S.A.cidx)) { sh.C.status = PPCG_ERR_ARG; sh.C.state = S_DONE; }
   }
   __syncthreads();
   const SysDesc& S = sh.S;
@@ -1916,8 +1933,8 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
             if (C.first) pass_iter_staged<double, kNS64, true>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, wst, bars, phases, S.err);
             else pass_iter_staged<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, wst, bars, phases, S.err);
           } else {
-            if (C.first) pass_iter<double, kNS64, true>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
-            else pass_iter<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
+            if (C.first) pass_iter<double, kNS64, true, DICT>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
+            else pass_iter<double, kNS64, false, DICT>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
           }
           break;
         case P_TRUE: pass_true<kNS64, V_X>(S, L, d); break;
@@ -1956,8 +1973,8 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
             if (C.first) pass_iter_staged<float, kNS32, true>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper, wst, bars, phases, S.err);
             else pass_iter_staged<float, kNS32, false>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper, wst, bars, phases, S.err);
           } else {
-            if (C.first) pass_iter<float, kNS32, true>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
-            else pass_iter<float, kNS32, false>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
+            if (C.first) pass_iter<float, kNS32, true, DICT>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
+            else pass_iter<float, kNS32, false, DICT>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
           }
           break;
         case P_RR1: pass_rr1(S.A, V, L, C.inner_iter == 0 || C.restart); partials = false; break;
@@ -1991,7 +2008,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
   }
 }
 
-template <int THREADS, int MINB, bool STAGED, bool BOX = false>
+template <int THREADS, int MINB, bool STAGED, bool BOX = false, bool DICT = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_grid(const SysDesc* d, int budget) {
   __shared__ SharedT<kSmGrid> sh;
   __shared__ uint64_t bars[2 * (THREADS / 32)];
@@ -2006,13 +2023,14 @@ __global__ void __launch_bounds__(THREADS, MINB) k_grid(const SysDesc* d, int bu
     __syncthreads();
   }
   GridGroup g{d->bar, d->err, (long long)d->spin_limit_ns, 0u};
-  run_system<STAGED, BOX>(g, d, budget, sh, stage_mem, bars, phases);
+  run_system<STAGED, BOX, DICT>(g, d, budget, sh, stage_mem, bars, phases);
 }
 
 // Launch shapes of the grid path: (threads per CTA, minimum CTAs per SM for the register
 // budget, bulk-copy staging).  Index 0 is the default (fastest measured on the 256^3
 // stencil); the others trade registers, resident warps and staging.  From kFirstBoxShape on:
-// the kernels of matrix-free box-stencil plans.
+// the kernels of matrix-free box-stencil plans; last, the default shape reading the column
+// dictionary (plans whose matrix has one).
 struct GridShape {
   void (*fn)(const SysDesc*, int);
   int threads;
@@ -2025,9 +2043,12 @@ const GridShape kGridShapes[] = {
     {k_grid<384, 1, true>, 384, 12 * kWarpStageBytes},
     {k_grid<512, 2, false, true>, 512, 0}, {k_grid<256, 4, false, true>, 256, 0},
     {k_grid<1024, 1, false, true>, 1024, 0},
+    {k_grid<512, 2, false, false, true>, 512, 0},
 };
 constexpr int kNumGridShapes = (int)(sizeof(kGridShapes) / sizeof(kGridShapes[0]));
 constexpr int kFirstBoxShape = 9;
+constexpr int kDictShape = 12;   // the default shape with the column dictionary
+static_assert(kDictShape == kNumGridShapes - 1, "the dictionary kernel is the last shape");
 
 // Cluster path.  Static schedule (next == nullptr): cluster c runs list[list_ptr[c] ..
 // list_ptr[c + 1]).  Dynamic schedule: every cluster takes the next entry of list (ordered
@@ -2406,7 +2427,8 @@ __global__ void k_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, in
 
 int grid_shape_count() { return kFirstBoxShape; }
 int grid_box_shape_first() { return kFirstBoxShape; }
-int grid_box_shape_count() { return kNumGridShapes - kFirstBoxShape; }
+int grid_box_shape_count() { return kDictShape - kFirstBoxShape; }
+int grid_dict_shape() { return kDictShape; }
 int grid_threads(int shape) { return kGridShapes[shape].threads; }
 
 cudaError_t ensure_smem_attr(const void* fn, size_t bytes);

@@ -500,3 +500,17 @@ def test_mixed_launch_shapes(shape, precision, monkeypatch):
     assert t <= 1e-8
     x64 = oracle.pipecg(a, b, tol=1e-10, maxit=20000)["x"]
     assert rel(x, x64) <= 1e-4
+
+
+def test_column_dictionary_gives_bitwise_the_same_iterates(monkeypatch):
+    """A stencil's SELL columns as one-byte indices into its few col - row offsets (the
+    default where a matrix has at most 255 of them) and as plain 4-byte columns
+    (PPCG_COL_DICT=0) give bitwise the same iterates: only the addressing differs."""
+    for name, prec in (("varcoeff3d_31", 0), ("box125_12", 0), ("varcoeff3d_31", 2)):
+        a, b = problem(name)
+        x1, i1 = gpu(a, b, tol=0.0, maxit=25, path=1, format=2, precision=prec)
+        monkeypatch.setenv("PPCG_COL_DICT", "0")
+        x0, i0 = gpu(a, b, tol=0.0, maxit=25, path=1, format=2, precision=prec)
+        monkeypatch.delenv("PPCG_COL_DICT")
+        assert i1.iters == i0.iters == 25
+        assert np.array_equal(x1, x0), name
