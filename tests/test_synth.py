@@ -137,3 +137,23 @@ def test_batch_mix_sizes():
     assert sizes.min() >= 900 and sizes.max() <= 2.1e5
     assert 0.4 < np.mean([f == "varcoeff2d" for f, *_ in specs]) < 0.6
     assert 8e3 < np.median(sizes) < 2.2e4
+
+
+def test_fullsize_golden_matches_the_generators():
+    """The stored full-size oracle record (tests/golden/fullsize_oracle.json) belongs to the
+    inputs the generators make today: the batch's 1024 system sizes, the 256^3 grid and the
+    RGG parameters; its calibrated fixed k meets the 1e-12 rounding-sensitivity rule."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_oracle.json")) as f:
+        gold = json.load(f)
+    specs = synth.batch_mix(gold["batch_1024"]["count"], gold["batch_1024"]["seed"])
+    assert len(specs) == len(gold["batch_1024"]["systems"]) == 1024
+    for (fam, size, _, _), rec in zip(specs, gold["batch_1024"]["systems"]):
+        assert rec["n"] == (size ** 2 if fam == "varcoeff2d" else size ** 3)
+        assert rec["status"] == 0 and rec["rel_res_true"] <= 1e-8
+    vc = gold["varcoeff3d_256"]
+    assert vc["grid"] == 256 and vc["iters"] > 0 and vc["rel_res_true"] <= 1e-8
+    for rec in (vc, gold["rgg_4M"]):
+        assert rec["fixed_k"] in (5, 10, 20) and rec["fixed_k_rel_diff_seq_vs_pairwise"] <= 1e-12
+    assert gold["rgg_4M"]["iters_1e-10"] > gold["rgg_4M"]["iters_1e-08"]
