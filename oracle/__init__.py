@@ -66,7 +66,8 @@ def lib(openmp=False):
         _lib.oracle_spmv.restype = None
         _lib.oracle_pipecg.argtypes = [ctypes.c_int64, P, P, P, P, P, P, ctypes.c_double,
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                       ctypes.c_int32, ctypes.c_int32, P, P, P, P, ctypes.POINTER(Result)]
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                       P, P, P, P, ctypes.POINTER(Result)]
         _lib.oracle_pipecg.restype = ctypes.c_int
         _lib.oracle_pcg.argtypes = [ctypes.c_int64, P, P, P, P, P, P, ctypes.c_double,
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -101,11 +102,18 @@ def spmv(a, x, openmp=False):
     return y
 
 
+GAP_THETA, GAP_FALL = 1e-6, 100.0
+
+
 def pipecg(a, b, x0=None, tol=1e-8, maxit=10000, norm=NORM_REL_R, rr_period=0, max_restarts=8,
-           jacobi_elim=False, sum_mode=0, history=False, state=False, openmp=False):
+           jacobi_elim=False, sum_mode=0, gap_theta=GAP_THETA, gap_fall=GAP_FALL, history=False,
+           state=False, openmp=False):
     """Algorithm 2 (with restart on breakdown, up to max_restarts times).  jacobi_elim: the
-    variant with q = M^-1 s and u = M^-1 r in place of their recurrences.  openmp: the
-    OpenMP build of the same source (bitwise-identical results).
+    variant with q = M^-1 s and u = M^-1 r in place of their recurrences.  gap_theta > 0:
+    measured-gap residual replacement (each time gamma has fallen by gap_fall since the
+    residuals were last measured or replaced, replace them if ||(b - A x) - r|| exceeds
+    gap_theta ||r||); 0 turns it off.  openmp: the OpenMP build of the same source
+    (bitwise-identical results).
     Returns dict(x, result, [alpha, beta, res], [state])."""
     rp, ci, v = _csr_args(a)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -117,7 +125,8 @@ def pipecg(a, b, x0=None, tol=1e-8, maxit=10000, norm=NORM_REL_R, rr_period=0, m
     st = np.empty(10 * a.n) if state else None
     res = Result()
     lib(openmp).oracle_pipecg(a.n, _ptr(rp), _ptr(ci), _ptr(v), _ptr(b), _ptr(x0), _ptr(x), tol,
-                        maxit, norm, rr_period, max_restarts, int(bool(jacobi_elim)), sum_mode, _ptr(ah),
+                        maxit, norm, rr_period, max_restarts, int(bool(jacobi_elim)), sum_mode,
+                        float(gap_theta), float(gap_fall), _ptr(ah),
                         _ptr(bh), _ptr(rh),
                         _ptr(st), ctypes.byref(res))
     out = {"x": x, "result": res.as_dict()}

@@ -29,6 +29,15 @@
  *     formed; if it fails, the recurrence vectors are replaced by their true values
  *     (residual replacement, not in the paper) and the iteration continues.
  *   - rr_period > 0 additionally replaces residuals every rr_period iterations.
+ *   - gap_theta > 0 (not in the paper; the accuracy criterion of the residual-replacement
+ *     literature for pipelined CG: van der Vorst & Ye 2000, Cools et al., SIMAX 2018):
+ *     whenever gamma has fallen by the factor gap_fall since the residuals were last
+ *     measured or replaced, the deviation of the recursive residual from the true one,
+ *     ||(b - A x) - r||, is measured, and the residuals are replaced when it exceeds
+ *     gap_theta * ||r||.  Replacing while that deviation is still small keeps the alpha
+ *     and beta recurrences consistent with the vectors; a replacement made only once the
+ *     recursive residual has passed the stopping test can change r by a percent or more
+ *     and derail the iteration (it can then grow until the alpha denominator breaks down).
  *   - jacobi_elim (a variant, not the paper's literal algorithm): with a diagonal M the
  *     recurrences of q and u in the update block reproduce q = M^-1 s and u = M^-1 r in exact
  *     arithmetic, so the variant computes q and u from s and r after their updates instead.
@@ -147,7 +156,8 @@ static double true_residual(int64_t n, const int64_t* rp, const int32_t* ci, con
 int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
                   const double* b, const double* x0, double* x, double tol, int32_t maxit,
                   int32_t norm_mode, int32_t rr_period, int32_t max_restarts, int32_t jacobi_elim,
-                  int32_t sum_mode, double* alpha_hist, double* beta_hist, double* res_hist,
+                  int32_t sum_mode, double gap_theta, double gap_fall,
+                  double* alpha_hist, double* beta_hist, double* res_hist,
                   double* state_out, oracle_result* res) {
   memset(res, 0, sizeof(*res));
   if (n < 0 || maxit < 0 || !(tol >= 0.0)) { res->status = OR_ERR_ARG; return res->status; }
@@ -171,6 +181,7 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
   int restart = 0;        /* the next step starts the recurrences afresh (beta = 0) */
   int32_t restarts = 0;
   int32_t last_rr_it = -1; /* iteration of the latest residual replacement */
+  double gamma_ref = 0.0;  /* gamma when the residuals were last measured or replaced */
 
   for (int64_t i = 0; i < n; i++) x[i] = x0 ? x0[i] : 0.0;
   res->bnorm = sqrt(dot(sum_mode, n, b, b));
@@ -191,6 +202,7 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
   gamma = dot(sum_mode, n, r, u);
   delta = dot(sum_mode, n, w, u);
   norm = norm_mode ? sqrt(dot(sum_mode, n, u, u)) : sqrt(dot(sum_mode, n, r, r));
+  gamma_ref = gamma;
   /* setup: m0 = M^-1 w0; n0 = A m0 */
   apply_jacobi(n, d, w, m);
   oracle_spmv(n, rp, ci, v, m, nv);
@@ -200,6 +212,16 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
     if (res_hist) res_hist[it] = norm;
     /* optional periodic residual replacement (not in the paper) */
     int replace = (rr_period > 0 && it > 0 && it % rr_period == 0 && last_rr_it != it);
+    /* optional measured-gap replacement (not in the paper) */
+    if (!replace && gap_theta > 0.0 && it > 0 && gamma > 0.0 && gamma * gap_fall <= gamma_ref) {
+      oracle_spmv(n, rp, ci, v, x, tmp);
+#pragma omp parallel for schedule(static)
+      for (int64_t i = 0; i < n; i++) tmp[i] = (b[i] - tmp[i]) - r[i];
+      double gap = sqrt(dot(sum_mode, n, tmp, tmp));
+      double rnorm = sqrt(dot(sum_mode, n, r, r));
+      gamma_ref = gamma;
+      if (gap > gap_theta * rnorm) replace = 1;
+    }
     /* stop test at the top of iteration i on norm_i */
     if (!replace) {
       int passed = norm_mode ? (norm <= tol) : (norm <= tol * res->bnorm);
@@ -227,6 +249,7 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
       norm = norm_mode ? sqrt(dot(sum_mode, n, u, u)) : sqrt(dot(sum_mode, n, r, r));
       res->rr_count++;
       last_rr_it = it;
+      gamma_ref = gamma;
       if (norm_mode ? (norm <= tol) : (norm <= tol * res->bnorm)) { status = OR_OK; break; }
     }
     if (it >= maxit) { status = OR_ERR_NOT_CONVERGED; break; }
@@ -252,6 +275,7 @@ int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
         norm = norm_mode ? sqrt(dot(sum_mode, n, u, u)) : sqrt(dot(sum_mode, n, r, r));
         res->rr_count++;
         last_rr_it = it;
+        gamma_ref = gamma;
         restart = 1;
         it--;              /* re-enter the top of this iteration with the new values */
         continue;

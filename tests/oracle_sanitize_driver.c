@@ -19,8 +19,8 @@ typedef struct {
 int oracle_pipecg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* b,
                   const double* x0, double* x, double tol, int32_t maxit, int32_t norm_mode,
                   int32_t rr_period, int32_t max_restarts, int32_t jacobi_elim, int32_t sum_mode,
-                  double* alpha_hist, double* beta_hist, double* res_hist, double* state_out,
-                  oracle_result* res);
+                  double gap_theta, double gap_fall, double* alpha_hist, double* beta_hist,
+                  double* res_hist, double* state_out, oracle_result* res);
 int oracle_pcg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* b,
                const double* x0, double* x, double tol, int32_t maxit, int32_t norm_mode, int32_t sum_mode,
                double* alpha_hist, double* beta_hist, double* res_hist, double* state_out, oracle_result* res);
@@ -59,15 +59,17 @@ int main(void) {
   double* rh = malloc((maxit + 1) * sizeof(double));
   double* st = malloc(10 * n * sizeof(double));
   oracle_result r;
-  struct { const char* name; int alg, norm, rr, restarts, elim, sum, use_x0, hist, it; double tol; } runs[] = {
-    {"pipecg", 2, 0, 0, 8, 0, 0, 0, 1, maxit, 1e-8},
-    {"pipecg_paper", 2, 1, 0, 8, 0, 0, 0, 0, maxit, 1e-5},
-    {"pipecg_rr", 2, 0, 7, 8, 0, 0, 1, 1, maxit, 1e-8},
-    {"pipecg_elim", 2, 0, 0, 8, 1, 0, 0, 1, maxit, 1e-8},
-    {"pipecg_pairwise", 2, 0, 0, 8, 0, 1, 0, 0, maxit, 1e-8},
-    {"pipecg_maxit", 2, 0, 0, 8, 0, 0, 0, 1, 5, 1e-8},
-    {"pcg", 1, 0, 0, 0, 0, 0, 0, 1, maxit, 1e-8},
-    {"pcg_paper_x0", 1, 1, 0, 0, 0, 1, 1, 1, maxit, 1e-5},
+  struct { const char* name; int alg, norm, rr, restarts, elim, sum, use_x0, hist, it; double tol, gap; } runs[] = {
+    {"pipecg", 2, 0, 0, 8, 0, 0, 0, 1, maxit, 1e-8, 1e-6},
+    {"pipecg_nogap", 2, 0, 0, 8, 0, 0, 0, 1, maxit, 1e-8, 0.0},
+    {"pipecg_gap_every", 2, 0, 0, 8, 0, 0, 0, 1, maxit, 1e-8, 1e-300},
+    {"pipecg_paper", 2, 1, 0, 8, 0, 0, 0, 0, maxit, 1e-5, 1e-6},
+    {"pipecg_rr", 2, 0, 7, 8, 0, 0, 1, 1, maxit, 1e-8, 1e-6},
+    {"pipecg_elim", 2, 0, 0, 8, 1, 0, 0, 1, maxit, 1e-8, 1e-6},
+    {"pipecg_pairwise", 2, 0, 0, 8, 0, 1, 0, 0, maxit, 1e-8, 1e-6},
+    {"pipecg_maxit", 2, 0, 0, 8, 0, 0, 0, 1, 5, 1e-8, 1e-6},
+    {"pcg", 1, 0, 0, 0, 0, 0, 0, 1, maxit, 1e-8, 0.0},
+    {"pcg_paper_x0", 1, 1, 0, 0, 0, 1, 1, 1, maxit, 1e-5, 0.0},
   };
   for (size_t k = 0; k < sizeof(runs) / sizeof(runs[0]); k++) {
     const double* x0p = runs[k].use_x0 ? x0 : NULL;
@@ -75,7 +77,7 @@ int main(void) {
     double* s1 = runs[k].hist ? st : NULL;
     if (runs[k].alg == 2)
       oracle_pipecg(n, rp, ci, v, b, x0p, x, runs[k].tol, runs[k].it, runs[k].norm, runs[k].rr, runs[k].restarts,
-                    runs[k].elim, runs[k].sum, a1, b1, r1, s1, &r);
+                    runs[k].elim, runs[k].sum, runs[k].gap, runs[k].gap > 1e-100 ? 100.0 : 1.0, a1, b1, r1, s1, &r);
     else
       oracle_pcg(n, rp, ci, v, b, x0p, x, runs[k].tol, runs[k].it, runs[k].norm, runs[k].sum, a1, b1, r1, s1, &r);
     printf("%s %d %d %d\n", runs[k].name, r.status, r.iters, r.rr_count);
@@ -86,9 +88,9 @@ int main(void) {
   const double v3[5] = {1.0, 2.0, 2.0, 1.0, 1.0};
   const double b3[3] = {1.0, -1.0, 1.0};
   double x3[3];
-  oracle_pipecg(3, rp3, ci3, v3, b3, NULL, x3, 1e-8, 100, 0, 0, 8, 0, 0, NULL, NULL, NULL, NULL, &r);
+  oracle_pipecg(3, rp3, ci3, v3, b3, NULL, x3, 1e-8, 100, 0, 0, 8, 0, 0, 1e-6, 100.0, NULL, NULL, NULL, NULL, &r);
   printf("indefinite %d %d %d\n", r.status, r.iters, r.rr_count);
-  oracle_pipecg(3, rp3, ci3, v3, b3, NULL, x3, 1e-8, 100, 0, 0, 0, 0, 0, NULL, NULL, NULL, NULL, &r);
+  oracle_pipecg(3, rp3, ci3, v3, b3, NULL, x3, 1e-8, 100, 0, 0, 0, 0, 0, 1e-6, 100.0, NULL, NULL, NULL, NULL, &r);
   printf("indefinite_norestart %d %d %d\n", r.status, r.iters, r.rr_count);
   free(rp); free(ci); free(v); free(b); free(x0); free(x); free(ah); free(bh); free(rh); free(st);
   return 0;

@@ -324,15 +324,15 @@ def _breakdown_system():
 
 
 def test_restart_on_breakdown():
-    """Without restarts Alg. 2 stops with a breakdown near its attainable accuracy while
-    Alg. 1 converges; with restarts (true residuals, reset directions, beta = 0) the
-    pipelined solve reaches the same true residual as Alg. 1."""
+    """With the measured-gap replacement off: Alg. 2 stops with a breakdown near its
+    attainable accuracy while Alg. 1 converges; with restarts (true residuals, reset
+    directions, beta = 0) the pipelined solve reaches the same true residual as Alg. 1."""
     a, b = _breakdown_system()
-    plain = oracle.pipecg(a, b, tol=1e-8, maxit=20000, max_restarts=0)
+    plain = oracle.pipecg(a, b, tol=1e-8, maxit=20000, max_restarts=0, gap_theta=0.0)
     assert plain["result"]["status"] == oracle.ERR_BREAKDOWN
     classic = oracle.pcg(a, b, tol=1e-8, maxit=20000)
     assert classic["result"]["status"] == oracle.OK
-    out = oracle.pipecg(a, b, tol=1e-8, maxit=20000)
+    out = oracle.pipecg(a, b, tol=1e-8, maxit=20000, gap_theta=0.0)
     r = out["result"]
     assert r["status"] == oracle.OK and 1 <= r["rr_count"] <= 8
     A = a.to_scipy()
@@ -340,8 +340,46 @@ def test_restart_on_breakdown():
     assert rel(out["x"], classic["x"]) < 1e-6
     # before the first breakdown the two runs are the same computation
     k = plain["result"]["iters"] - 5
-    assert np.array_equal(oracle.pipecg(a, b, tol=0.0, maxit=k, max_restarts=0)["x"],
-                          oracle.pipecg(a, b, tol=0.0, maxit=k)["x"])
+    assert np.array_equal(oracle.pipecg(a, b, tol=0.0, maxit=k, max_restarts=0, gap_theta=0.0)["x"],
+                          oracle.pipecg(a, b, tol=0.0, maxit=k, gap_theta=0.0)["x"])
+
+
+def test_gap_replacement():
+    """Measured-gap residual replacement (the accuracy criterion of the pipelined-CG
+    literature, not in the paper).  In exact arithmetic Alg. 2 and Alg. 1 are the same
+    iteration, so Alg. 1's count is the reference:
+      * on the system where Alg. 2 breaks down, replacing the residuals while their
+        deviation from b - A x is still below 1e-6 ||r|| keeps the alpha/beta recurrences
+        consistent: no breakdown even with restarts off, the true residual at the bar, and
+        Alg. 1's iteration count within 2 -- where the late replacement and the beta = 0
+        restart cost more than a hundred iterations;
+      * the count no longer depends on the order of the dot products' sums (it does, by
+        tens of iterations, without the trigger);
+      * on a well-conditioned system the deviation never reaches 1% of ||r||, so a 1e-2
+        threshold never replaces and the run is bit for bit the run without the trigger (a
+        gap formed with a wrong sign or a dropped term would reach ||r|| and replace)."""
+    a, b = _breakdown_system()
+    A = a.to_scipy()
+    classic = oracle.pcg(a, b, tol=1e-8, maxit=20000)["result"]["iters"]
+    runs = {m: oracle.pipecg(a, b, tol=1e-8, maxit=20000, max_restarts=0, sum_mode=m) for m in (0, 1)}
+    for m, out in runs.items():
+        r = out["result"]
+        assert r["status"] == oracle.OK and r["rr_count"] >= 1, (m, r)
+        assert np.linalg.norm(b - A @ out["x"]) <= 1e-8 * np.linalg.norm(b)
+        assert abs(r["iters"] - classic) <= 2, (m, r["iters"], classic)
+    assert abs(runs[0]["result"]["iters"] - runs[1]["result"]["iters"]) <= 2
+    off = [oracle.pipecg(a, b, tol=1e-8, maxit=20000, gap_theta=0.0, sum_mode=m)["result"]["iters"] for m in (0, 1)]
+    assert min(off) > classic + 100 and abs(off[0] - off[1]) > 10, (off, classic)
+    p = synth.poisson2d(64)
+    bp = p.to_scipy() @ synth.xtrue_uniform(p.n, 1)
+    loose = oracle.pipecg(p, bp, tol=1e-10, maxit=10000, gap_theta=1e-2)
+    none = oracle.pipecg(p, bp, tol=1e-10, maxit=10000, gap_theta=0.0)
+    assert loose["result"]["rr_count"] == 0 and loose["result"] == none["result"]
+    assert np.array_equal(loose["x"], none["x"])
+    # every check replaces (gap_fall 0: a check at every iteration): r is b - A x at exit
+    st = oracle.pipecg(p, bp, tol=0.0, maxit=30, gap_theta=1e-300, gap_fall=0.0, state=True)
+    assert st["result"]["rr_count"] == 30        # iterations 1..30, the last before the maxit exit
+    assert rel(st["state"]["r"], bp - p.to_scipy() @ st["state"]["x"]) < 1e-14
 
 
 # ---------------------------------------------------------------- Jacobi elimination -----

@@ -42,6 +42,8 @@ def test_oracle_clean_under_asan_ubsan(tmp_path):
     P = oracle.NORM_PAPER_U_ABS
     want = {
         "pipecg": key(oracle.pipecg(a, b, tol=1e-8, maxit=2000)),
+        "pipecg_nogap": key(oracle.pipecg(a, b, tol=1e-8, maxit=2000, gap_theta=0.0)),
+        "pipecg_gap_every": key(oracle.pipecg(a, b, tol=1e-8, maxit=2000, gap_theta=1e-300, gap_fall=1.0)),
         "pipecg_paper": key(oracle.pipecg(a, b, tol=1e-5, maxit=2000, norm=P)),
         "pipecg_rr": key(oracle.pipecg(a, b, x0=x0, tol=1e-8, maxit=2000, rr_period=7)),
         "pipecg_elim": key(oracle.pipecg(a, b, tol=1e-8, maxit=2000, jacobi_elim=True)),
