@@ -134,7 +134,22 @@ typedef struct {
                                0 = report PPCG_ERR_BREAKDOWN instead.  FP32_IR: per inner solve
                                (an inner breakdown past the restarts ends that inner solve) */
   int32_t variant;          /* ppcg_variant */
-  int32_t reserved[4];
+  double gap_theta;         /* FP64 iteration (also the FP32 forms' FP64 fallback): measured-gap
+                               residual replacement, from the accuracy criterion of the pipelined-CG
+                               literature (not in the paper).  Whenever gamma = (r, M^-1 r) has fallen
+                               by the factor gap_fall since the residuals were last measured or
+                               replaced, one extra pass measures ||(b - A x) - r||, the deviation of
+                               the recursive residual from the true one; when it exceeds
+                               gap_theta * ||r||, the residuals are replaced (r, u, w, s, q, z
+                               recomputed from x and p; alpha and beta keep their recurrences).
+                               Replacing while that deviation is small keeps the recurrences
+                               consistent: a replacement made only once the recursive residual has
+                               passed the stopping test can change r by a percent or more, after which
+                               the iteration can grow until the alpha denominator breaks down.
+                               0 = 1e-6; negative = off */
+  int32_t gap_fall;         /* the fall of gamma between two measurements; 0 = 100 (the residual
+                               norm about 10x) */
+  int32_t reserved[1];
 } ppcg_opts;
 
 /* Per-solve results.  Filled asynchronously; valid after the solve's stream is synchronised. */
@@ -282,17 +297,29 @@ ppcg_status ppcg_selftest_barrier_timeout(int32_t grid, int32_t drop_rank, int64
  * that may not allocate device memory while solving -- code whose device memory is owned by
  * a framework pool, real-time loops where cudaMalloc/cudaFree (which can synchronise the
  * whole device) are not allowed, or plug-ins whose host forbids allocation after start-up.
- * It runs Alg. 2 with the Jacobi preconditioner straight from the caller's device CSR on one
- * thread-block cluster, keeping every working vector in a statically sized device array of
- * the library (4.5 MiB on each GPU that loads the library, held until the process exits).
- * It calls no cudaMalloc, cudaFree or allocating library routine.
+ * It runs pipelined preconditioned CG with a Jacobi (diagonal) preconditioner straight from
+ * the caller's device CSR on one thread-block cluster, keeping every working vector in a
+ * statically sized device array of the library (4.5 MiB on each GPU that loads the
+ * library, held until the process exits).  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.
  *   n <= 65536 rows; larger n returns PPCG_ERR_ARG (use ppcg_create/ppcg_solve instead).
  *   row_ptr [n+1] int64, col [nnz] int32, val [nnz], b [n], x [n]: DEVICE pointers, caller-owned.
  *   x0: device initial guess or NULL for zero; may alias x.  Stopping test: REL_R (||r|| <=
  *   tol ||b||), maxit as in ppcg_solve; no residual replacement.
- *   info: NULL, or a host struct filled after the call waits for the solve to finish.
- * The first call on a device looks up the scratch array's device address (once per device,
- * with that device current); make that first call before capturing the stream into a graph.
+ *   The matrix is checked on the device before it is used: row pointers outside [0, nnz],
+ *   decreasing, or with row_ptr[0] != 0 or row_ptr[n] != nnz, or a column outside [0, n),
+ *   end the solve with status PPCG_ERR_ARG (nothing is gathered through them); a missing or
+ *   non-positive diagonal entry with PPCG_ERR_NOT_SPD.
+ *   Return value: argument and launch errors only (PPCG_OK once the solve is enqueued).  The
+ *   solve's own status -- OK, NOT_CONVERGED, BREAKDOWN, NONFINITE, NOT_SPD, or ERR_ARG for a
+ *   malformed matrix -- is reported only through info: with info non-NULL the call waits for
+ *   the solve (it synchronises `stream`) and fills it; with info NULL it only enqueues the
+ *   work and the status is not available.
+ * Set-up: the first call on a device (any call, including one with n = 0) looks up the
+ * scratch array's device address and loads the library's kernel on that device, with that
+ * device current; under lazy module loading this is where the array itself is allocated.
+ * Make one call with n = 0 at initialisation, before any stream capture: later calls on
+ * that device then allocate nothing.
  * All calls on a device share the scratch array: calls whose GPU work overlaps (other streams
  * or host threads) race on it, so order them.  Each call rewrites the scratch it reads, so
  * earlier calls' contents never affect a result.

@@ -52,7 +52,8 @@ class Opts(ctypes.Structure):
                 ("max_outer", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64),
                 ("cluster_max_rows", ctypes.c_int32), ("epoch_iters", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("gap_theta", ctypes.c_double), ("gap_fall", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class Info(ctypes.Structure):

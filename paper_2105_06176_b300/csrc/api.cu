@@ -374,6 +374,8 @@ void ppcg_opts_default(ppcg_opts* o) {
   o->cluster_max_rows = 16384;
   o->epoch_iters = 256;
   o->max_restarts = 8;
+  o->gap_theta = 1e-6;
+  o->gap_fall = 100;
 }
 
 const char* ppcg_last_error(void) { return g_err; }
@@ -570,6 +572,8 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   d.max_restarts = h->opts.max_restarts < 0 ? 0 : h->opts.max_restarts;
   d.variant = h->opts.variant;
   d.inner_tol = h->opts.inner_tol;
+  d.gap_theta = h->opts.gap_theta == 0.0 ? 1e-6 : h->opts.gap_theta > 0.0 ? h->opts.gap_theta : 0.0;
+  d.gap_fall = h->opts.gap_fall > 0 ? (double)h->opts.gap_fall : 100.0;
   d.onchip_slots = (int32_t)std::min<int64_t>(h->onchip_nc == 16 ? h->sell.onchip_slots16 : h->sell.onchip_slots,
                                                INT32_MAX);
   d.box_g = h->box_g;

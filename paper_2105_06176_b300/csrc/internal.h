@@ -58,13 +58,14 @@ enum Pass : int32_t {
                //          q32 = M^-1 s32 ; partials (t,t) (b,b)
   P_URR2,      // FP32_RU: w32 = A u32 ; z32 = A q32 ; partials
   P_UFLUSH,    // FP32_RU: x += d32 ; d32 = 0
+  P_GAP,       // partials ||(b - A x) - r||^2, ||r||^2 (measured-gap replacement test)
 };
 
 // Control states (see control() in solver.cu).
 enum State : int32_t {
   // FP64 iteration (also the FP32 modes' fallback): every state below S_O_START
   S_START = 0, S_AFTER_SETUP1, S_AFTER_SETUP2, S_TOP, S_AFTER_ITER, S_AFTER_TRUE, S_AFTER_RR1,
-  S_AFTER_RR2, S_FINAL, S_AFTER_FINAL, S_DONE, S_AFTER_NORM,
+  S_AFTER_RR2, S_FINAL, S_AFTER_FINAL, S_DONE, S_AFTER_NORM, S_AFTER_GAP,
   // FP32_IR
   S_O_START, S_O_AFTER_ORES, S_O_AFTER_ZERO, S_O_AFTER_OINIT, S_I_AFTER_SETUP2, S_I_TOP,
   S_I_AFTER_ITER, S_I_AFTER_RR1, S_I_AFTER_RR2, S_O_AFTER_OUPD, S_O_AFTER_UNDO,
@@ -86,6 +87,7 @@ struct Ctl {
   double gamma, gamma_prev, delta, alpha, alpha_prev, beta, norm;
   double inv_gamma, inv_alpha;  // 1 / gamma and 1 / alpha of the last scalars step
   double bnorm, rn, rn_prev, res_true, inner_norm0, inner_target, rr_norm_prev;
+  double gamma_ref;             // gamma when the residuals were last measured or replaced
   unsigned long long t_start, t_end;
   double red[4];                           // reduced partials of the last pass
 };
@@ -97,6 +99,7 @@ struct SysDesc {
   int32_t max_restarts, budget;   // budget: iterations this launch may advance (0 = launch's)
   int32_t variant, onchip_slots;  // ppcg_variant; on-chip path: matrix slots of the fullest CTA
   double tol, inner_tol;
+  double gap_theta, gap_fall;   // measured-gap replacement (gap_theta 0: off)
   double dmin, dmax;     // extreme diagonal entries (bounds of ||r||^2 / gamma)
   // Matrix-free box stencil (box_g > 0): A = box_cd I + box_co (adjacency of the
   // (2 box_r + 1)^3 box on a box_g^3 grid, truncated at the boundary); box_t holds the

@@ -657,6 +657,34 @@ __device__ __forceinline__ void pass_true(const SysDesc& S, const Lanes& L, Dots
   }
 }
 
+// P_GAP (FP64): partials ||(b - A x) - r||^2 and ||r||^2, x and r in slots XS and RS of an
+// NS-slot FP64 block: the measured deviation of the recursive residual from the true one.
+template <int NS, int XS, int RS>
+__device__ __forceinline__ void pass_gap(const SysDesc& S, const Lanes& L, Dots<double>& d) {
+  const DevMatrix& A = S.A;
+  const Blk<double, NS> v{S.v64};
+  const GatherSlot<double, NS> gx{S.v64 + XS * kChunk};
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
+    const bool in = row < A.n;
+    double ax = 0.0, bi = 0.0, ri = 0.0;
+    if (in) {
+      const double* pc = v.chunk(c, L.lane);
+      bi = __ldg(S.b + row);
+      ri = ldcs(pc + RS * kChunk);
+      ax = __ldg(A.diag + row) * ldcg(pc + XS * kChunk);
+    }
+    ax = row_dot<double, true>(A.col, A.val, gx, A.diag, base, len, ax);
+    if (in) {
+      const double g = (bi - ax) - ri;
+      d.add(0, g, g);
+      d.add(1, ri, ri);
+    }
+  }
+}
+
 // P_RR1: residual replacement, first half: r = rhs - A x ; u = M^-1 r ; s = A p ; q = M^-1 s.
 // (At iteration 0 p is zero, so s = q = 0.)
 template <typename T, int NS>
@@ -871,6 +899,34 @@ __device__ __forceinline__ void spass_true(const SysDesc& S, const Lanes& L, Dot
     if (in) {
       const double t = fma(sg, bi, -ax);
       d.add(0, di * t, t);
+    }
+  }
+}
+
+// P_GAP (scaled): ||(b - A x) - r||^2 = sum d ((sig b - A~ x~) - r~)^2 and ||r||^2 = sum d r~^2.
+__device__ __forceinline__ void spass_gap(const SysDesc& S, const Lanes& L, Dots<double>& d) {
+  const DevMatrix& A = S.A;
+  const Blk<double, kNSS> v{S.v64};
+  const GatherSlot<double, kNSS> gx{S.v64 + VS_X * kChunk};
+  FOR_CHUNKS(A, L) {
+    int64_t base; int len;
+    chunk_slots(A, c, L.lane, base, len);
+    const int32_t row = c * kChunk + L.lane;
+    const bool in = row < A.n;
+    double* pc = v.chunk(c, L.lane);
+    double ax = 0.0, bi = 0.0, sg = 0.0, di = 0.0, ri = 0.0;
+    if (in) {
+      bi = __ldg(S.b + row);
+      sg = ldcs(pc + VS_SIG * kChunk);
+      di = ldcs(pc + VS_D * kChunk);
+      ri = ldcs(pc + VS_R * kChunk);
+      ax = ldcg(pc + VS_X * kChunk);
+    }
+    ax = row_dot<double, false>(A.col, A.val, gx, nullptr, base, len, ax);
+    if (in) {
+      const double g = fma(sg, bi, -ax) - ri;
+      d.add(0, di * g, g);
+      d.add(1, di * ri, ri);
     }
   }
 }
@@ -1298,6 +1354,7 @@ __device__ __forceinline__ bool control_fast(Ctl& c, const SysDesc& S, int iter_
   };
   if (iter >= iter_end) return false;
   if (S.rr_period > 0 && iter % S.rr_period == 0 && c.last_rr_iter != iter) return false;
+  if (S.gap_theta > 0.0 && gamma > 0.0 && gamma * S.gap_fall <= c.gamma_ref) return false;
   if (!rr_valid && may(1.001)) return false;
   if (paper ? (norm <= tol) : (norm <= tol * bnorm)) return false;
   if (iter >= S.maxit) return false;
@@ -1341,7 +1398,7 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
         }
         c.pass = P_SETUP2; c.state = S_AFTER_SETUP2; return;
       case S_AFTER_SETUP2:
-        take_dots(c); c.rr_valid = 1; c.state = S_TOP; break;
+        take_dots(c); c.rr_valid = 1; c.gamma_ref = c.gamma; c.state = S_TOP; break;
       case S_AFTER_ITER:
         c.gamma_prev = c.gamma; c.alpha_prev = c.alpha; c.iter++; c.restart = 0;
         take_dots(c);
@@ -1351,13 +1408,18 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
       case S_AFTER_NORM:
         c.norm = sqrt(c.red[2]); c.rr_valid = 1; c.state = c.norm_return; break;
       case S_AFTER_RR2:
-        take_dots(c); c.rr_valid = 1; c.rr_count++; c.last_rr_iter = c.iter;
+        take_dots(c); c.rr_valid = 1; c.rr_count++; c.last_rr_iter = c.iter; c.gamma_ref = c.gamma;
         if (passed(c, S)) { c.status = PPCG_OK; c.state = S_FINAL; break; }
         c.state = S_TOP; break;
       case S_TOP: {
         if (c.iter >= iter_end) { c.pass = P_NONE; c.exit_now = 1; return; }
         if (S.rr_period > 0 && c.iter > 0 && c.iter % S.rr_period == 0 && c.last_rr_iter != c.iter) {
           c.pass = P_RR1; c.state = S_AFTER_RR1; return;
+        }
+        // gamma has fallen by gap_fall since the residuals were last measured or replaced:
+        // measure how far the recursive residual has drifted from b - A x
+        if (S.gap_theta > 0.0 && c.iter > 0 && c.gamma > 0.0 && c.gamma * S.gap_fall <= c.gamma_ref) {
+          c.pass = P_GAP; c.state = S_AFTER_GAP; return;
         }
         // ||r||^2 lies in [dmin, dmax] * gamma ((u,u) in gamma * [1/dmax, 1/dmin]); when the
         // last pass skipped the norm and the bound allows convergence, compute it exactly.
@@ -1383,6 +1445,10 @@ __device__ void control(Ctl& c, const SysDesc& S, int iter_end) {
         c.want_rr = may_pass(c, S, 64.0) ? 1 : 0;
         c.pass = P_ITER; c.state = S_AFTER_ITER; return;
       }
+      case S_AFTER_GAP:
+        c.gamma_ref = c.gamma;
+        if (sqrt(c.red[0]) > S.gap_theta * sqrt(c.red[1])) { c.pass = P_RR1; c.state = S_AFTER_RR1; return; }
+        c.state = S_TOP; break;
       case S_AFTER_TRUE:
         c.res_true = sqrt(c.red[0]);
         if (c.res_true <= S.tol * c.bnorm) { c.status = PPCG_OK; c.state = S_DONE; c.pass = P_NONE; return; }
@@ -1684,7 +1750,7 @@ __device__ __forceinline__ void box_sources(const Ctl& C, const SysDesc& S, int&
     case P_SETUP1: if (!(S.x_zero != 0 && !C.fallback)) slot_a = V_X; break;
     case P_SETUP2: slot_a = V_R; break;
     case P_ITER: slot_a = (C.iter & 1) ? V_WB : V_WA; break;
-    case P_TRUE: slot_a = V_X; break;
+    case P_TRUE: case P_GAP: slot_a = V_X; break;
     case P_RR1: slot_a = V_X; if (!(C.iter == 0 || C.restart)) slot_b = V_P; break;
     case P_RR2: slot_a = V_R; slot_b = V_S; break;
     default: break;
@@ -1700,6 +1766,7 @@ __device__ bool box_pass(const SysDesc& S, const Ctl& C, const Lanes& L, Dots<do
   switch (C.pass) {
     case P_SETUP1:
     case P_TRUE:
+    case P_GAP:
     case P_RR1: {
       const bool x_zero = C.pass == P_SETUP1 && S.x_zero != 0 && !C.fallback;
       const bool rr = C.pass == P_RR1, p_zero = rr && (C.iter == 0 || C.restart);
@@ -1717,6 +1784,12 @@ __device__ bool box_pass(const SysDesc& S, const Ctl& C, const Lanes& L, Dots<do
         }
         const double ri = bi - ax;
         if (C.pass == P_TRUE) { d.add(0, ri, ri); continue; }
+        if (C.pass == P_GAP) {
+          const double rr_i = ldcs(pc + V_R * kChunk), gi = ri - rr_i;
+          d.add(0, gi, gi);
+          d.add(1, rr_i, rr_i);
+          continue;
+        }
         const double id = ldcs(pc + V_INVD * kChunk);
         stcs(pc + V_R * kChunk, ri);
         stcs(pc + V_U * kChunk, id * ri);
@@ -1901,6 +1974,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
           break;
         case P_NORM: spass_norm(S, L, d, paper); break;
         case P_TRUE: spass_true(S, L, d); break;
+        case P_GAP: spass_gap(S, L, d); break;
         case P_RR1: spass_rr1(S, L, C.iter == 0 || C.restart); partials = false; break;
         case P_RR2: spass_rr2(S, L, d, C.iter, paper); break;
         case P_ZERO_X: pass_zero_x<kNSS, VS_X>(S, L); partials = false; break;
@@ -1908,7 +1982,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
       }
       if (partials) write_block_partials<kPacked>(d.get(0), d.get(1), d.get(2), slot, sh.sm);
     } else if (BOX && !fp32 && (pass == P_SETUP1 || pass == P_SETUP2 || pass == P_ITER ||
-                                          pass == P_TRUE || pass == P_RR1 || pass == P_RR2)) {
+                                          pass == P_TRUE || pass == P_GAP || pass == P_RR1 || pass == P_RR2)) {
       int sa, sb;
       box_sources(C, S, sa, sb);
       if (sa >= 0) {
@@ -1938,6 +2012,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
           }
           break;
         case P_TRUE: pass_true<kNS64, V_X>(S, L, d); break;
+        case P_GAP: pass_gap<kNS64, V_X, V_R>(S, L, d); break;
         case P_NORM: pass_norm(S.A, V, L, d, paper); break;
         case P_RR1: pass_rr1(S.A, V, L, C.iter == 0 || C.restart); partials = false; break;
         case P_RR2: pass_rr2(S.A, V, L, d, C.iter, paper); break;
@@ -2168,9 +2243,10 @@ __device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dot
   switch (C.pass) {
     case P_SETUP1:
     case P_TRUE:
+    case P_GAP:
     case P_RR1: {
       // r = b - A x (SCALE); setup1: u = M^-1 r, partials (b,b) (r,r); true: partial (r,r) only;
-      // rr1: u = M^-1 r, s = A p, q = M^-1 s.
+      // gap: partials ((b - A x) - r)^2, r^2; rr1: u = M^-1 r, s = A p, q = M^-1 s.
       const bool x_zero = C.pass == P_SETUP1 && S.x_zero != 0 && !C.fallback;
       const bool rr = C.pass == P_RR1, p_zero = rr && (C.iter == 0 || C.restart);
       const GatherDS gx{O.tile_addr, V_X, (uint32_t)O.lg}, gp{O.tile_addr, V_P, (uint32_t)O.lg};
@@ -2193,6 +2269,12 @@ __device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dot
         if (in) {
           const double ri = bi - ax;
           if (C.pass == P_TRUE) { d.add(0, ri, ri); continue; }
+          if (C.pass == P_GAP) {
+            const double rr_i = t[V_R * kChunk], gi = ri - rr_i;
+            d.add(0, gi, gi);
+            d.add(1, rr_i, rr_i);
+            continue;
+          }
           const double id = t[V_INVD * kChunk];
           t[V_R * kChunk] = ri;
           t[V_U * kChunk] = id * ri;

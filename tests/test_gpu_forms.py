@@ -34,7 +34,13 @@ def dev(a):
 
 
 def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    """Relative difference of a from b: the larger of the norm-wise ||a - b||_2 / ||b||_2 and
+    the element-wise ||a - b||_inf / ||b||_inf, so that one wrong entry cannot hide in the
+    norm of a long vector."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    d = a - b
+    return float(max(np.linalg.norm(d) / np.linalg.norm(b), np.max(np.abs(d)) / np.max(np.abs(b))))
 
 
 def rgg(npts, seed):
