@@ -31,6 +31,7 @@ constexpr int kNaVectors = 9;                      // r u wa wb z q s p invd
 constexpr int64_t kPartOff = kNaVectors * kNoAllocMaxRows;
 constexpr int64_t kResultOff = kPartOff + 2 * kNaCluster * 4;
 constexpr int64_t kScratchDoubles = kResultOff + 16;
+constexpr int kBadArg = 1, kBadDiag = 2;           // validation flags of the first phase
 
 // 4.5 MiB per device.
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
@@ -98,7 +99,7 @@ __device__ __forceinline__ double na_row(const int64_t* rp, const int32_t* col, 
 // every CTA from the same partials, a cluster barrier between phases, and the final true
 // residual.
 __global__ void __cluster_dims__(kNaCluster, 1, 1) __launch_bounds__(kNaThreads)
-k_solve_noalloc(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+k_solve_noalloc(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                 const double* __restrict__ val, const double* __restrict__ b, const double* x0,
                 double* x, double tol, int32_t maxit) {
   __shared__ double sm[3 * 32];
@@ -123,21 +124,38 @@ k_solve_noalloc(int64_t n, const int64_t* __restrict__ rp, const int32_t* __rest
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
 
-  // Jacobi diagonal and x0 (x may alias x0).
+  // Validation of the caller's CSR, the Jacobi diagonal and x0 (x may alias x0).  A row's
+  // columns are read only once its pointers are known to lie in [0, nnz], and no phase
+  // below gathers anything unless every row passed: a malformed matrix ends the call with
+  // PPCG_ERR_ARG before any vector is indexed by a column, and a missing or non-positive
+  // diagonal entry with PPCG_ERR_NOT_SPD.
   for (int64_t i = t0; i < n; i += T) {
+    const int64_t a = rp[i], e = rp[i + 1];
+    int f = 0;
+    if (a < 0 || e < a || e > nnz || (i == 0 && a != 0) || (i == n - 1 && e != nnz)) f |= kBadArg;
     double d = 0.0;
     bool found = false;
-    for (int64_t k = rp[i]; k < rp[i + 1]; k++)
-      if (col[k] == i) { d += val[k]; found = true; }
-    if (!found || !(d > 0.0)) bad = 1;
-    invd[i] = found && d > 0.0 ? 1.0 / d : 0.0;
+    if (!(f & kBadArg)) {
+      for (int64_t k = a; k < e; k++) {
+        const int32_t c = col[k];
+        if (c < 0 || c >= n) f |= kBadArg;
+        else if (c == i) { d += val[k]; found = true; }
+      }
+    }
+    if (!found || !(d > 0.0)) f |= kBadDiag;
+    invd[i] = f == 0 ? 1.0 / d : 0.0;
     x[i] = x0 ? x0[i] : 0.0;
+    if (f) atomicOr(&bad, f);
   }
   na_cluster_sync();
-  // Every CTA must agree on the diagonal check: share the flags through the partials.
+  // Every CTA must agree on the checks: share the flags through the partials.
   {
     double* slot = part + (parity * kNaCluster + rank) * 4;
-    if (threadIdx.x == 0) { slot[0] = bad ? 1.0 : 0.0; slot[1] = 0.0; slot[2] = 0.0; }
+    if (threadIdx.x == 0) {
+      slot[0] = (bad & kBadArg) ? 1.0 : 0.0;
+      slot[1] = (bad & kBadDiag) ? 1.0 : 0.0;
+      slot[2] = 0.0;
+    }
     na_cluster_sync();
     na_reduce(part + parity * kNaCluster * 4, red);
     parity ^= 1;
@@ -146,7 +164,8 @@ k_solve_noalloc(int64_t n, const int64_t* __restrict__ rp, const int32_t* __rest
   int it = 0;
   double bnorm = 0.0, gamma = 0.0, delta = 0.0, norm = 0.0, gamma_prev = 0.0, alpha_prev = 0.0;
   bool done = false;
-  if (red[0] != 0.0) { status = PPCG_ERR_NOT_SPD; done = true; }
+  if (red[0] != 0.0) { status = PPCG_ERR_ARG; done = true; }
+  else if (red[1] != 0.0) { status = PPCG_ERR_NOT_SPD; done = true; }
 
   if (!done) {
     // setup, first half: r0 = b - A x0; u0 = M^-1 r0; partial (b, b)
@@ -237,7 +256,7 @@ k_solve_noalloc(int64_t n, const int64_t* __restrict__ rp, const int32_t* __rest
   }
   // final true residual ||b - A x||
   double res_true = 0.0;
-  if (status != PPCG_ERR_NOT_SPD) {
+  if (status != PPCG_ERR_NOT_SPD && status != PPCG_ERR_ARG) {
     double a0 = 0.0;
     for (int64_t i = t0; i < n; i += T) {
       double t = b[i] - na_row(rp, col, val, x, i);
@@ -262,6 +281,36 @@ k_solve_noalloc(int64_t n, const int64_t* __restrict__ rp, const int32_t* __rest
 std::mutex g_setup_mu;
 void* g_scratch_addr[64] = {nullptr};
 
+// Once per device, with that device current: look up the scratch array's device address
+// and make the driver load this file's kernel.  With lazy module loading (the CUDA
+// default) the module -- the scratch array among its globals -- is brought onto the
+// device by the first use of one of its symbols, which allocates; doing both lookups here
+// keeps every later call free of that work.
+ppcg_status noalloc_setup(void** scratch) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    ppcg::set_error("ppcg_solve_noalloc: no current CUDA device");
+    return PPCG_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  if (!g_scratch_addr[dev]) {
+    void* addr = nullptr;
+    e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+    if (e == cudaSuccess) {
+      cudaFuncAttributes fa;
+      e = cudaFuncGetAttributes(&fa, k_solve_noalloc);
+    }
+    if (e != cudaSuccess) {
+      ppcg::set_error("ppcg_solve_noalloc: device set-up failed: %s", cudaGetErrorString(e));
+      return PPCG_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = addr;
+  }
+  *scratch = g_scratch_addr[dev];
+  return PPCG_OK;
+}
+
 }  // namespace
 
 extern "C" ppcg_status ppcg_solve_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
@@ -277,32 +326,15 @@ extern "C" ppcg_status ppcg_solve_noalloc(int64_t n, int64_t nnz, const int64_t*
     set_error("ppcg_solve_noalloc: bad arguments");
     return PPCG_ERR_ARG;
   }
+  void* scratch = nullptr;
+  const ppcg_status st = noalloc_setup(&scratch);   // also on n = 0: the set-up call
+  if (st != PPCG_OK) return st;
   if (n == 0) {
     if (info) { memset(info, 0, sizeof(*info)); info->status = PPCG_OK; }
     return PPCG_OK;
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) {
-    set_error("ppcg_solve_noalloc: no current CUDA device");
-    return PPCG_ERR_CUDA;
-  }
-  void* scratch = nullptr;
-  {
-    // Once per device, with that device current: the device address of the scratch array.
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-      e = cudaGetSymbolAddress(&g_scratch_addr[dev], g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        g_scratch_addr[dev] = nullptr;
-        set_error("ppcg_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-        return PPCG_ERR_CUDA;
-      }
-    }
-    scratch = g_scratch_addr[dev];
-  }
-  k_solve_noalloc<<<kNaCluster, kNaThreads, 0, stream>>>(n, row_ptr, col, val, b, x0, x, tol, maxit);
-  e = cudaGetLastError();
+  k_solve_noalloc<<<kNaCluster, kNaThreads, 0, stream>>>(n, nnz, row_ptr, col, val, b, x0, x, tol, maxit);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error("ppcg_solve_noalloc: launch failed: %s", cudaGetErrorString(e));
     return PPCG_ERR_CUDA;
