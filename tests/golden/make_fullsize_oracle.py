@@ -7,7 +7,7 @@ Every value comes from ``oracle/`` alone; the inputs come from the seeded genera
 loops and keeps the dot products sequential, so its iterates are bitwise those of the plain
 build (tested in ``tests/test_oracle_pins.py``).
 
-Records:
+Records (the oracle's defaults, measured-gap residual replacement included):
   * 3-D 7-point log-normal diffusion 256^3 (seed 1, b ~ U[-1, 1] seed 1), rel tol 1e-8:
     iterations, exit status and true relative residual; and the fixed k for the GPU's x_k
     comparison: the largest k of (20, 10, 5) at which the oracle's x_k with sequential and
@@ -17,9 +17,12 @@ Records:
     tol 1e-8 and 1e-10: iterations; and the fixed k chosen the same way.
   * The 1024-system ragged batch (batch_mix(1024, 11)), rel tol 1e-8: iterations and
     residual replacements per system.
+Every iteration count is stored twice: with the oracle's sequential dot products (the
+definition) and with pairwise ones ("_pairwise").  The two bound how far rounding order alone
+moves the count; the GPU tests hold the GPU's count within that envelope widened by 2.
 
-Run from the repository root:  python tests/golden/make_fullsize_oracle.py   (about ten
-minutes on eight cores).
+Run from the repository root:  python tests/golden/make_fullsize_oracle.py   (about half
+an hour on eight cores).
 """
 import json
 import multiprocessing as mp
@@ -41,8 +44,9 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fullsize_oracle.
 def _batch_one(spec):
     a, b = synth.build_spec(tuple(spec))
     r = oracle.pipecg(a, b, tol=1e-8, maxit=20000)["result"]
-    return {"n": a.n, "iters": r["iters"], "status": r["status"], "rr_count": r["rr_count"],
-            "rel_res_true": r["res_true"] / r["bnorm"]}
+    p = oracle.pipecg(a, b, tol=1e-8, maxit=20000, sum_mode=1)["result"]
+    return {"n": a.n, "iters": r["iters"], "iters_pairwise": p["iters"], "status": r["status"],
+            "rr_count": r["rr_count"], "rel_res_true": r["res_true"] / r["bnorm"]}
 
 
 def calibrated_k(a, b):
@@ -62,9 +66,10 @@ def main():
     a = synth.varcoeff3d(256, 1)
     b = synth.rhs_uniform(a.n, 1)
     r = oracle.pipecg(a, b, tol=1e-8, maxit=20000, openmp=True)["result"]
+    rp = oracle.pipecg(a, b, tol=1e-8, maxit=20000, sum_mode=1, openmp=True)["result"]
     k, d = calibrated_k(a, b)
     out["varcoeff3d_256"] = {"grid": 256, "matrix_seed": 1, "rhs_seed": 1, "tol": 1e-8,
-                             "iters": r["iters"], "status": r["status"],
+                             "iters": r["iters"], "iters_pairwise": rp["iters"], "status": r["status"],
                              "rel_res_true": r["res_true"] / r["bnorm"],
                              "fixed_k": k, "fixed_k_rel_diff_seq_vs_pairwise": d}
     print("varcoeff3d_256", out["varcoeff3d_256"], f"{time.time() - t0:.0f} s", flush=True)
@@ -77,7 +82,9 @@ def main():
     rec["fixed_k"], rec["fixed_k_rel_diff_seq_vs_pairwise"] = calibrated_k(a, b)
     for tol in (1e-8, 1e-10):
         r = oracle.pipecg(a, b, tol=tol, maxit=20000, openmp=True)["result"]
+        rp = oracle.pipecg(a, b, tol=tol, maxit=20000, sum_mode=1, openmp=True)["result"]
         rec[f"iters_{tol:.0e}"] = r["iters"]
+        rec[f"iters_pairwise_{tol:.0e}"] = rp["iters"]
         rec[f"status_{tol:.0e}"] = r["status"]
         rec[f"rel_res_true_{tol:.0e}"] = r["res_true"] / r["bnorm"]
     out["rgg_4M"] = rec

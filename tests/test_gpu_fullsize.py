@@ -45,11 +45,24 @@ def dev(a):
 
 
 def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    """Relative difference of a from b: the larger of the norm-wise ||a - b||_2 / ||b||_2 and
+    the element-wise ||a - b||_inf / ||b||_inf, so that one wrong entry cannot hide in the
+    norm of a long vector."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    d = a - b
+    return float(max(np.linalg.norm(d) / np.linalg.norm(b), np.max(np.abs(d)) / np.max(np.abs(b))))
 
 
 def true_rel_res(a, b, x):
     return float(np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b))
+
+
+def in_envelope(iters, seq, pairwise):
+    """The count the oracle fixes: its sequential-sum count and its pairwise-sum count bound
+    how far rounding order alone moves it; the GPU's count must lie in that range widened
+    by 2 iterations."""
+    return min(seq, pairwise) - 2 <= iters <= max(seq, pairwise) + 2
 
 
 # --------------------------------------------------------- 3-D diffusion, 256^3 (main line) --
@@ -91,7 +104,7 @@ def test_varcoeff256_full_solve(vc256, precision):
     t = true_rel_res(a, b, x)
     assert t <= 1e-8 and abs(t - info.rel_res_true) <= 1e-3 * t
     if precision == 0:
-        assert abs(info.iters - g["iters"]) <= 2, (info.iters, g["iters"])
+        assert in_envelope(info.iters, g["iters"], g["iters_pairwise"]), (info.iters, g["iters"], g["iters_pairwise"])
 
 
 # ------------------------------------------------------------- RGG Laplacian, 4M points --
@@ -133,7 +146,8 @@ def test_rgg4m_full_solves(rgg4m):
         s.close()
         x = x.cpu().numpy()
         assert info.status == m.OK, info
-        assert abs(info.iters - g[f"iters_{key}"]) <= 2, (tol, info.iters, g[f"iters_{key}"])
+        assert in_envelope(info.iters, g[f"iters_{key}"], g[f"iters_pairwise_{key}"]), \
+            (tol, info.iters, g[f"iters_{key}"], g[f"iters_pairwise_{key}"])
         assert true_rel_res(a, b, x) <= tol
         sols[key] = x
     for precision in (m.FP32_RU, m.FP32_IR):
@@ -152,9 +166,13 @@ def test_rgg4m_full_solves(rgg4m):
 
 def test_batch1024_against_oracle_and_solo():
     """The benchmark's batch (1024 systems, 39.1M rows) in one batched launch: every system
-    OK with its residual at the bar, within +-2 iterations of the oracle where no residual
-    replacement ran (measured: 901 of 1024 systems, every one with the oracle's exact
-    count), and a sample of the systems bitwise equal to their solo solves."""
+    OK with its residual at the bar and its iteration count inside the oracle's envelope
+    (its sequential- and pairwise-sum counts, widened by 2), and a sample of the systems
+    bitwise equal to their solo solves.  The measured-gap residual replacement, on in the
+    library and the oracle alike, is what makes a 2-iteration envelope hold: without it,
+    122 of these 2-D log-normal systems replaced their residuals only after the recursive
+    one had passed the stopping test, the iteration then drifted into a breakdown, and the
+    restart that followed cost a rounding-dependent 0-30% more iterations."""
     m = pp()
     gold = GOLD["batch_1024"]
     specs = synth.batch_mix(gold["count"], gold["seed"])
@@ -168,19 +186,8 @@ def test_batch1024_against_oracle_and_solo():
         assert a.n == ref["n"] and ref["status"] == oracle.OK
         assert inf.status == m.OK, (k, inf)
         assert inf.rel_res_true <= 1e-8, (k, inf.rel_res_true)
-        # +-2 iterations.  A solve that reached the attainable accuracy of the pipelined
-        # recurrences -- its recursive residual passed while the true one did not, so a
-        # residual replacement ran on either side -- has a stopping iteration that rounding
-        # decides (the oracle's own sequential and pairwise dot products move it by up to
-        # ~50 iterations on these systems): there the bar is the true residual above, and
-        # the count only has to stay within 1.5x either way of the oracle's.
-        replaced = ref["rr_count"] > 0 or inf.rr_count > 0
-        if replaced:
-            ok = ref["iters"] / 1.5 <= inf.iters <= 1.5 * ref["iters"]
-        else:
-            ok = abs(inf.iters - ref["iters"]) <= 2
-        if not ok:
-            off.append((k, a.n, inf.iters, ref["iters"], inf.rr_count, ref["rr_count"]))
+        if not in_envelope(inf.iters, ref["iters"], ref["iters_pairwise"]):
+            off.append((k, a.n, inf.iters, ref["iters"], ref["iters_pairwise"], inf.rr_count, ref["rr_count"]))
     assert not off, off[:10]
     for k in range(0, len(systems), 61):
         a, b = systems[k]
