@@ -240,6 +240,40 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* handles, const do
                              const double* const* x0, double* const* x, const double* tol,
                              const int32_t* maxit, cudaStream_t stream, ppcg_info* infos);
 
+/* The execution plan ppcg_create chose for a handle (fixed for the handle's lifetime). */
+typedef enum {
+  PPCG_COLS_SELL = 0,      /* SELL-C-sigma, 4-byte column per slot */
+  PPCG_COLS_DICT = 1,      /* SELL-C-sigma; the iteration pass reads a one-byte index per slot into the
+                              matrix's few distinct col - row offsets */
+  PPCG_COLS_PATTERN = 2,   /* offset pattern: every row's off-diagonal columns are an ascending subset of
+                              row + pat[0..pattern_k); pattern_k slots per row (zeros where a neighbour is
+                              absent), and every pass forms the columns instead of reading them */
+  PPCG_COLS_MATRIX_FREE = 3  /* the constant-coefficient box stencil of PPCG_FMT_BOX: no matrix is read */
+} ppcg_columns;
+typedef struct {
+  int32_t path;             /* ppcg_path taken (never AUTO) */
+  int32_t columns;          /* ppcg_columns of the kernel running the iteration (the pattern and the
+                               dictionary have grid-path kernels; a pattern matrix is also a valid SELL
+                               matrix, whose stored columns the cluster and on-chip kernels read) */
+  int32_t sigma;            /* SELL sorting window (1 = rows in CSR order) */
+  int32_t pattern_k;        /* offsets in the pattern (0: none) */
+  int32_t dict_size;        /* offsets in the column dictionary (0: none) */
+  int32_t ctas;             /* CTAs of one solve's launch (grid path), or of its cluster */
+  int64_t slots;            /* SELL slots stored, padding included */
+  double padding;           /* padded slots / off-diagonal nonzeros */
+  double convert_seconds;   /* CSR -> SELL conversion on the device (the paper keeps CSR, Sec. V-A, to avoid
+                               this cost; it is paid once per handle here) */
+  double create_seconds;    /* the whole ppcg_create: staging, validation, conversion, detection, workspace */
+  double bytes_per_iter;    /* algorithmic bytes of one iteration, as in ppcg_info */
+} ppcg_plan;
+
+/*
+ * Report the plan of a handle (host only, no CUDA call).  Returns PPCG_OK, or PPCG_ERR_ARG
+ * for a NULL handle or plan.  The paper has no counterpart: it describes the conversion
+ * cost that its CSR choice avoids (Sec. V-A); this is where the library states its own.
+ */
+ppcg_status ppcg_plan_info(ppcg_handle handle, ppcg_plan* plan);
+
 /* Destroy a handle (synchronises its last stream first).  NULL is ignored. */
 void ppcg_destroy(ppcg_handle handle);
 

@@ -27,6 +27,7 @@ FMT_AUTO, FMT_CSR, FMT_SELL, FMT_BOX = 0, 1, 2, 3
 NORM_REL_R, NORM_PAPER_U_ABS = 0, 1
 PATH_AUTO, PATH_GRID, PATH_CLUSTER, PATH_ONCHIP = 0, 1, 2, 3
 VARIANT_ALG2, VARIANT_JACOBI_SCALED = 0, 1
+COLS_SELL, COLS_DICT, COLS_PATTERN, COLS_MATRIX_FREE = 0, 1, 2, 3
 
 _NAMES = {OK: "OK", PENDING: "PENDING", ERR_ARG: "ERR_ARG", ERR_NOT_SPD: "ERR_NOT_SPD",
           ERR_BREAKDOWN: "ERR_BREAKDOWN", ERR_NOT_CONVERGED: "ERR_NOT_CONVERGED",
@@ -37,7 +38,7 @@ _NAMES = {OK: "OK", PENDING: "PENDING", ERR_ARG: "ERR_ARG", ERR_NOT_SPD: "ERR_NO
 EXPORTED_SYMBOLS = (
     "ppcg_opts_default", "ppcg_create", "ppcg_solve", "ppcg_last_info", "ppcg_batch_solve", "ppcg_destroy",
     "ppcg_server_create", "ppcg_submit", "ppcg_poll", "ppcg_server_stats", "ppcg_server_destroy",
-    "ppcg_last_error", "ppcg_selftest_barrier_timeout", "ppcg_solve_noalloc",
+    "ppcg_last_error", "ppcg_selftest_barrier_timeout", "ppcg_solve_noalloc", "ppcg_plan_info",
 )
 
 
@@ -54,6 +55,16 @@ class Opts(ctypes.Structure):
                 ("max_restarts", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("gap_theta", ctypes.c_double), ("gap_fall", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 1)]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("columns", ctypes.c_int32), ("sigma", ctypes.c_int32),
+                ("pattern_k", ctypes.c_int32), ("dict_size", ctypes.c_int32), ("ctas", ctypes.c_int32),
+                ("slots", ctypes.c_int64), ("padding", ctypes.c_double), ("convert_seconds", ctypes.c_double),
+                ("create_seconds", ctypes.c_double), ("bytes_per_iter", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Info(ctypes.Structure):
@@ -117,6 +128,8 @@ def lib(build_if_missing=True):
     L.ppcg_solve_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, P, ctypes.c_double,
                                      ctypes.c_int32, P, ctypes.POINTER(Info)]
     L.ppcg_solve_noalloc.restype = ctypes.c_int
+    L.ppcg_plan_info.argtypes = [P, ctypes.POINTER(Plan)]
+    L.ppcg_plan_info.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -212,6 +225,15 @@ class Solver:
                 info = self.last_info()
         self._last_info = info
         return x, info
+
+    def plan(self):
+        """ppcg_plan_info: the plan ppcg_create chose (path, column mode, sigma, padding,
+        conversion and create times)."""
+        p = Plan()
+        st = lib().ppcg_plan_info(self.handle, ctypes.byref(p))
+        if st != OK:
+            raise PPCGError(st, "ppcg_plan_info")
+        return p
 
     def last_info(self):
         """ppcg_last_info: the record of this handle's latest solve (after a stream sync)."""

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <chrono>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -384,6 +385,7 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
                         const int32_t* col, const double* val, const ppcg_opts* opts,
                         cudaStream_t stream) {
   NvtxRange nvtx_range("ppcg_create");
+  const auto t_create = std::chrono::steady_clock::now();
   g_err[0] = 0;
   if (!handle) { set_error("ppcg_create: handle is NULL"); return PPCG_ERR_ARG; }
   *handle = nullptr;
@@ -503,8 +505,9 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
     if (const char* e = getenv("PPCG_GRID_SHAPE")) k = atoi(e);
     if (k < 0 || k >= nshapes) k = 0;
     h->shape = box ? grid_box_shape_first() + k : k;
-    // the column dictionary, where the matrix has one, on the default shape
-    if (!box && k == 0 && h->A.cidx) h->shape = grid_dict_shape();
+    // the offset pattern or the column dictionary, where the matrix has one, on the default shape
+    if (!box && k == 0 && h->A.pat_k > 0) h->shape = grid_pat_shape();
+    else if (!box && k == 0 && h->A.cidx) h->shape = grid_dict_shape();
     // One CTA per SM at most for small systems: enough warps for one 32-row chunk each,
     // so the grid barrier spans only the CTAs that have rows to work on.
     const int full = grid_blocks_for_device(h->device, h->shape);
@@ -588,7 +591,32 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   d.ctl = h->ctl;
   d.bar = h->bar;
   d.err = h->err;
+  h->create_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_create).count();
   *handle = h;
+  return PPCG_OK;
+}
+
+ppcg_status ppcg_plan_info(ppcg_handle h, ppcg_plan* out) {
+  g_err[0] = 0;
+  if (!h || !out) { set_error("ppcg_plan_info: NULL handle or plan"); return PPCG_ERR_ARG; }
+  memset(out, 0, sizeof(*out));
+  out->path = h->path;
+  // the column source of the kernel that runs the iteration (a pattern matrix is also a
+  // valid SELL matrix: the cluster and on-chip kernels read its stored columns)
+  const bool grid = h->path == PPCG_PATH_GRID;
+  out->columns = h->box_g > 0                                ? PPCG_COLS_MATRIX_FREE
+                 : grid && h->shape == grid_pat_shape()  ? PPCG_COLS_PATTERN
+                 : grid && h->shape == grid_dict_shape() ? PPCG_COLS_DICT
+                                                         : PPCG_COLS_SELL;
+  out->sigma = h->sell.sigma;
+  out->pattern_k = h->A.pat_k;
+  out->dict_size = h->sell.col_dict;
+  out->ctas = h->path == PPCG_PATH_GRID ? h->grid : (h->path == PPCG_PATH_ONCHIP ? h->onchip_nc : h->grid);
+  out->slots = h->sell.nslots;
+  out->padding = h->sell.padding;
+  out->convert_seconds = h->sell.seconds;
+  out->create_seconds = h->create_seconds;
+  out->bytes_per_iter = h->bytes_per_iter;
   return PPCG_OK;
 }
 

@@ -111,7 +111,7 @@ constexpr int kDictTable = 1024;
 constexpr int32_t kDictEmpty = INT32_MIN;
 
 __device__ __forceinline__ int dict_probe(int32_t* table, int32_t key, bool insert, int32_t* count,
-                                          int32_t* overflow) {
+                                          int32_t* overflow, int32_t limit = kColDict) {
   const uint32_t h = (uint32_t)key * 2654435761u;
   for (int probe = 0; probe < kDictTable; probe++) {
     const int pos = (int)((h + (uint32_t)probe) & (kDictTable - 1));
@@ -121,7 +121,7 @@ __device__ __forceinline__ int dict_probe(int32_t* table, int32_t key, bool inse
     if (!insert || *(volatile int32_t*)overflow) return -1;
     const int32_t prev = atomicCAS(table + pos, kDictEmpty, key);
     if (prev == kDictEmpty) {
-      if (atomicAdd(count, 1) >= kColDict) atomicExch(overflow, 1);
+      if (atomicAdd(count, 1) >= limit) atomicExch(overflow, 1);
       return pos;
     }
     if (prev == key) return pos;
@@ -151,6 +151,62 @@ __global__ void k_dict(int64_t nchunks, const int64_t* __restrict__ cptr, const 
       const int pos = dict_probe(table, key, false, count, overflow);
       cidx[slot] = pos < 0 ? 0 : pos2idx[pos];
     }
+  }
+}
+
+// Offset pattern, first pass.  One thread per row: insert the row's off-diagonal offsets
+// col - row into the table (overflow beyond kPatMax distinct offsets), and flag a row whose
+// off-diagonal offsets do not ascend in CSR order (then the pattern order would not be the
+// row's summation order).
+__global__ void k_pat_offsets(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              int32_t* table, int32_t* count, int32_t* overflow, int32_t* unsorted) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t prev = INT64_MIN;
+  for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+    const int64_t c = col[k];
+    if (c == i) continue;
+    const int64_t off = c - i;
+    if (off <= prev) atomicExch(unsorted, 1);
+    prev = off;
+    if (dict_probe(table, (int32_t)off, true, count, overflow, kPatMax) < 0) return;
+  }
+}
+
+// Offset pattern, fill.  One thread per (chunk, lane): the row's pat_k slots, slot p holding
+// the row's entry at column i + pat[p] (scaled as in k_fill), or a zero with column i where
+// the row has no such entry (rows past n: zeros with column n - 1).  Rows are in CSR order.
+__global__ void k_fill_pat(int64_t n, int64_t nchunks, const int64_t* __restrict__ rp,
+                           const int32_t* __restrict__ col, const double* __restrict__ val,
+                           const double* __restrict__ diag, const int32_t* __restrict__ pat, int K,
+                           int32_t* __restrict__ scol, double* __restrict__ sval, float* __restrict__ sval32,
+                           int sym) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = t / kChunk;
+  const int lane = (int)(t % kChunk);
+  if (c >= nchunks) return;
+  const int64_t i = c * kChunk + lane;
+  const int64_t base = c * (int64_t)K * kChunk + lane;
+  const int32_t self = (int32_t)(i < n ? i : n - 1);
+  for (int p = 0; p < K; p++) {
+    scol[base + (int64_t)p * kChunk] = self;
+    sval[base + (int64_t)p * kChunk] = 0.0;
+    if (sval32) sval32[base + (int64_t)p * kChunk] = 0.0f;
+  }
+  if (i >= n) return;
+  int p = 0;
+  for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+    const int32_t oc = col[k];
+    if (oc == i) continue;
+    const int64_t off = (int64_t)oc - i;
+    while (p < K && pat[p] != off) p++;            // offsets ascend in the row and in pat
+    if (p == K) return;                            // cannot happen after k_pat_offsets
+    const double v = sym ? val[k] / (sqrt(diag[i]) * sqrt(diag[oc])) : val[k] / diag[oc];
+    const int64_t slot = base + (int64_t)p * kChunk;
+    scol[slot] = oc;
+    sval[slot] = v;
+    if (sval32) sval32[slot] = (float)v;
+    p++;
   }
 }
 
@@ -375,6 +431,40 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   if (flags & F_ARG) { free_tmp(); set_error("ppcg_create: malformed CSR (row_ptr or column index)"); return PPCG_ERR_ARG; }
   if (flags & F_NOT_SPD) { free_tmp(); set_error("ppcg_create: missing or non-positive diagonal entry"); return PPCG_ERR_NOT_SPD; }
 
+  // Offset pattern (see DevMatrix): stencil-like matrices whose rows all draw their
+  // off-diagonal columns, in ascending order, from at most kPatMax offsets.  Taken when its
+  // slots (pat_k per row, zeros where a row lacks a neighbour) are at most 1.25x the slots
+  // of sigma = 1 SELL: a pattern slot carries no column bytes, a SELL slot four.
+  std::vector<int32_t> pat;
+  const char* no_dict = getenv("PPCG_COL_DICT");                    // diagnostic knobs: "0" = off
+  const char* no_pat = getenv("PPCG_COL_PAT");
+  if ((sigma_req <= 1) && !(no_dict && no_dict[0] == '0') && !(no_pat && no_pat[0] == '0') && nnz > n) {
+    int32_t* d_tab = nullptr;   // table, count, overflow, unsorted
+    if ((e = dalloc(&d_tab, kDictTable + 3, tmp, st)) != cudaSuccess) {
+      free_tmp();
+      set_error("ppcg_create: device allocation failed: %s", cudaGetErrorString(e));
+      return PPCG_ERR_OOM;
+    }
+    std::vector<int32_t> h(kDictTable + 3, kDictEmpty);
+    h[kDictTable] = h[kDictTable + 1] = h[kDictTable + 2] = 0;
+    cudaMemcpyAsync(d_tab, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    k_pat_offsets<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(n, d_rp, d_col, d_tab, d_tab + kDictTable,
+                                                                d_tab + kDictTable + 1, d_tab + kDictTable + 2);
+    cudaMemcpyAsync(h.data(), d_tab, h.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
+      free_tmp();
+      set_error("ppcg_create: %s", cudaGetErrorString(e));
+      return PPCG_ERR_CUDA;
+    }
+    if (h[kDictTable + 1] == 0 && h[kDictTable + 2] == 0 && h[kDictTable] >= 1 && h[kDictTable] <= kPatMax) {
+      for (int k = 0; k < kDictTable; k++)
+        if (h[k] != kDictEmpty) pat.push_back(h[k]);
+      std::sort(pat.begin(), pat.end());
+      const int64_t pat_slots = (int64_t)pat.size() * kChunk * ((n + kChunk - 1) / kChunk);
+      if ((double)pat_slots > 1.25 * (double)sell_slots(len, 1, nullptr, nullptr)) pat.clear();
+    }
+  }
+
   // sigma autotune.  Sorting rows by length within a window of sigma > C rows cuts the
   // padding, but it also scatters the rows of a chunk over the window, so the 32 lanes of
   // a warp gather from unrelated rows and every gathered value costs its own L2 sector.
@@ -384,7 +474,9 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   // 17% (FP64) and 27% (FP32) faster than the padding-optimal sigma = 2048 despite 57%
   // padding).  The smallest-cost window wins.
   int64_t sigma = sigma_req;
-  if (sigma_req <= 0) {
+  if (!pat.empty()) {
+    sigma = 1;
+  } else if (sigma_req <= 0) {
     const int64_t cands[] = {1, 256, 2048};
     const double penalty[] = {0.0, 0.65 * 16.0, 16.0};
     const double slot_bytes = want_fp32 ? 8.0 : 12.0;
@@ -398,7 +490,16 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   }
   std::vector<int32_t> perm;
   std::vector<int64_t> cptr;
-  int64_t nslots = sell_slots(len, sigma, &perm, &cptr);
+  const int K = (int)pat.size();
+  int64_t nslots = 0;
+  if (K > 0) {                     // pat_k slots in every row
+    const int64_t nch = (n + kChunk - 1) / kChunk;
+    cptr.resize(nch + 1);
+    for (int64_t c = 0; c <= nch; c++) cptr[c] = c * K * kChunk;
+    nslots = nch * K * kChunk;
+  } else {
+    nslots = sell_slots(len, sigma, &perm, &cptr);
+  }
   const int64_t nchunks = (int64_t)cptr.size() - 1;
 
   int64_t* d_cptr = nullptr; int32_t* d_scol = nullptr; double* d_sval = nullptr; float* d_sval32 = nullptr;
@@ -435,9 +536,22 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   } else {
     cudaMemcpyAsync(d_cptr, cptr.data(), (nchunks + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
     int64_t threads = nchunks * kChunk;
-    k_fill<<<(unsigned)((threads + tb - 1) / tb), tb, 0, st>>>(n, nchunks, d_rp, d_col, d_val, d_diag0,
-                                                               d_len, nullptr, nullptr, d_cptr, d_scol,
-                                                               d_sval, d_sval32, sym_scale ? 1 : 0);
+    if (K > 0) {
+      int32_t* d_pat = nullptr;
+      if ((e = dalloc(&d_pat, K, tmp, st)) != cudaSuccess) {
+        free_tmp();
+        set_error("ppcg_create: device allocation failed: %s", cudaGetErrorString(e));
+        return PPCG_ERR_OOM;
+      }
+      cudaMemcpyAsync(d_pat, pat.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+      k_fill_pat<<<(unsigned)((threads + tb - 1) / tb), tb, 0, st>>>(n, nchunks, d_rp, d_col, d_val, d_diag0,
+                                                                     d_pat, K, d_scol, d_sval, d_sval32,
+                                                                     sym_scale ? 1 : 0);
+    } else {
+      k_fill<<<(unsigned)((threads + tb - 1) / tb), tb, 0, st>>>(n, nchunks, d_rp, d_col, d_val, d_diag0,
+                                                                 d_len, nullptr, nullptr, d_cptr, d_scol,
+                                                                 d_sval, d_sval32, sym_scale ? 1 : 0);
+    }
     k_permute_diag<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(n, nullptr, d_diag0, d_invd0, d_sdiag,
                                                                  d_sinvd, d_sdiag32, d_sinvd32);
     e = cudaStreamSynchronize(st);
@@ -455,6 +569,8 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   A->col = d_scol;
   A->cidx = nullptr;
   A->coff = nullptr;
+  A->pat_k = K;
+  for (int k = 0; k < kPatMax; k++) A->pat[k] = k < K ? pat[k] : 0;
   A->val = d_sval;
   A->val32 = d_sval32;
   A->invd = d_sinvd;
@@ -472,7 +588,8 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
     for (int r = 0; r < 8; r++) per8[r] = per[r] + per[r + 8];   // c % 8 == r  <=>  c % 16 in {r, r + 8}
     out->onchip_slots = *std::max_element(per8, per8 + 8);
   }
-  out->col_dict = build_col_dict(A, allocs, st);
+  out->pattern_k = K;
+  out->col_dict = K > 0 ? 0 : build_col_dict(A, allocs, st);   // the pattern needs no dictionary
   if (out->col_dict < 0) {
     set_error("ppcg_create: out of device memory for the column dictionary");
     return PPCG_ERR_OOM;

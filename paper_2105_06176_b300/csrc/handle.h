@@ -76,6 +76,7 @@ struct ppcg_ctx {
   ppcg::Stage* stage = nullptr;   // pinned, from the library's stage pool
   cudaStream_t stream = nullptr;  // stream of the handle's latest work (creation or solve)
   int32_t last_solve = 0;   // ppcg_last_info source: 0 none, 1 the stage, 2 a trivial OK (n = 0)
+  double create_seconds = 0.0;   // wall time of ppcg_create (ppcg_plan_info)
 };
 
 

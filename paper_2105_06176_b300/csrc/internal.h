@@ -31,6 +31,13 @@ struct DevMatrix {
   // byte per slot instead of four.
   const uint8_t* cidx;   // [nslots]
   const int32_t* coff;   // [kColDict]
+  // Offset pattern (pat_k > 0): every row's off-diagonal columns are an ascending subset of
+  // row + pat[0..pat_k), pat ascending, and the SELL arrays hold exactly pat_k slots per row
+  // (slot p of row i is the entry at column i + pat[p], or a zero with column i when the
+  // row has no such entry).  Chunk c's slots start at c * pat_k * 32, and kernels built for
+  // the pattern form each column as i + pat[p] (clamped into [0, n)) instead of reading it.
+  int32_t pat_k;
+  int32_t pat[16];
   const double* val;     // [nslots] a_ij / a_jj
   const float* val32;    // [nslots] same rounded to FP32 (FP32 modes only)
   const double* invd;    // [n] 1 / a_ii
@@ -138,6 +145,7 @@ int grid_shape_count();        // SELL/CSR plans: shapes [0, grid_shape_count())
 int grid_box_shape_first();    // matrix-free box plans: shapes first + [0, count)
 int grid_box_shape_count();
 int grid_dict_shape();         // the default SELL shape reading the column dictionary
+int grid_pat_shape();          // the default SELL shape forming columns from the offset pattern
 int grid_threads(int shape);
 int grid_blocks_for_device(int device, int shape);
 int max_active_clusters(int device);
@@ -156,7 +164,9 @@ struct SellBuild {
   int64_t onchip_slots = 0;        // SELL slots of the fullest CTA when chunk c goes to CTA c % 8
   int64_t onchip_slots16 = 0;      // the same for clusters of 16 CTAs
   int32_t col_dict = 0;            // distinct col - row offsets in the dictionary (0: none)
+  int32_t pattern_k = 0;           // offsets of the offset pattern (0: none; see DevMatrix)
 };
+constexpr int kPatMax = 16;      // largest offset pattern
 ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, const int32_t* d_col,
                                 const double* d_val, int32_t sigma_req, bool want_fp32, bool sym_scale,
                                 cudaStream_t st, std::vector<void*>& allocs, SellBuild* out,

@@ -175,6 +175,22 @@ __device__ __forceinline__ float ld_stream(const float* p) {
   return v;
 }
 
+// p, made to depend on v for the compiler: loads through the result cannot be scheduled
+// before v is computed.  The iteration passes load a row's own vector entries this way,
+// after the row's product: hoisted above the gathers (as the compiler otherwise does, to
+// overlap their latency) they no longer fit the 64-register budget of two 512-thread CTAs
+// per SM together with the product's operands and were spilled to local memory and
+// reloaded (about 40 local-memory instructions per 32-row chunk and iteration).  Other
+// warps hide the latency instead: 256^3 FP64 iteration 630 -> 597 us.
+template <typename T> __device__ __forceinline__ T* after(T* p, double v) {
+  asm volatile("" : "+l"(p) : "d"(v));
+  return p;
+}
+template <typename T> __device__ __forceinline__ T* after(T* p, float v) {
+  asm volatile("" : "+l"(p) : "f"(v));
+  return p;
+}
+
 // ---------------------------------------------------------- bulk-copy staging (TMA) --
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -238,17 +254,44 @@ template <typename T, int NS> struct GatherSlot {
   }
 };
 
-// Column of SELL slot s: the 4-byte column array, or the column dictionary (DevMatrix):
-// row + coff[cidx[s]], one byte read per slot.
-__device__ __forceinline__ int32_t slot_col(const int32_t* __restrict__ col, int64_t s) { return ld_stream(col + s); }
+// Column of SELL slot s (the row's j-th slot): the 4-byte column array; or the column
+// dictionary (DevMatrix), row + coff[cidx[s]], one byte read per slot; or the offset
+// pattern, row + pat[j] clamped into [0, n) -- nothing read per slot (a slot whose
+// neighbour is off the grid holds a zero, so the clamped gather adds nothing).
+__device__ __forceinline__ int32_t slot_col(const int32_t* __restrict__ col, int64_t s, int) {
+  return ld_stream(col + s);
+}
 struct ColDict {
   const uint8_t* __restrict__ idx;
   const int32_t* __restrict__ off;
   int32_t row;
 };
-__device__ __forceinline__ int32_t slot_col(const ColDict& d, int64_t s) {
+__device__ __forceinline__ int32_t slot_col(const ColDict& d, int64_t s, int) {
   return d.row + __ldg(d.off + __ldcs(d.idx + s));
 }
+struct ColPat {
+  const int32_t* off;    // DevMatrix::pat (shared memory: the block's copy of the descriptor)
+  int32_t row, last;
+};
+__device__ __forceinline__ int32_t slot_col(const ColPat& p, int64_t, int j) {
+  return min(max(p.row + p.off[j], 0), p.last);
+}
+
+// Column modes of a kernel: the 4-byte columns everywhere; the dictionary in the iteration
+// pass (4-byte columns elsewhere); the offset pattern in every pass.
+enum : int { kColA = 0, kColDict = 1, kColPat = 2 };
+template <int CM> struct Cols;
+template <> struct Cols<kColA> {
+  static __device__ __forceinline__ const int32_t* make(const DevMatrix& A, int32_t) { return A.col; }
+};
+template <> struct Cols<kColDict> {
+  static __device__ __forceinline__ ColDict make(const DevMatrix& A, int32_t row) { return {A.cidx, A.coff, row}; }
+};
+template <> struct Cols<kColPat> {
+  static __device__ __forceinline__ ColPat make(const DevMatrix& A, int32_t row) {
+    return {A.pat, row, (int32_t)A.n - 1};
+  }
+};
 
 // acc + sum_j val[slot_j] * x(col[slot_j]) (* dsc[col] when SCALE) over the row's
 // off-diagonal slots base + j*32, j < len, in CSR order; acc enters holding the diagonal
@@ -262,7 +305,7 @@ __device__ __forceinline__ T row_dot(const CS& col, const T* __restrict__ val, c
     T a[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk);
+      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk, j + k);
       a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
 #pragma unroll
@@ -277,7 +320,7 @@ __device__ __forceinline__ T row_dot(const CS& col, const T* __restrict__ val, c
 #pragma unroll
   for (int k = 0; k < 7; k++) {
     if (j + k < len) {
-      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk);
+      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk, j + k);
       a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
   }
@@ -305,7 +348,7 @@ __device__ __forceinline__ void row_dot2(const CS& col, const T* __restrict__ va
     T a[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk);
+      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk, j + k);
       a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
 #pragma unroll
@@ -321,7 +364,7 @@ __device__ __forceinline__ void row_dot2(const CS& col, const T* __restrict__ va
 #pragma unroll
   for (int k = 0; k < 7; k++) {
     if (j + k < len) {
-      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk);
+      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk, j + k);
       a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
   }
@@ -345,10 +388,16 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 template <typename T, int NS>
 __device__ __forceinline__ void prefetch_chunk(const int64_t* __restrict__ cptr, const int32_t* __restrict__ col,
                                                const uint8_t* __restrict__ cidx, const T* __restrict__ val,
-                                               const T* blk, int32_t c, int lane) {
+                                               const T* blk, int32_t c, int lane, int pat_k = 0) {
   constexpr int kTileBytes = NS * kChunk * (int)sizeof(T);
   const char* tile = reinterpret_cast<const char*>(blk + (int64_t)c * NS * kChunk);
   for (int off = lane * 128; off < kTileBytes; off += 32 * 128) prefetch_l2(tile + off);
+  if (pat_k > 0) {                 // offset pattern: values only, no column bytes
+    const char* pv = reinterpret_cast<const char*>(val + (int64_t)c * pat_k * kChunk);
+    const int nv = pat_k * kChunk * (int)sizeof(T);
+    for (int off = lane * 128; off < nv; off += 32 * 128) prefetch_l2(pv + off);
+    return;
+  }
   const int64_t b0 = __ldg(cptr + c), b1 = __ldg(cptr + c + 1);
   // Long rows (over 16 slots) keep enough loads in flight on their own, and prefetching
   // their matrix slots a chunk ahead from every warp would overflow L2 (the 125-point box:
@@ -379,10 +428,16 @@ struct Lanes {
 
 #define FOR_CHUNKS(A, L) for (int32_t c = (L).gw; c < (int32_t)(A).nchunks; c += (L).W)
 
+template <int CM = kColA>
 __device__ __forceinline__ void chunk_slots(const DevMatrix& A, int32_t c, int lane, int64_t& base, int& len) {
-  const int64_t b0 = __ldg(A.cptr + c);
-  len = (int)((__ldg(A.cptr + c + 1) - b0) / kChunk);
-  base = b0 + lane;
+  if constexpr (CM == kColPat) {   // pat_k slots in every chunk: no chunk pointers to read
+    len = A.pat_k;
+    base = (int64_t)c * A.pat_k * kChunk + lane;
+  } else {
+    const int64_t b0 = __ldg(A.cptr + c);
+    len = (int)((__ldg(A.cptr + c + 1) - b0) / kChunk);
+    base = b0 + lane;
+  }
 }
 
 // Per-precision matrix/vector view used by the generic passes.
@@ -403,13 +458,14 @@ __device__ __forceinline__ View<float, kNS32> view32(const SysDesc& S) {
 // -------------------------------------------------------------------------- passes --
 
 // P_SETUP1 (FP64), Alg. 2 setup: r0 = b - A x0 ; u0 = M^-1 r0.  Partials (b,b), (r,r).
+template <int CM>
 __device__ __forceinline__ void pass_setup1(const SysDesc& S, const Lanes& L, Dots<double>& d, bool x_zero) {
   const DevMatrix& A = S.A;
   const Blk<double, kNS64> v{S.v64};
   const GatherSlot<double, kNS64> gx{S.v64 + V_X * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     double* pc = v.chunk(c, L.lane);
@@ -419,7 +475,7 @@ __device__ __forceinline__ void pass_setup1(const SysDesc& S, const Lanes& L, Do
       id = ldcs(pc + V_INVD * kChunk);
       if (!x_zero) ax = __ldg(A.diag + row) * ldcg(pc + V_X * kChunk);
     }
-    if (!x_zero) ax = row_dot<double, true>(A.col, A.val, gx, A.diag, base, len, ax);
+    if (!x_zero) ax = row_dot<double, true>(Cols<CM>::make(A, row), A.val, gx, A.diag, base, len, ax);
     if (in) {
       const double ri = bi - ax;
       stcs(pc + V_R * kChunk, ri);
@@ -431,19 +487,19 @@ __device__ __forceinline__ void pass_setup1(const SysDesc& S, const Lanes& L, Do
 }
 
 // P_SETUP2, Alg. 2 setup: w0 = A u0 (= Ahat r0) ; partials (r,u), (w,u), norm.
-template <typename T, int NS>
+template <typename T, int NS, int CM>
 __device__ __forceinline__ void pass_setup2(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, Dots<T>& d,
                                             bool paper_norm) {
   const GatherSlot<T, NS> gr{V.v.b + V_R * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     T* pc = V.v.chunk(c, L.lane);
     T ri = T(0), ui = T(0);
     if (in) { ri = ldcg(pc + V_R * kChunk); ui = ldcs(pc + V_U * kChunk); }
-    const T wi = row_dot<T, false>(A.col, V.val, gr, nullptr, base, len, ri);
+    const T wi = row_dot<T, false>(Cols<CM>::make(A, row), V.val, gr, nullptr, base, len, ri);
     if (in) {
       stcs(pc + V_WA * kChunk, wi);
       d.add(0, ri, ui);
@@ -454,14 +510,13 @@ __device__ __forceinline__ void pass_setup2(const DevMatrix& A, const View<T, NS
 }
 
 // P_ITER: one full iteration of Alg. 2 for the group's rows (see the file comment).  The
-// row's own vector entries are loaded before the gather so their latency overlaps it.
-template <typename T, int NS, bool FIRST, bool DICT = false>
+// row's own vector entries other than w are loaded after the product (see after()).
+template <typename T, int NS, bool FIRST, int CM = kColA>
 __device__ __forceinline__ void pass_iter(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, Dots<T>& d,
                                           T alpha, T beta, int k, bool paper_norm, bool with_rr = true) {
   const int wcs = (k & 1) ? V_WB : V_WA;
   const int wns = (k & 1) ? V_WA : V_WB;
   const GatherSlot<T, NS> gw{V.v.b + wcs * kChunk};
-  const int32_t* __restrict__ col = A.col;
   const T* __restrict__ val = V.val;
   const int32_t n = (int32_t)A.n;
   FOR_CHUNKS(A, L) {
@@ -469,31 +524,31 @@ __device__ __forceinline__ void pass_iter(const DevMatrix& A, const View<T, NS>&
     // same occupancy), 433 -> 350 us per 256^3 iteration; the FP64 pass, already near the
     // HBM and FP64-pipe limits, ran 10-20% slower with it.
     if (PPCG_PREFETCH && sizeof(T) == 4 && c + L.W < (int32_t)A.nchunks)
-      prefetch_chunk<T, NS>(A.cptr, col, DICT ? A.cidx : nullptr, val, V.v.b, c + L.W, L.lane);
+      prefetch_chunk<T, NS>(A.cptr, A.col, CM == kColDict ? A.cidx : nullptr, val, V.v.b, c + L.W, L.lane,
+                            CM == kColPat ? A.pat_k : 0);
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < n;
     T* pc = V.v.chunk(c, L.lane);
     T wi = T(0), id = T(0), ui = T(0), xi = T(0), ri = T(0);
     T zo = T(0), qo = T(0), so = T(0), po = T(0);
-    if (in) {
-      wi = ldcg(pc + wcs * kChunk);
-      id = ldcs(pc + V_INVD * kChunk);
-      ui = ldcs(pc + V_U * kChunk);
-      xi = ldcs(pc + V_X * kChunk);
-      ri = ldcs(pc + V_R * kChunk);
+    if (in) wi = ldcg(pc + wcs * kChunk);
+    // n_i = (A M^-1 w)_i = w_i + sum_{j != i} ahat_ij w_j
+    const T ni = row_dot<T, false>(Cols<CM>::make(A, row), val, gw, nullptr, base, len, wi);
+    if (in) {          // the row's own entries, after the product (see after())
+      const T* q = after(pc, ni);
+      id = ldcs(q + V_INVD * kChunk);
+      ui = ldcs(q + V_U * kChunk);
+      xi = ldcs(q + V_X * kChunk);
+      ri = ldcs(q + V_R * kChunk);
       if (!FIRST) {
-        zo = ldcs(pc + V_Z * kChunk);
-        qo = ldcs(pc + V_Q * kChunk);
-        so = ldcs(pc + V_S * kChunk);
-        po = ldcs(pc + V_P * kChunk);
+        zo = ldcs(q + V_Z * kChunk);
+        qo = ldcs(q + V_Q * kChunk);
+        so = ldcs(q + V_S * kChunk);
+        po = ldcs(q + V_P * kChunk);
       }
     }
-    // n_i = (A M^-1 w)_i = w_i + sum_{j != i} ahat_ij w_j
-    T ni;
-    if constexpr (DICT) ni = row_dot<T, false>(ColDict{A.cidx, A.coff, row}, val, gw, nullptr, base, len, wi);
-    else ni = row_dot<T, false>(col, val, gw, nullptr, base, len, wi);
     if (in) {
       const T mi = id * wi;
       const T zi = FIRST ? ni : fma(beta, zo, ni);
@@ -637,19 +692,19 @@ __device__ __forceinline__ void pass_iter_staged(const DevMatrix& A, const View<
 }
 
 // P_TRUE (FP64): partial ||b - A x||^2, x in slot XS of an NS-slot FP64 block.
-template <int NS, int XS>
+template <int NS, int XS, int CM>
 __device__ __forceinline__ void pass_true(const SysDesc& S, const Lanes& L, Dots<double>& d) {
   const DevMatrix& A = S.A;
   const Blk<double, NS> v{S.v64};
   const GatherSlot<double, NS> gx{S.v64 + XS * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     double ax = 0.0, bi = 0.0;
     if (in) { bi = __ldg(S.b + row); ax = __ldg(A.diag + row) * ldcg(v.chunk(c, L.lane) + XS * kChunk); }
-    ax = row_dot<double, true>(A.col, A.val, gx, A.diag, base, len, ax);
+    ax = row_dot<double, true>(Cols<CM>::make(A, row), A.val, gx, A.diag, base, len, ax);
     if (in) {
       const double t = bi - ax;
       d.add(0, t, t);
@@ -659,14 +714,14 @@ __device__ __forceinline__ void pass_true(const SysDesc& S, const Lanes& L, Dots
 
 // P_GAP (FP64): partials ||(b - A x) - r||^2 and ||r||^2, x and r in slots XS and RS of an
 // NS-slot FP64 block: the measured deviation of the recursive residual from the true one.
-template <int NS, int XS, int RS>
+template <int NS, int XS, int RS, int CM>
 __device__ __forceinline__ void pass_gap(const SysDesc& S, const Lanes& L, Dots<double>& d) {
   const DevMatrix& A = S.A;
   const Blk<double, NS> v{S.v64};
   const GatherSlot<double, NS> gx{S.v64 + XS * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     double ax = 0.0, bi = 0.0, ri = 0.0;
@@ -676,7 +731,7 @@ __device__ __forceinline__ void pass_gap(const SysDesc& S, const Lanes& L, Dots<
       ri = ldcs(pc + RS * kChunk);
       ax = __ldg(A.diag + row) * ldcg(pc + XS * kChunk);
     }
-    ax = row_dot<double, true>(A.col, A.val, gx, A.diag, base, len, ax);
+    ax = row_dot<double, true>(Cols<CM>::make(A, row), A.val, gx, A.diag, base, len, ax);
     if (in) {
       const double g = (bi - ax) - ri;
       d.add(0, g, g);
@@ -687,13 +742,13 @@ __device__ __forceinline__ void pass_gap(const SysDesc& S, const Lanes& L, Dots<
 
 // P_RR1: residual replacement, first half: r = rhs - A x ; u = M^-1 r ; s = A p ; q = M^-1 s.
 // (At iteration 0 p is zero, so s = q = 0.)
-template <typename T, int NS>
+template <typename T, int NS, int CM>
 __device__ __forceinline__ void pass_rr1(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, bool p_zero) {
   const GatherSlot<T, NS> gx{V.v.b + V_X * kChunk};
   const GatherSlot<T, NS> gp{V.v.b + V_P * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     T* pc = V.v.chunk(c, L.lane);
@@ -705,8 +760,8 @@ __device__ __forceinline__ void pass_rr1(const DevMatrix& A, const View<T, NS>& 
       ax = di * ldcg(pc + V_X * kChunk);
       if (!p_zero) ap = di * ldcg(pc + V_P * kChunk);
     }
-    if (p_zero) ax = row_dot<T, true>(A.col, V.val, gx, V.dsc, base, len, ax);
-    else row_dot2<T, true>(A.col, V.val, gx, gp, V.dsc, base, len, ax, ap);
+    if (p_zero) ax = row_dot<T, true>(Cols<CM>::make(A, row), V.val, gx, V.dsc, base, len, ax);
+    else row_dot2<T, true>(Cols<CM>::make(A, row), V.val, gx, gp, V.dsc, base, len, ax, ap);
     if (in) {
       const T ri = rh - ax;
       stcs(pc + V_R * kChunk, ri);
@@ -718,7 +773,7 @@ __device__ __forceinline__ void pass_rr1(const DevMatrix& A, const View<T, NS>& 
 }
 
 // P_RR2: w = A u (= Ahat r) ; z = A q (= Ahat s) ; partials (r,u), (w,u), norm.
-template <typename T, int NS>
+template <typename T, int NS, int CM>
 __device__ __forceinline__ void pass_rr2(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, Dots<T>& d,
                                          int k, bool paper_norm) {
   const int wcs = (k & 1) ? V_WB : V_WA;
@@ -726,16 +781,16 @@ __device__ __forceinline__ void pass_rr2(const DevMatrix& A, const View<T, NS>& 
   const GatherSlot<T, NS> gs{V.v.b + V_S * kChunk};
   FOR_CHUNKS(A, L) {
     if (PPCG_PREFETCH && sizeof(T) == 4 && c + L.W < (int32_t)A.nchunks)
-      prefetch_chunk<T, NS>(A.cptr, A.col, nullptr, V.val, V.v.b, c + L.W, L.lane);
+      prefetch_chunk<T, NS>(A.cptr, A.col, nullptr, V.val, V.v.b, c + L.W, L.lane, CM == kColPat ? A.pat_k : 0);
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     T* pc = V.v.chunk(c, L.lane);
     T ri = T(0), ui = T(0), si = T(0);
     if (in) { ri = ldcg(pc + V_R * kChunk); ui = ldcs(pc + V_U * kChunk); si = ldcg(pc + V_S * kChunk); }
     T wi = ri, zi = si;
-    row_dot2<T, false>(A.col, V.val, gr, gs, nullptr, base, len, wi, zi);
+    row_dot2<T, false>(Cols<CM>::make(A, row), V.val, gr, gs, nullptr, base, len, wi, zi);
     if (in) {
       stcs(pc + wcs * kChunk, wi);
       stcs(pc + V_Z * kChunk, zi);
@@ -760,13 +815,14 @@ __device__ __forceinline__ double scaled_norm_term(bool paper, double ri, double
 }
 
 // P_SETUP1: r~ = sig b - A~ x~ ; partial (b, b).
+template <int CM>
 __device__ __forceinline__ void spass_setup1(const SysDesc& S, const Lanes& L, Dots<double>& d, bool x_zero) {
   const DevMatrix& A = S.A;
   const Blk<double, kNSS> v{S.v64};
   const GatherSlot<double, kNSS> gx{S.v64 + VS_X * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     double* pc = v.chunk(c, L.lane);
@@ -776,7 +832,7 @@ __device__ __forceinline__ void spass_setup1(const SysDesc& S, const Lanes& L, D
       sg = ldcs(pc + VS_SIG * kChunk);
       if (!x_zero) ax = ldcg(pc + VS_X * kChunk);
     }
-    if (!x_zero) ax = row_dot<double, false>(A.col, A.val, gx, nullptr, base, len, ax);
+    if (!x_zero) ax = row_dot<double, false>(Cols<CM>::make(A, row), A.val, gx, nullptr, base, len, ax);
     if (in) {
       stcs(pc + VS_R * kChunk, fma(sg, bi, -ax));
       d.add(0, bi, bi);
@@ -785,13 +841,14 @@ __device__ __forceinline__ void spass_setup1(const SysDesc& S, const Lanes& L, D
 }
 
 // P_SETUP2: w~ = A~ r~ ; partials gamma = (r~, r~), delta = (w~, r~), stopping norm.
+template <int CM>
 __device__ __forceinline__ void spass_setup2(const SysDesc& S, const Lanes& L, Dots<double>& d, bool paper) {
   const DevMatrix& A = S.A;
   const Blk<double, kNSS> v{S.v64};
   const GatherSlot<double, kNSS> gr{S.v64 + VS_R * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     double* pc = v.chunk(c, L.lane);
@@ -800,7 +857,7 @@ __device__ __forceinline__ void spass_setup2(const SysDesc& S, const Lanes& L, D
       ri = ldcg(pc + VS_R * kChunk);
       if (paper) sg = ldcs(pc + VS_SIG * kChunk); else di = ldcs(pc + VS_D * kChunk);
     }
-    const double wi = row_dot<double, false>(A.col, A.val, gr, nullptr, base, len, ri);
+    const double wi = row_dot<double, false>(Cols<CM>::make(A, row), A.val, gr, nullptr, base, len, ri);
     if (in) {
       stcs(pc + VS_WA * kChunk, wi);
       d.add(0, ri, ri);
@@ -812,7 +869,7 @@ __device__ __forceinline__ void spass_setup2(const SysDesc& S, const Lanes& L, D
 
 // P_ITER (scaled): n~ = A~ w~ ; z = n + beta z ; s = w + beta s ; p = r + beta p ;
 // x += alpha p ; r -= alpha s ; w -= alpha z ; partials.
-template <bool FIRST>
+template <bool FIRST, int CM>
 __device__ __forceinline__ void spass_iter(const SysDesc& S, const Lanes& L, Dots<double>& d, double alpha,
                                            double beta, int k, bool paper, bool with_rr) {
   const DevMatrix& A = S.A;
@@ -820,28 +877,28 @@ __device__ __forceinline__ void spass_iter(const SysDesc& S, const Lanes& L, Dot
   const int wcs = (k & 1) ? VS_WB : VS_WA;
   const int wns = (k & 1) ? VS_WA : VS_WB;
   const GatherSlot<double, kNSS> gw{S.v64 + wcs * kChunk};
-  const int32_t* __restrict__ col = A.col;
   const double* __restrict__ val = A.val;
   const int32_t n = (int32_t)A.n;
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < n;
     double* pc = v.chunk(c, L.lane);
     double wi = 0.0, ri = 0.0, xi = 0.0, zo = 0.0, so = 0.0, po = 0.0, di = 0.0, sg = 0.0;
-    if (in) {
-      wi = ldcg(pc + wcs * kChunk);
-      ri = ldcs(pc + VS_R * kChunk);
-      xi = ldcs(pc + VS_X * kChunk);
-      if (with_rr) { if (paper) sg = ldcs(pc + VS_SIG * kChunk); else di = ldcs(pc + VS_D * kChunk); }
+    if (in) wi = ldcg(pc + wcs * kChunk);
+    const double ni = row_dot<double, false>(Cols<CM>::make(A, row), val, gw, nullptr, base, len, wi);
+    if (in) {          // the row's own entries, after the product (see after())
+      const double* q = after(pc, ni);
+      ri = ldcs(q + VS_R * kChunk);
+      xi = ldcs(q + VS_X * kChunk);
+      if (with_rr) { if (paper) sg = ldcs(q + VS_SIG * kChunk); else di = ldcs(q + VS_D * kChunk); }
       if (!FIRST) {
-        zo = ldcs(pc + VS_Z * kChunk);
-        so = ldcs(pc + VS_S * kChunk);
-        po = ldcs(pc + VS_P * kChunk);
+        zo = ldcs(q + VS_Z * kChunk);
+        so = ldcs(q + VS_S * kChunk);
+        po = ldcs(q + VS_P * kChunk);
       }
     }
-    const double ni = row_dot<double, false>(col, val, gw, nullptr, base, len, wi);
     if (in) {
       const double zi = FIRST ? ni : fma(beta, zo, ni);
       const double si = FIRST ? wi : fma(beta, so, wi);
@@ -878,13 +935,14 @@ __device__ __forceinline__ void spass_norm(const SysDesc& S, const Lanes& L, Dot
 }
 
 // P_TRUE (scaled): ||b - A x||^2 = sum d (sig b - A~ x~)^2.
+template <int CM>
 __device__ __forceinline__ void spass_true(const SysDesc& S, const Lanes& L, Dots<double>& d) {
   const DevMatrix& A = S.A;
   const Blk<double, kNSS> v{S.v64};
   const GatherSlot<double, kNSS> gx{S.v64 + VS_X * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     double* pc = v.chunk(c, L.lane);
@@ -895,7 +953,7 @@ __device__ __forceinline__ void spass_true(const SysDesc& S, const Lanes& L, Dot
       di = ldcs(pc + VS_D * kChunk);
       ax = ldcg(pc + VS_X * kChunk);
     }
-    ax = row_dot<double, false>(A.col, A.val, gx, nullptr, base, len, ax);
+    ax = row_dot<double, false>(Cols<CM>::make(A, row), A.val, gx, nullptr, base, len, ax);
     if (in) {
       const double t = fma(sg, bi, -ax);
       d.add(0, di * t, t);
@@ -904,13 +962,14 @@ __device__ __forceinline__ void spass_true(const SysDesc& S, const Lanes& L, Dot
 }
 
 // P_GAP (scaled): ||(b - A x) - r||^2 = sum d ((sig b - A~ x~) - r~)^2 and ||r||^2 = sum d r~^2.
+template <int CM>
 __device__ __forceinline__ void spass_gap(const SysDesc& S, const Lanes& L, Dots<double>& d) {
   const DevMatrix& A = S.A;
   const Blk<double, kNSS> v{S.v64};
   const GatherSlot<double, kNSS> gx{S.v64 + VS_X * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     double* pc = v.chunk(c, L.lane);
@@ -922,7 +981,7 @@ __device__ __forceinline__ void spass_gap(const SysDesc& S, const Lanes& L, Dots
       ri = ldcs(pc + VS_R * kChunk);
       ax = ldcg(pc + VS_X * kChunk);
     }
-    ax = row_dot<double, false>(A.col, A.val, gx, nullptr, base, len, ax);
+    ax = row_dot<double, false>(Cols<CM>::make(A, row), A.val, gx, nullptr, base, len, ax);
     if (in) {
       const double g = fma(sg, bi, -ax) - ri;
       d.add(0, di * g, g);
@@ -932,6 +991,7 @@ __device__ __forceinline__ void spass_gap(const SysDesc& S, const Lanes& L, Dots
 }
 
 // P_RR1 (scaled): r~ = sig b - A~ x~ ; s~ = A~ p~ (0 at a restart or at iteration 0).
+template <int CM>
 __device__ __forceinline__ void spass_rr1(const SysDesc& S, const Lanes& L, bool p_zero) {
   const DevMatrix& A = S.A;
   const Blk<double, kNSS> v{S.v64};
@@ -939,7 +999,7 @@ __device__ __forceinline__ void spass_rr1(const SysDesc& S, const Lanes& L, bool
   const GatherSlot<double, kNSS> gp{S.v64 + VS_P * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     double* pc = v.chunk(c, L.lane);
@@ -950,8 +1010,8 @@ __device__ __forceinline__ void spass_rr1(const SysDesc& S, const Lanes& L, bool
       ax = ldcg(pc + VS_X * kChunk);
       if (!p_zero) ap = ldcg(pc + VS_P * kChunk);
     }
-    if (p_zero) ax = row_dot<double, false>(A.col, A.val, gx, nullptr, base, len, ax);
-    else row_dot2<double, false>(A.col, A.val, gx, gp, nullptr, base, len, ax, ap);
+    if (p_zero) ax = row_dot<double, false>(Cols<CM>::make(A, row), A.val, gx, nullptr, base, len, ax);
+    else row_dot2<double, false>(Cols<CM>::make(A, row), A.val, gx, gp, nullptr, base, len, ax, ap);
     if (in) {
       stcs(pc + VS_R * kChunk, fma(sg, bi, -ax));
       stcs(pc + VS_S * kChunk, ap);
@@ -960,6 +1020,7 @@ __device__ __forceinline__ void spass_rr1(const SysDesc& S, const Lanes& L, bool
 }
 
 // P_RR2 (scaled): w~ = A~ r~ ; z~ = A~ s~ ; partials.
+template <int CM>
 __device__ __forceinline__ void spass_rr2(const SysDesc& S, const Lanes& L, Dots<double>& d, int k, bool paper) {
   const DevMatrix& A = S.A;
   const Blk<double, kNSS> v{S.v64};
@@ -968,7 +1029,7 @@ __device__ __forceinline__ void spass_rr2(const SysDesc& S, const Lanes& L, Dots
   const GatherSlot<double, kNSS> gs{S.v64 + VS_S * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     double* pc = v.chunk(c, L.lane);
@@ -979,7 +1040,7 @@ __device__ __forceinline__ void spass_rr2(const SysDesc& S, const Lanes& L, Dots
       if (paper) sg = ldcs(pc + VS_SIG * kChunk); else di = ldcs(pc + VS_D * kChunk);
     }
     double wi = ri, zi = si;
-    row_dot2<double, false>(A.col, A.val, gr, gs, nullptr, base, len, wi, zi);
+    row_dot2<double, false>(Cols<CM>::make(A, row), A.val, gr, gs, nullptr, base, len, wi, zi);
     if (in) {
       stcs(pc + wcs * kChunk, wi);
       stcs(pc + VS_Z * kChunk, zi);
@@ -1001,19 +1062,20 @@ __device__ __forceinline__ void pass_zero_x(const SysDesc& S, const Lanes& L) {
 }
 
 // P_ORES (FP32_IR outer step): r64 = b - A x in FP64 ; partials (r64,r64), (b,b).
+template <int CM>
 __device__ __forceinline__ void pass_ores(const SysDesc& S, const Lanes& L, Dots<double>& d) {
   const DevMatrix& A = S.A;
   const Blk<double, kNS64> v{S.v64};
   const GatherSlot<double, kNS64> gx{S.v64 + IR_X * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     double* pc = v.chunk(c, L.lane);
     double ax = 0.0, bi = 0.0;
     if (in) { bi = __ldg(S.b + row); ax = __ldg(A.diag + row) * ldcg(pc + IR_X * kChunk); }
-    ax = row_dot<double, true>(A.col, A.val, gx, A.diag, base, len, ax);
+    ax = row_dot<double, true>(Cols<CM>::make(A, row), A.val, gx, A.diag, base, len, ax);
     if (in) {
       const double t = bi - ax;
       stcs(pc + IR_R * kChunk, t);
@@ -1074,8 +1136,8 @@ __device__ __forceinline__ void pass_oupd(const SysDesc& S, const Lanes& L, doub
 
 // t_x += A x and (DP) t_p += A p over one row's slots in one sweep: x in FP64 against the
 // FP64 values, p in FP32 against the FP32 values.
-template <bool DP>
-__device__ __forceinline__ void row_dot_ures(const DevMatrix& A, const GatherSlot<double, kNS64>& gx,
+template <bool DP, class CS>
+__device__ __forceinline__ void row_dot_ures(const DevMatrix& A, const CS& col, const GatherSlot<double, kNS64>& gx,
                                              const GatherSlot<float, kNS32>& gp, int64_t base, int len, double& ax,
                                              float& ap) {
   int j = 0;
@@ -1085,7 +1147,7 @@ __device__ __forceinline__ void row_dot_ures(const DevMatrix& A, const GatherSlo
     float b[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-      c[k] = ld_stream(A.col + base + (int64_t)(j + k) * kChunk);
+      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk, j + k);
       a[k] = ld_stream(A.val + base + (int64_t)(j + k) * kChunk);
       if (DP) b[k] = ld_stream(A.val32 + base + (int64_t)(j + k) * kChunk);
     }
@@ -1101,7 +1163,7 @@ __device__ __forceinline__ void row_dot_ures(const DevMatrix& A, const GatherSlo
 #pragma unroll
   for (int k = 0; k < 7; k++) {
     if (j + k < len) {
-      c[k] = ld_stream(A.col + base + (int64_t)(j + k) * kChunk);
+      c[k] = slot_col(col, base + (int64_t)(j + k) * kChunk, j + k);
       a[k] = ld_stream(A.val + base + (int64_t)(j + k) * kChunk);
       if (DP) b[k] = ld_stream(A.val32 + base + (int64_t)(j + k) * kChunk);
     }
@@ -1118,6 +1180,7 @@ __device__ __forceinline__ void row_dot_ures(const DevMatrix& A, const GatherSlo
 // P_URES (d32 already folded into x).  x_zero: x = 0 (first update of a solve with x0 = 0);
 // d_zero: d32 unset, set it to 0 (first update); p_zero: p = 0 (first update or a restart),
 // so s = q = 0.
+template <int CM>
 __device__ __forceinline__ void pass_ures(const SysDesc& S, const Lanes& L, Dots<double>& d, bool x_zero,
                                           bool d_zero, bool p_zero) {
   const DevMatrix& A = S.A;
@@ -1127,7 +1190,7 @@ __device__ __forceinline__ void pass_ures(const SysDesc& S, const Lanes& L, Dots
   const GatherSlot<float, kNS32> gp{S.v32 + V_P * kChunk};
   FOR_CHUNKS(A, L) {
     int64_t base; int len;
-    chunk_slots(A, c, L.lane, base, len);
+    chunk_slots<CM>(A, c, L.lane, base, len);
     const int32_t row = c * kChunk + L.lane;
     const bool in = row < A.n;
     float* p32 = v32.chunk(c, L.lane);
@@ -1140,8 +1203,8 @@ __device__ __forceinline__ void pass_ures(const SysDesc& S, const Lanes& L, Dots
       if (!p_zero) ap = __ldg(A.diag32 + row) * ldcg(p32 + V_P * kChunk);
     }
     if (!x_zero) {
-      if (p_zero) row_dot_ures<false>(A, gx, gp, base, len, ax, ap);
-      else row_dot_ures<true>(A, gx, gp, base, len, ax, ap);
+      if (p_zero) row_dot_ures<false>(A, Cols<CM>::make(A, row), gx, gp, base, len, ax, ap);
+      else row_dot_ures<true>(A, Cols<CM>::make(A, row), gx, gp, base, len, ax, ap);
     }
     if (in) {
       const double t = bi - ax;
@@ -1925,9 +1988,11 @@ constexpr int kSmGrid = 3 * 32, kSmCluster = 3 * 32 * (kClusterThreads / 32);
 // BOX: the kernel carries the matrix-free box passes (a plan with box_g > 0 runs only on
 // such a kernel, every other plan only on the others, so the SELL kernels' register
 // allocation does not carry the box code); a mismatch ends the solve with PPCG_ERR_ARG.
-// DICT: the iteration passes read the column dictionary (a plan without one ends with
-// PPCG_ERR_ARG on such a kernel; kernels without DICT read the 4-byte columns).
-template <bool STAGED, bool BOX = false, bool DICT = false, class G, class Shared>
+// CM: the column mode -- kColA: every pass reads the 4-byte columns; kColDict: the iteration
+// passes read the column dictionary (a plan without one ends with PPCG_ERR_ARG); kColPat:
+// every SELL pass forms its columns from the offset pattern (a plan without one ends with
+// PPCG_ERR_ARG).  A pattern matrix is also a valid SELL matrix, so kColA kernels run it too.
+template <bool STAGED, bool BOX = false, int CM = kColA, class G, class Shared>
 __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsigned char* stage_mem,
                            uint64_t* stage_bars, unsigned& phases) {
   __syncthreads();   // previous system's readers of sh are done
@@ -1939,7 +2004,10 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
     for (int i = 0; i < (int)(sizeof(Ctl) / 8); i++) dst[i] = __ldcg(src + i);
     if (sh.C.t_start == 0) sh.C.t_start = globaltimer();
     sh.C.exit_now = 0;
-    if ((sh.S.box_g > 0) != BOX || (DICT && !sh.S.A.cidx)) { sh.C.status = PPCG_ERR_ARG; sh.C.state = S_DONE; }
+    if ((sh.S.box_g > 0) != BOX || (CM == kColDict && !sh.S.A.cidx) || (CM == kColPat && sh.S.A.pat_k <= 0)) {
+      sh.C.status = PPCG_ERR_ARG;
+      sh.C.state = S_DONE;
+    }
   }
   __syncthreads();
   const SysDesc& S = sh.S;
@@ -1954,6 +2022,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
   const bool paper = S.norm == PPCG_NORM_PAPER_U_ABS;
   const int P = g.size();
   constexpr bool kPacked = Shared::kPacked;
+  constexpr int CMO = CM == kColDict ? kColA : CM;   // column mode of the passes other than P_ITER
 
   for (;;) {
     if (threadIdx.x == 0) control(C, S, iter_end);
@@ -1966,17 +2035,17 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
     if (!fp32 && S.variant == PPCG_VARIANT_JACOBI_SCALED) {
       Dots<double> d;
       switch (pass) {
-        case P_SETUP1: spass_setup1(S, L, d, S.x_zero != 0); break;
-        case P_SETUP2: spass_setup2(S, L, d, paper); break;
+        case P_SETUP1: spass_setup1<CMO>(S, L, d, S.x_zero != 0); break;
+        case P_SETUP2: spass_setup2<CMO>(S, L, d, paper); break;
         case P_ITER:
-          if (C.first) spass_iter<true>(S, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
-          else spass_iter<false>(S, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
+          if (C.first) spass_iter<true, CMO>(S, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
+          else spass_iter<false, CMO>(S, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
           break;
         case P_NORM: spass_norm(S, L, d, paper); break;
-        case P_TRUE: spass_true(S, L, d); break;
-        case P_GAP: spass_gap(S, L, d); break;
-        case P_RR1: spass_rr1(S, L, C.iter == 0 || C.restart); partials = false; break;
-        case P_RR2: spass_rr2(S, L, d, C.iter, paper); break;
+        case P_TRUE: spass_true<CMO>(S, L, d); break;
+        case P_GAP: spass_gap<CMO>(S, L, d); break;
+        case P_RR1: spass_rr1<CMO>(S, L, C.iter == 0 || C.restart); partials = false; break;
+        case P_RR2: spass_rr2<CMO>(S, L, d, C.iter, paper); break;
         case P_ZERO_X: pass_zero_x<kNSS, VS_X>(S, L); partials = false; break;
         default: partials = false; break;
       }
@@ -1998,8 +2067,8 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
       Dots<double> d;
       const View<double, kNS64> V = view64(S);
       switch (pass) {
-        case P_SETUP1: pass_setup1(S, L, d, S.x_zero != 0 && !C.fallback); break;
-        case P_SETUP2: pass_setup2(S.A, V, L, d, paper); break;
+        case P_SETUP1: pass_setup1<CMO>(S, L, d, S.x_zero != 0 && !C.fallback); break;
+        case P_SETUP2: pass_setup2<double, kNS64, CMO>(S.A, V, L, d, paper); break;
         case P_ITER:
           if (STAGED) {
             unsigned char* wst = stage_mem + (threadIdx.x >> 5) * kWarpStageBytes;
@@ -2007,15 +2076,15 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
             if (C.first) pass_iter_staged<double, kNS64, true>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, wst, bars, phases, S.err);
             else pass_iter_staged<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, wst, bars, phases, S.err);
           } else {
-            if (C.first) pass_iter<double, kNS64, true, DICT>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
-            else pass_iter<double, kNS64, false, DICT>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
+            if (C.first) pass_iter<double, kNS64, true, CM>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
+            else pass_iter<double, kNS64, false, CM>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
           }
           break;
-        case P_TRUE: pass_true<kNS64, V_X>(S, L, d); break;
-        case P_GAP: pass_gap<kNS64, V_X, V_R>(S, L, d); break;
+        case P_TRUE: pass_true<kNS64, V_X, CMO>(S, L, d); break;
+        case P_GAP: pass_gap<kNS64, V_X, V_R, CMO>(S, L, d); break;
         case P_NORM: pass_norm(S.A, V, L, d, paper); break;
-        case P_RR1: pass_rr1(S.A, V, L, C.iter == 0 || C.restart); partials = false; break;
-        case P_RR2: pass_rr2(S.A, V, L, d, C.iter, paper); break;
+        case P_RR1: pass_rr1<double, kNS64, CMO>(S.A, V, L, C.iter == 0 || C.restart); partials = false; break;
+        case P_RR2: pass_rr2<double, kNS64, CMO>(S.A, V, L, d, C.iter, paper); break;
         case P_ZERO_X: pass_zero_x<kNS64, V_X>(S, L); partials = false; break;
         default: partials = false; break;
       }
@@ -2025,10 +2094,10 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
       Dots<double> d;
       switch (pass) {
         case P_URES:
-          pass_ures(S, L, d, S.x_zero != 0 && C.outer == 0, C.outer == 0, C.inner_iter == 0 || C.restart);
+          pass_ures<CMO>(S, L, d, S.x_zero != 0 && C.outer == 0, C.outer == 0, C.inner_iter == 0 || C.restart);
           break;
         case P_UFLUSH: pass_uflush(S, L); partials = false; break;
-        case P_ORES: pass_ores(S, L, d); break;
+        case P_ORES: pass_ores<CMO>(S, L, d); break;
         case P_ZERO_X: pass_zero_x<kNS64, IR_X>(S, L); partials = false; break;
         case P_OINIT: pass_oinit(S, L, 1.0 / C.rn); partials = false; break;
         case P_OUPD: pass_oupd(S, L, C.rn); partials = false; break;
@@ -2040,7 +2109,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
       Dots<float> d;
       const View<float, kNS32> V = view32(S);
       switch (pass) {
-        case P_SETUP2: pass_setup2(S.A, V, L, d, paper); break;
+        case P_SETUP2: pass_setup2<float, kNS32, CMO>(S.A, V, L, d, paper); break;
         case P_ITER:
           if (STAGED) {
             unsigned char* wst = stage_mem + (threadIdx.x >> 5) * kWarpStageBytes;
@@ -2048,13 +2117,13 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
             if (C.first) pass_iter_staged<float, kNS32, true>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper, wst, bars, phases, S.err);
             else pass_iter_staged<float, kNS32, false>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper, wst, bars, phases, S.err);
           } else {
-            if (C.first) pass_iter<float, kNS32, true, DICT>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
-            else pass_iter<float, kNS32, false, DICT>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
+            if (C.first) pass_iter<float, kNS32, true, CM>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
+            else pass_iter<float, kNS32, false, CM>(S.A, V, L, d, (float)C.alpha, (float)C.beta, C.inner_iter, paper);
           }
           break;
-        case P_RR1: pass_rr1(S.A, V, L, C.inner_iter == 0 || C.restart); partials = false; break;
-        case P_RR2: pass_rr2(S.A, V, L, d, C.inner_iter, paper); break;
-        case P_URR2: pass_rr2(S.A, V, L, d, C.inner_iter, paper); break;
+        case P_RR1: pass_rr1<float, kNS32, CMO>(S.A, V, L, C.inner_iter == 0 || C.restart); partials = false; break;
+        case P_RR2: pass_rr2<float, kNS32, CMO>(S.A, V, L, d, C.inner_iter, paper); break;
+        case P_URR2: pass_rr2<float, kNS32, CMO>(S.A, V, L, d, C.inner_iter, paper); break;
         default: partials = false; break;
       }
       if (partials) write_block_partials<kPacked>(d.get(0), d.get(1), d.get(2), slot, sh.sm);
@@ -2083,7 +2152,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
   }
 }
 
-template <int THREADS, int MINB, bool STAGED, bool BOX = false, bool DICT = false>
+template <int THREADS, int MINB, bool STAGED, bool BOX = false, int CM = kColA>
 __global__ void __launch_bounds__(THREADS, MINB) k_grid(const SysDesc* d, int budget) {
   __shared__ SharedT<kSmGrid> sh;
   __shared__ uint64_t bars[2 * (THREADS / 32)];
@@ -2098,14 +2167,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_grid(const SysDesc* d, int bu
     __syncthreads();
   }
   GridGroup g{d->bar, d->err, (long long)d->spin_limit_ns, 0u};
-  run_system<STAGED, BOX, DICT>(g, d, budget, sh, stage_mem, bars, phases);
+  run_system<STAGED, BOX, CM>(g, d, budget, sh, stage_mem, bars, phases);
 }
 
 // Launch shapes of the grid path: (threads per CTA, minimum CTAs per SM for the register
 // budget, bulk-copy staging).  Index 0 is the default (fastest measured on the 256^3
 // stencil); the others trade registers, resident warps and staging.  From kFirstBoxShape on:
 // the kernels of matrix-free box-stencil plans; last, the default shape reading the column
-// dictionary (plans whose matrix has one).
+// dictionary (plans whose matrix has one) and the default shape forming columns from the
+// offset pattern (plans whose matrix has one).
 struct GridShape {
   void (*fn)(const SysDesc*, int);
   int threads;
@@ -2118,12 +2188,14 @@ const GridShape kGridShapes[] = {
     {k_grid<384, 1, true>, 384, 12 * kWarpStageBytes},
     {k_grid<512, 2, false, true>, 512, 0}, {k_grid<256, 4, false, true>, 256, 0},
     {k_grid<1024, 1, false, true>, 1024, 0},
-    {k_grid<512, 2, false, false, true>, 512, 0},
+    {k_grid<512, 2, false, false, kColDict>, 512, 0},
+    {k_grid<512, 2, false, false, kColPat>, 512, 0},
 };
 constexpr int kNumGridShapes = (int)(sizeof(kGridShapes) / sizeof(kGridShapes[0]));
 constexpr int kFirstBoxShape = 9;
 constexpr int kDictShape = 12;   // the default shape with the column dictionary
-static_assert(kDictShape == kNumGridShapes - 1, "the dictionary kernel is the last shape");
+constexpr int kPatShape = 13;    // the default shape with the offset pattern
+static_assert(kPatShape == kNumGridShapes - 1, "the pattern kernel is the last shape");
 
 // Cluster path.  Static schedule (next == nullptr): cluster c runs list[list_ptr[c] ..
 // list_ptr[c + 1]).  Dynamic schedule: every cluster takes the next entry of list (ordered
@@ -2511,6 +2583,7 @@ int grid_shape_count() { return kFirstBoxShape; }
 int grid_box_shape_first() { return kFirstBoxShape; }
 int grid_box_shape_count() { return kDictShape - kFirstBoxShape; }
 int grid_dict_shape() { return kDictShape; }
+int grid_pat_shape() { return kPatShape; }
 int grid_threads(int shape) { return kGridShapes[shape].threads; }
 
 cudaError_t ensure_smem_attr(const void* fn, size_t bytes);

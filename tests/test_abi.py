@@ -55,6 +55,7 @@ def test_library_loads_and_binding_matches(libpath):
     assert lib.ppcg_last_info(None, ctypes.byref(info)) == pp.ERR_ARG
     lib.ppcg_last_error.restype = ctypes.c_char_p
     assert b"ppcg_last_info" in lib.ppcg_last_error()
+    assert lib.ppcg_plan_info(None, ctypes.byref(pp.Plan())) == pp.ERR_ARG
 
 
 def test_struct_layouts_match_header(tmp_path):
@@ -70,17 +71,20 @@ int main(void) {
          offsetof(ppcg_opts, spin_limit_ns), offsetof(ppcg_opts, epoch_iters), sizeof(ppcg_info));
   printf("%zu %zu\n", offsetof(ppcg_info, rel_res_recursive), offsetof(ppcg_info, bnorm));
   printf("%zu %zu\n", offsetof(ppcg_opts, gap_theta), offsetof(ppcg_opts, gap_fall));
+  printf("%zu %zu %zu\n", sizeof(ppcg_plan), offsetof(ppcg_plan, slots), offsetof(ppcg_plan, bytes_per_iter));
   return 0;
 }''')
     exe = tmp_path / "layout"
     cuda_inc = "/usr/local/cuda/include"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, str(prog), "-o", str(exe)],
                    check=True)
-    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
+    a, b, c, d = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:4]
     so, oi, osp, oe, si = map(int, a.split())
     orr, ob = map(int, b.split())
     og, of = map(int, c.split())
     assert og == pp.Opts.gap_theta.offset and of == pp.Opts.gap_fall.offset
+    sp_, osl, obp = map(int, d.split())
+    assert sp_ == ctypes.sizeof(pp.Plan) and osl == pp.Plan.slots.offset and obp == pp.Plan.bytes_per_iter.offset
     assert so == ctypes.sizeof(pp.Opts) and oi == pp.Opts.inner_tol.offset
     assert osp == pp.Opts.spin_limit_ns.offset and oe == pp.Opts.epoch_iters.offset
     assert si == ctypes.sizeof(pp.Info) and orr == pp.Info.rel_res_recursive.offset

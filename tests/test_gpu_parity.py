@@ -515,15 +515,47 @@ def test_mixed_launch_shapes(shape, precision, monkeypatch):
     assert rel(x, x64) <= 1e-4
 
 
-def test_column_dictionary_gives_bitwise_the_same_iterates(monkeypatch):
-    """A stencil's SELL columns as one-byte indices into its few col - row offsets (the
-    default where a matrix has at most 255 of them) and as plain 4-byte columns
-    (PPCG_COL_DICT=0) give bitwise the same iterates: only the addressing differs."""
-    for name, prec in (("varcoeff3d_31", 0), ("box125_12", 0), ("varcoeff3d_31", 2)):
+def test_column_modes_give_bitwise_the_same_iterates(monkeypatch):
+    """A stencil's columns formed from its offset pattern (the default where every row draws
+    its off-diagonals, in ascending order, from at most 16 offsets), read as one-byte indices
+    into its distinct col - row offsets (PPCG_COL_PAT=0, the default where a matrix has at most
+    255 of them) and read as plain 4-byte columns (PPCG_COL_DICT=0) give bitwise the same
+    iterates: the pattern's extra slots hold zeros, which add nothing, and the nonzero terms
+    of each row are summed in the same order.  Covers FP64 Alg. 2, FP32_RU, FP32_IR and the
+    Jacobi-scaled variant on the grid path, a pattern matrix on the cluster path (whose
+    kernel reads the pattern's stored columns), full solves, and the plan each mode reports."""
+    m = pp()
+    cases = [("varcoeff3d_31", dict(path=1, precision=0), m.COLS_PATTERN),
+             ("varcoeff2d_150", dict(path=1, precision=0), m.COLS_PATTERN),
+             ("varcoeff3d_31", dict(path=1, precision=2), m.COLS_PATTERN),
+             ("varcoeff3d_31", dict(path=1, precision=1), m.COLS_PATTERN),
+             ("varcoeff3d_31", dict(path=1, variant=1), m.COLS_PATTERN),
+             ("varcoeff2d_150", dict(path=2, precision=0), m.COLS_SELL),
+             ("box125_12", dict(path=1, precision=0), m.COLS_DICT)]
+    for name, kw, want in cases:
         a, b = problem(name)
-        x1, i1 = gpu(a, b, tol=0.0, maxit=25, path=1, format=2, precision=prec)
-        monkeypatch.setenv("PPCG_COL_DICT", "0")
-        x0, i0 = gpu(a, b, tol=0.0, maxit=25, path=1, format=2, precision=prec)
-        monkeypatch.delenv("PPCG_COL_DICT")
-        assert i1.iters == i0.iters == 25
-        assert np.array_equal(x1, x0), name
+        res = {}
+        for mode, env in (("default", {}), ("dict", {"PPCG_COL_PAT": "0"}), ("col4", {"PPCG_COL_DICT": "0"})):
+            for k in ("PPCG_COL_PAT", "PPCG_COL_DICT"):
+                monkeypatch.delenv(k, raising=False)
+            for k, v in env.items():
+                monkeypatch.setenv(k, v)
+            s = m.Solver.from_csr(a, format=2, **kw)
+            plan = s.plan()
+            xk, ik = s.solve(dev(b), tol=0.0, maxit=25)
+            xf, inf = s.solve(dev(b), tol=1e-8, maxit=20000)
+            res[mode] = (plan, xk.cpu().numpy(), ik, xf.cpu().numpy(), inf)
+            s.close()
+        for k in ("PPCG_COL_PAT", "PPCG_COL_DICT"):
+            monkeypatch.delenv(k, raising=False)
+        p0 = res["default"][0]
+        assert p0.columns == want, (name, kw, p0.columns)
+        assert res["col4"][0].columns == m.COLS_SELL and res["col4"][0].pattern_k == 0
+        if want == m.COLS_PATTERN:
+            assert p0.pattern_k in (4, 6) and res["dict"][0].pattern_k == 0
+        assert p0.convert_seconds > 0 and p0.create_seconds >= p0.convert_seconds
+        for mode in ("dict", "col4"):
+            assert res[mode][2].iters == res["default"][2].iters == 25
+            assert np.array_equal(res[mode][1], res["default"][1]), (name, kw, mode)
+            assert res[mode][4].iters == res["default"][4].iters and res[mode][4].status == m.OK
+            assert np.array_equal(res[mode][3], res["default"][3]), (name, kw, mode)
