@@ -11,8 +11,9 @@ iterations/s through host buffers (e2e), the roofline of the solve kernel agains
 measured HBM copy bandwidth (with the DRAM traffic of the committed ncu capture), SM clocks
 sampled during the timed region, the FP32 forms (reliable updates; inner solves in FP64
 refinement) and the Jacobi-scaled variant against FP64 in time to 1e-8 on the same system,
-the 64^2 solve latency, a batch and a serving figure, and the CPU oracle (single-thread and
-OpenMP builds) timed on a bounded sample.
+the 64^2 solve latency, the 1024-system batch (FP64 and FP32_RU against sequential FP64), a
+serving slice over 1e3-4e6 rows at two offered rates, the create (conversion) time, and the
+CPU oracle (single-thread and OpenMP builds) timed on a bounded sample.
 
 Multi-GPU: replicas only.  Each rank solves its own copy; value = all ranks' iterations /
 the slowest rank's time ("scaling": "weak").
@@ -233,42 +234,46 @@ def measure_latency_2d(pp, torch):
     return out
 
 
-def measure_batch(pp, torch, count, seed=11, precision=0):
-    """Ragged batch (sizes log-uniform 1e3-2e5, half 2-D / half 3-D log-normal stencils):
-    one ppcg_batch_solve of CLUSTER-path handles against sequential ppcg_solve calls of
-    default-plan handles, both to rel 1e-8."""
+def measure_batch(pp, torch, count, seed=11, precisions=(0,)):
+    """Ragged batch (sizes log-uniform 1e3-2e5, half 2-D / half 3-D log-normal stencils), to
+    rel 1e-8: one ppcg_batch_solve of CLUSTER-path handles per precision, against `count`
+    sequential ppcg_solve calls of default-plan FP64 handles (the plain solver)."""
     specs = synth.batch_mix(count, seed)
     systems = [synth.build_spec(sp) for sp in specs]
     rows = sum(a.n for a, _ in systems)
     bs = [torch.from_numpy(b).cuda() for _, b in systems]
     xs = [torch.empty_like(b) for b in bs]
-    seq = [pp.Solver.from_csr(a, precision=precision) for a, _ in systems]
-    bat = [pp.Solver.from_csr(a, precision=precision, path=pp.PATH_CLUSTER) for a, _ in systems]
+    seq = [pp.Solver.from_csr(a) for a, _ in systems]
     # warm-up (first launches of each kernel shape)
     seq[0].solve(bs[0], None, xs[0], tol=TOL, maxit=MAXIT)
-    pp.batch_solve(bat[:2], bs[:2], xs[:2], tol=TOL, maxit=MAXIT)
     e0, e1 = _events()
     e0.record()
     infos_seq = [s.solve(b, None, x, tol=TOL, maxit=MAXIT, sync=False)[1] for s, b, x in zip(seq, bs, xs)]
     e1.record()
     torch.cuda.synchronize()
     t_seq = e0.elapsed_time(e1) * 1e-3
-    e0, e1 = _events()
-    e0.record()
-    infos_bat = pp.batch_solve(bat, bs, xs, tol=TOL, maxit=MAXIT, sync=False)
-    e1.record()
-    torch.cuda.synchronize()
-    t_bat = e0.elapsed_time(e1) * 1e-3
-    ok = all(i.status == pp.OK for i in infos_bat) and all(i.status == pp.OK for i in infos_seq)
-    bad = [{"n": a.n, "seq": pp.status_name(i.status), "seq_iters": i.iters, "batch": pp.status_name(j.status),
-            "batch_iters": j.iters} for (a, _), i, j in zip(systems, infos_seq, infos_bat)
-           if i.status != pp.OK or j.status != pp.OK][:8]
-    iters = sum(i.iters for i in infos_bat)
-    for s in seq + bat:
+    seq_ok = all(i.status == pp.OK for i in infos_seq)
+    for s in seq:
         s.close()
-    return {"systems": count, "rows": rows, "precision": ("fp64", "fp32_ir", "fp32_ru")[precision],
-            "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat, "all_ok": ok, "not_ok": bad,
-            "iters_total": iters, "row_iters_per_s": sum(i.iters * a.n for i, (a, _) in zip(infos_bat, systems)) / t_bat}
+    out = {"systems": count, "rows": rows, "sequential_fp64_s": t_seq, "sequential_all_ok": seq_ok}
+    for precision in precisions:
+        name = ("fp64", "fp32_ir", "fp32_ru")[precision]
+        bat = [pp.Solver.from_csr(a, precision=precision, path=pp.PATH_CLUSTER) for a, _ in systems]
+        pp.batch_solve(bat[:2], bs[:2], xs[:2], tol=TOL, maxit=MAXIT)
+        e0, e1 = _events()
+        e0.record()
+        infos = pp.batch_solve(bat, bs, xs, tol=TOL, maxit=MAXIT, sync=False)
+        e1.record()
+        torch.cuda.synchronize()
+        t_bat = e0.elapsed_time(e1) * 1e-3
+        bad = [{"n": a.n, "status": pp.status_name(j.status), "iters": j.iters}
+               for (a, _), j in zip(systems, infos) if j.status != pp.OK][:8]
+        out[name] = {"batched_s": t_bat, "speedup_vs_sequential_fp64": t_seq / t_bat,
+                     "all_ok": not bad, "not_ok": bad, "iters_total": sum(i.iters for i in infos),
+                     "row_iters_per_s": sum(i.iters * a.n for i, (a, _) in zip(infos, systems)) / t_bat}
+        for s in bat:
+            s.close()
+    return out
 
 
 def _serving_pool(seed, count, hi, buckets=24):
@@ -326,10 +331,10 @@ def run_server(pp, reqs, arrivals, precision=2, epoch_iters=128):
     return lat, wall, status
 
 
-def measure_serving(pp, nreq=160, hi=2e5, seed=5, rate_factors=(0.5,)):
+def measure_serving(pp, nreq=160, hi=2e5, seed=5, rate_factors=(0.5,), buckets=24):
     """Continuous batching: saturation throughput (all requests at t = 0), then Poisson
     arrivals at rate_factor x saturation; p50/p99 latency = poll-visible completion - arrival."""
-    reqs = _serving_pool(seed, nreq, hi)
+    reqs = _serving_pool(seed, nreq, hi, buckets)
     run_server(pp, reqs[:8], [0.0] * 8)                       # warm-up
     lat, wall, st = run_server(pp, reqs, [0.0] * len(reqs))
     sat = len(reqs) / wall
@@ -345,7 +350,8 @@ def measure_serving(pp, nreq=160, hi=2e5, seed=5, rate_factors=(0.5,)):
     seq = len(reqs) / (time.perf_counter() - t0)
     print(json.dumps({"progress": {"saturation_solves_per_s": sat, "sequential_fp64_solves_per_s": seq}}),
           file=sys.stderr, flush=True)
-    out = {"requests": nreq, "size_range": [1e3, hi], "precision": "fp32_ru", "saturation_solves_per_s": sat,
+    out = {"requests": nreq, "size_range": [1e3, hi], "size_buckets_per_family": buckets,
+           "largest_rows": max(a.n for a, _ in reqs), "precision": "fp32_ru", "saturation_solves_per_s": sat,
            "sequential_fp64_solves_per_s": seq, "speedup_vs_sequential_fp64": sat / seq,
            "all_ok": all(s == pp.OK for s in st) and seq_ok, "rates": []}
     rng = np.random.default_rng(seed)
@@ -577,8 +583,8 @@ def main():
         elif args.mode == "latency":
             res = {"mode": "latency", "latency_2d64": measure_latency_2d(pp, torch)}
         elif args.mode == "batch":
-            res = {"mode": "batch", "fp64": measure_batch(pp, torch, args.batch_count),
-                   "fp32_ru": measure_batch(pp, torch, args.batch_count, precision=pp.FP32_RU)}
+            res = {"mode": "batch", "batch": measure_batch(pp, torch, args.batch_count,
+                                                           precisions=(pp.FP64, pp.FP32_RU))}
         else:
             res = {"mode": "serve", "serving": measure_serving(pp, nreq=2000, hi=4e6,
                                                                rate_factors=(0.25, 0.5, 1.0, 2.0, 4.0))}
@@ -604,6 +610,7 @@ def main():
     n, nnz = a.n, a.nnz
     prec = {"fp64": pp.FP64, "fp32_ru": pp.FP32_RU, "fp32_ir": pp.FP32_IR}[args.precision]
     solver = pp.Solver.from_csr(a, precision=prec)
+    plan = solver.plan()
     b_d = torch.from_numpy(b).cuda()
     x_d = torch.empty(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -688,6 +695,12 @@ def main():
                        "l2": f"inputs larger than L2 ({bytes_iter / 1e9:.2f} GB streamed per iteration vs 126 MB L2)",
                        "parallelism": f"replicas x{ws}"},
             "e2e": e2e, "roofline": roofline, "clocks": clocks,
+            # ppcg_create of the timed handle (host CSR upload, validation, CSR -> device
+            # layout conversion, detection, workspace): paid once per matrix
+            "create_s": plan.create_seconds,
+            "plan": {"columns": ("sell", "sell+dictionary", "offset pattern", "matrix-free")[plan.columns],
+                     "pattern_k": plan.pattern_k, "sigma": plan.sigma, "ctas": plan.ctas,
+                     "padding": plan.padding, "convert_s": plan.convert_seconds},
             "gpu_launches": 4 * args.steps}   # per solve: x0 fill, control init, k_grid, x copy-out
 
     if not args.no_mixed:
@@ -733,8 +746,12 @@ def main():
 
     if not args.no_extras:
         line["latency_2d64"] = measure_latency_2d(pp, torch)
-        line["batch"] = measure_batch(pp, torch, 128)
-        line["serving"] = measure_serving(pp)
+        # the 1024-system ragged batch, FP64 and FP32 + reliable updates, against 1024
+        # sequential FP64 solves
+        line["batch"] = measure_batch(pp, torch, 1024, precisions=(pp.FP64, pp.FP32_RU))
+        # a bounded slice of the serving stream: sizes 1e3-4e6 rows over the three families,
+        # saturation and two offered rates
+        line["serving"] = measure_serving(pp, nreq=96, hi=4e6, rate_factors=(0.5, 1.0), buckets=8)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(a, b)

@@ -202,9 +202,16 @@ def rgg_laplacian(npts, radius, shift, seed, chunk=1 << 22):
     np.cumsum(counts, out=start[1:])
     r2 = radius * radius
     rows_l, cols_l = [], []
+    # The distance test is symmetric to the last bit ((a - b)^2 == (b - a)^2 in IEEE
+    # arithmetic), so only the point's own cell and the 13 neighbour cells with a positive
+    # offset (in (dz, dy, dx) order) are searched, and each pair found across cells is kept in
+    # both orientations: the same edge set as searching all 27 cells, at half the work.
     for dz in (-1, 0, 1):
         for dy in (-1, 0, 1):
             for dx in (-1, 0, 1):
+                if (dz, dy, dx) < (0, 0, 0):
+                    continue
+                mirror = (dz, dy, dx) != (0, 0, 0)
                 for lo in range(0, npts, chunk):
                     hi = min(npts, lo + chunk)
                     c = cell3[lo:hi]
@@ -223,6 +230,9 @@ def rgg_laplacian(npts, radius, shift, seed, chunk=1 << 22):
                     keep = (np.einsum("ij,ij->i", d, d) < r2) & (i_rep != j)
                     rows_l.append(i_rep[keep])
                     cols_l.append(j[keep])
+                    if mirror:
+                        rows_l.append(cols_l[-1])
+                        cols_l.append(rows_l[-2])
     rows = np.concatenate(rows_l)
     cols = np.concatenate(cols_l)
     deg = np.bincount(rows, minlength=npts).astype(np.float64)
@@ -230,7 +240,7 @@ def rgg_laplacian(npts, radius, shift, seed, chunk=1 << 22):
     rows = np.concatenate([rows, diag_idx])
     cols = np.concatenate([cols, diag_idx])
     vals = np.concatenate([np.full(len(rows) - npts, -1.0), deg + shift])
-    o = np.lexsort((cols, rows))
+    o = np.argsort(rows * np.int64(npts) + cols, kind="stable")   # (row, col) pairs are unique
     rows, cols, vals = rows[o], cols[o], vals[o]
     row_ptr = np.zeros(npts + 1, dtype=np.int64)
     np.cumsum(np.bincount(rows, minlength=npts), out=row_ptr[1:])
