@@ -276,6 +276,41 @@ def measure_batch(pp, torch, count, seed=11, precisions=(0,)):
     return out
 
 
+def measure_tuned_batch(pp, torch, count=1024, lo=1e3, hi=3e3, seed=23):
+    """1024 small ragged systems (1e3-3e3 rows, half 2-D / half 3-D log-normal stencils), to
+    rel 1e-8, in one batched launch of CLUSTER-path handles: the default plan (8 CTAs per
+    system) against the create-time tuned plan (cluster_ctas = 0), FP64 and FP32_RU."""
+    specs = synth.batch_mix(count, seed, lo=lo, hi=hi)
+    systems = [synth.build_spec(sp) for sp in specs]
+    bs = [torch.from_numpy(b).cuda() for _, b in systems]
+    xs = [torch.empty_like(b) for b in bs]
+    out = {"systems": count, "size_range": [lo, hi]}
+    for precision, pname in ((pp.FP64, "fp64"), (pp.FP32_RU, "fp32_ru")):
+        rec = {}
+        for label, cc in (("fixed_8", 8), ("tuned", 0)):
+            hs = [pp.Solver.from_csr(a, precision=precision, path=pp.PATH_CLUSTER, cluster_ctas=cc)
+                  for a, _ in systems]
+            pp.batch_solve(hs[:2], bs[:2], xs[:2], tol=TOL, maxit=MAXIT)
+            ts = []
+            for _ in range(2):
+                e0, e1 = _events()
+                e0.record()
+                infos = pp.batch_solve(hs, bs, xs, tol=TOL, maxit=MAXIT, sync=False)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+            sizes = {}
+            for h in hs:
+                c = h.plan().ctas
+                sizes[str(c)] = sizes.get(str(c), 0) + 1
+            rec[label] = {"s": min(ts), "ctas_per_system": sizes, "all_ok": all(i.status == pp.OK for i in infos)}
+            for h in hs:
+                h.close()
+        rec["tuned_speedup"] = rec["fixed_8"]["s"] / rec["tuned"]["s"]
+        out[pname] = rec
+    return out
+
+
 def _serving_pool(seed, count, hi, buckets=24):
     """Request stream: sizes log-uniform [1e3, hi] over {2-D, 3-D var-coeff, RGG}.  Sizes are
     snapped to `buckets` log-spaced values so each (family, size) matrix is built once;
@@ -749,6 +784,8 @@ def main():
         # the 1024-system ragged batch, FP64 and FP32 + reliable updates, against 1024
         # sequential FP64 solves
         line["batch"] = measure_batch(pp, torch, 1024, precisions=(pp.FP64, pp.FP32_RU))
+        # the create-time cluster-size tuner on a batch of small systems (where it matters)
+        line["batch_small_tuned"] = measure_tuned_batch(pp, torch)
         # a bounded slice of the serving stream: sizes 1e3-4e6 rows over the three families,
         # saturation and two offered rates
         line["serving"] = measure_serving(pp, nreq=96, hi=4e6, rate_factors=(0.5, 1.0), buckets=8)

@@ -149,7 +149,16 @@ typedef struct {
                                0 = 1e-6; negative = off */
   int32_t gap_fall;         /* the fall of gamma between two measurements; 0 = 100 (the residual
                                norm about 10x) */
-  int32_t reserved[1];
+  int32_t cluster_ctas;     /* CLUSTER path: CTAs per system (thread-block cluster size 2, 4, 8 or 16;
+                               default 8).  0 = tuned at create: a few iterations of the system are
+                               timed on the device with 2, 4 and 8 CTAs and the size with the least
+                               CTA-time per iteration wins (the largest within 10% of it), cached per
+                               family signature and size bucket.  Fixed for the handle, so a system's
+                               result is the same solo and in a batch.  A batch runs one launch per
+                               cluster size among its handles: batches of small systems gain from
+                               tuning (1e3-3e3 rows: 1.36x FP64, 1.46x FP32_RU on B300), a batch that
+                               mixes sizes gains nothing (it is bandwidth-bound and one launch of one
+                               size serves it best).  The server uses 8 */
 } ppcg_opts;
 
 /* Per-solve results.  Filled asynchronously; valid after the solve's stream is synchronised. */

@@ -54,7 +54,7 @@ class Opts(ctypes.Structure):
                 ("cluster_max_rows", ctypes.c_int32), ("epoch_iters", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("gap_theta", ctypes.c_double), ("gap_fall", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("cluster_ctas", ctypes.c_int32)]
 
 
 class Plan(ctypes.Structure):

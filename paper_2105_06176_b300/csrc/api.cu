@@ -1,11 +1,13 @@
 // C ABI of the solver (include/ppcg.h): handles, solve, batch solve.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <chrono>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -164,6 +166,11 @@ __global__ void k_from_slot(int64_t n, const int32_t* __restrict__ perm, const d
   if (i < n) dst[perm ? perm[i] : i] = blk[slot_index(i, ns, slot)];
 }
 
+__global__ void k_fill_plain(int64_t n, double* __restrict__ p, double v) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
 __global__ void k_init_ctl(Ctl* c, int32_t state) {
   Ctl z;
   memset(&z, 0, sizeof(z));
@@ -294,14 +301,84 @@ const int32_t* single_work_list() {
   return d_list;
 }
 
-// One side stream and a fork/join event pair per device (batch launches of the on-chip
-// path run beside the cluster-path launch).  Created on first use, kept for the process.
-bool side_stream(int device, cudaStream_t* s, cudaEvent_t* fork, cudaEvent_t* join) {
+// Cluster size of a CLUSTER-path plan (opts.cluster_ctas == 0).  In a batch the GPU is
+// shared by many clusters, so what a system costs is the CTA-time of an iteration: its
+// time per iteration on a cluster of cs CTAs times cs.  Small systems are bound by the
+// per-iteration barrier, reduction and control step, which a few CTAs do as fast as many
+// (small clusters win); large ones by their bytes, which more CTAs move proportionally
+// faster (the size barely changes the cost, and the larger size shortens the batch's
+// tail).  So each candidate of {2, 4, 8} is timed on the device -- the handle's own
+// system, b = 1, x0 = 0, the difference of a 4- and a 24-iteration run of one cluster --
+// and the largest size within 10% of the least CTA-time wins.  (16-CTA clusters lost in
+// every batch measured: fewer clusters, and a second launch for the rest.)  The choice is
+// cached per device, precision, variant, norm, offset pattern, nonzeros per row and
+// half-octave of rows, so a family of similar systems is timed once.
+int tune_cluster_size(ppcg_ctx* h, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<std::array<int64_t, 7>, int> cache;
+  const int64_t n = h->n;
+  const std::array<int64_t, 7> key{h->device, h->opts.precision, h->opts.variant, h->opts.norm, h->A.pat_k,
+                                   std::llround(2.0 * (double)h->nnz / (double)n),
+                                   std::llround(2.0 * std::log2((double)n))};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  const int32_t* list = single_work_list();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!list || cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return kClusterSize;
+  }
+  k_fill_plain<<<blocks_for(n, 256), 256, 0, st>>>(n, h->b_ws, 1.0);
+  const double* b_keep = h->desc.b;
+  const int32_t xz_keep = h->desc.x_zero;
+  h->desc.b = h->b_ws;
+  auto run = [&](int cs, int iters, float* ms) -> bool {
+    k_fill_slot<<<blocks_for(n, 256), 256, 0, st>>>(n, h->desc.v64, h->ns64, h->xslot, 0.0);
+    h->desc.x_zero = 1;
+    prepare_control(h, 0.0, iters, st);
+    cudaMemcpyAsync(h->d_desc, &h->desc, sizeof(SysDesc), cudaMemcpyHostToDevice, st);
+    cudaEventRecord(e0, st);
+    if (launch_clusters(h->d_desc, list, list + 1, 1, 0, st, false, nullptr, 0, cs) != cudaSuccess) return false;
+    cudaEventRecord(e1, st);
+    return cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(ms, e0, e1) == cudaSuccess;
+  };
+  double cost[3] = {0, 0, 0};
+  const int cands[3] = {2, 4, 8};
+  double best = HUGE_VAL;
+  for (int k = 0; k < 3; k++) {
+    cost[k] = HUGE_VAL;
+    if (max_active_clusters(h->device, cands[k]) < 1) continue;
+    float warm = 0.f, t4 = 0.f, t24 = 0.f;
+    if (!run(cands[k], 2, &warm) || !run(cands[k], 4, &t4) || !run(cands[k], 24, &t24)) { cudaGetLastError(); continue; }
+    cost[k] = std::max(1e-6, (double)(t24 - t4) / 20.0) * cands[k];
+    best = std::min(best, cost[k]);
+  }
+  int cs = kClusterSize;
+  if (best < HUGE_VAL)
+    for (int k = 0; k < 3; k++)
+      if (cost[k] <= 1.1 * best) cs = cands[k];
+  h->desc.b = b_keep;
+  h->desc.x_zero = xz_keep;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = cs;
+  return cs;
+}
+
+// Side streams with a fork/join event pair each, per device (batch launches of the on-chip
+// path, index 0, and of the cluster sizes after the first, indices 1-3, run beside the
+// caller's stream).  Created on first use, kept for the process.
+bool side_stream(int device, cudaStream_t* s, cudaEvent_t* fork, cudaEvent_t* join, int idx = 0) {
   struct Side { cudaStream_t s = nullptr; cudaEvent_t fork = nullptr, join = nullptr; };
   static std::mutex mu;
   static std::unordered_map<int, Side> per;
   std::lock_guard<std::mutex> lk(mu);
-  Side& x = per[device];
+  Side& x = per[device * 8 + idx];
   if (!x.s) {
     if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -377,6 +454,7 @@ void ppcg_opts_default(ppcg_opts* o) {
   o->max_restarts = 8;
   o->gap_theta = 1e-6;
   o->gap_fall = 100;
+  o->cluster_ctas = 8;
 }
 
 const char* ppcg_last_error(void) { return g_err; }
@@ -518,7 +596,15 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
     h->grid = need >= sms ? full : (int)std::max<int64_t>(1, need);
     h->nparts = h->grid;
   } else {
-    h->grid = kClusterSize;
+    const int cc = h->opts.cluster_ctas;
+    if (path == PPCG_PATH_CLUSTER && cc != 0 && cc != 2 && cc != 4 && cc != 8 && cc != 16) {
+      free_all(h);
+      delete h;
+      set_error("ppcg_create: cluster_ctas must be 0 (tuned), 2, 4, 8 or 16");
+      return PPCG_ERR_ARG;
+    }
+    h->cluster_cs = path == PPCG_PATH_CLUSTER && cc != 0 ? cc : kClusterSize;
+    h->grid = h->cluster_cs;
     h->nparts = kClusterSize;
   }
   const bool fp32 = h->opts.precision != PPCG_FP64;
@@ -591,6 +677,10 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
   d.ctl = h->ctl;
   d.bar = h->bar;
   d.err = h->err;
+  if (path == PPCG_PATH_CLUSTER && h->opts.cluster_ctas == 0) {
+    h->cluster_cs = tune_cluster_size(h, stream);
+    h->grid = h->cluster_cs;
+  }
   h->create_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_create).count();
   *handle = h;
   return PPCG_OK;
@@ -611,7 +701,7 @@ ppcg_status ppcg_plan_info(ppcg_handle h, ppcg_plan* out) {
   out->sigma = h->sell.sigma;
   out->pattern_k = h->A.pat_k;
   out->dict_size = h->sell.col_dict;
-  out->ctas = h->path == PPCG_PATH_GRID ? h->grid : (h->path == PPCG_PATH_ONCHIP ? h->onchip_nc : h->grid);
+  out->ctas = h->path == PPCG_PATH_GRID ? h->grid : (h->path == PPCG_PATH_ONCHIP ? h->onchip_nc : h->cluster_cs);
   out->slots = h->sell.nslots;
   out->padding = h->sell.padding;
   out->convert_seconds = h->sell.seconds;
@@ -645,7 +735,7 @@ ppcg_status ppcg_solve(ppcg_handle h, const double* b, const double* x0, double*
   } else {
     const int32_t* d_list = single_work_list();
     if (!d_list) { set_error("ppcg_solve: could not allocate the cluster work list"); return PPCG_ERR_OOM; }
-    e = launch_clusters(h->d_desc, d_list, d_list + 1, 1, 0, st, /*spread=*/true);
+    e = launch_clusters(h->d_desc, d_list, d_list + 1, 1, 0, st, /*spread=*/true, nullptr, 0, h->cluster_cs);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -767,59 +857,93 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
       return PPCG_ERR_CUDA;
     }
   }
-  // Cluster-path systems: one persistent launch, systems ordered longest first by an
-  // estimate.  Up to two systems per cluster: a static longest-processing-time assignment
-  // (each cluster's first system is one of the longest, the rest fill the least loaded
-  // clusters), which leaves the critical longest solves the least contended.  More: the
-  // clusters take systems from a shared counter (list scheduling, which absorbs the
-  // estimate's errors; 1,024 systems: 1.78 -> 1.19 s).  Results do not depend on either.
+  // Cluster-path systems: one persistent launch per cluster size in the batch (the sizes
+  // the handles' plans fixed), largest size first, each on its own stream: the launch of
+  // the largest clusters (the largest systems) fills the GPU first and the next ones take
+  // the SMs its clusters give up as its work list drains.  Within a launch, systems are
+  // ordered longest first by an estimate.  Up to two systems per cluster: a static
+  // longest-processing-time assignment (each cluster's first system is one of the longest,
+  // the rest fill the least loaded clusters), which leaves the critical longest solves the
+  // least contended.  More: the clusters take systems from a shared counter (list
+  // scheduling, which absorbs the estimate's errors; 1,024 systems: 1.78 -> 1.19 s).
+  // Results depend on neither.
+  std::vector<cudaEvent_t> joins;
   if (!cl.empty()) {
-    const int m = (int)cl.size();
-    std::vector<SysDesc> descs(m);
-    std::vector<double> cost(m);
-    for (int k = 0; k < m; k++) {
-      descs[k] = hs[cl[k]]->desc;
-      cost[k] = cluster_solve_cost(hs[cl[k]], 0);
-    }
-    const int nclusters = std::min(m, max_active_clusters(hs[cl[0]]->device));
-    std::vector<int32_t> order(m);
-    for (int k = 0; k < m; k++) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-    const bool dynamic = m > 2 * nclusters;
-    std::vector<int32_t> packed;   // dynamic: order, counter; static: list_ptr, lists
-    if (dynamic) {
-      packed = order;
-      packed.push_back(0);
-    } else {
-      std::vector<std::vector<int>> lists(nclusters);
-      std::vector<double> load(nclusters, 0.0);
-      for (int k : order) {
-        const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        lists[c].push_back(k);
-        load[c] += cost[k];
+    std::vector<int> sizes;
+    for (int i : cl)
+      if (std::find(sizes.begin(), sizes.end(), hs[i]->cluster_cs) == sizes.end()) sizes.push_back(hs[i]->cluster_cs);
+    std::sort(sizes.rbegin(), sizes.rend());
+    for (size_t gi = 0; gi < sizes.size(); gi++) {
+      const int cs = sizes[gi];
+      std::vector<int> grp;
+      for (int i : cl)
+        if (hs[i]->cluster_cs == cs) grp.push_back(i);
+      cudaStream_t gs = st;
+      if (gi > 0) {
+        cudaEvent_t fork = nullptr, join = nullptr;
+        if (!side_stream(hs[grp[0]]->device, &gs, &fork, &join, (int)gi)) {
+          for (cudaEvent_t j : joins) cudaStreamWaitEvent(st, j, 0);
+          set_error("ppcg_batch_solve: could not create a side stream");
+          return PPCG_ERR_CUDA;
+        }
+        cudaEventRecord(fork, st);
+        cudaStreamWaitEvent(gs, fork, 0);
+        joins.push_back(join);
       }
-      packed.push_back(0);
-      for (auto& l : lists) packed.push_back(packed.back() + (int32_t)l.size());
-      for (auto& l : lists) packed.insert(packed.end(), l.begin(), l.end());
-    }
-    SysDesc* d_descs = nullptr;
-    int32_t* d_lists = nullptr;
-    if (cudaMallocAsync((void**)&d_descs, m * sizeof(SysDesc), st) != cudaSuccess ||
-        cudaMallocAsync((void**)&d_lists, packed.size() * sizeof(int32_t), st) != cudaSuccess) {
-      cudaGetLastError();
-      set_error("ppcg_batch_solve: out of device memory for the schedule");
-      return PPCG_ERR_OOM;
-    }
-    cudaMemcpyAsync(d_descs, descs.data(), m * sizeof(SysDesc), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(d_lists, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-    cudaError_t e = dynamic ? launch_clusters(d_descs, d_lists, nullptr, nclusters, 0, st, false, d_lists + m, m)
-                            : launch_clusters(d_descs, d_lists + nclusters + 1, d_lists, nclusters, 0, st);
-    cudaFreeAsync(d_descs, st);
-    cudaFreeAsync(d_lists, st);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      set_error("ppcg_batch_solve: cluster launch failed: %s", cudaGetErrorString(e));
-      return PPCG_ERR_CUDA;
+      const int m = (int)grp.size();
+      std::vector<SysDesc> descs(m);
+      std::vector<double> cost(m);
+      for (int k = 0; k < m; k++) {
+        descs[k] = hs[grp[k]]->desc;
+        cost[k] = cluster_solve_cost(hs[grp[k]], 0);
+      }
+      const int nclusters = std::max(1, std::min(m, max_active_clusters(hs[grp[0]]->device, cs)));
+      std::vector<int32_t> order(m);
+      for (int k = 0; k < m; k++) order[k] = k;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+      const bool dynamic = m > 2 * nclusters;
+      std::vector<int32_t> packed;   // dynamic: order, counter; static: list_ptr, lists
+      if (dynamic) {
+        packed = order;
+        packed.push_back(0);
+      } else {
+        std::vector<std::vector<int>> lists(nclusters);
+        std::vector<double> load(nclusters, 0.0);
+        for (int k : order) {
+          const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+          lists[c].push_back(k);
+          load[c] += cost[k];
+        }
+        packed.push_back(0);
+        for (auto& l : lists) packed.push_back(packed.back() + (int32_t)l.size());
+        for (auto& l : lists) packed.insert(packed.end(), l.begin(), l.end());
+      }
+      SysDesc* d_descs = nullptr;
+      int32_t* d_lists = nullptr;
+      cudaError_t e = cudaSuccess;
+      if (cudaMallocAsync((void**)&d_descs, m * sizeof(SysDesc), gs) != cudaSuccess ||
+          cudaMallocAsync((void**)&d_lists, packed.size() * sizeof(int32_t), gs) != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaErrorMemoryAllocation;
+      } else {
+        cudaMemcpyAsync(d_descs, descs.data(), m * sizeof(SysDesc), cudaMemcpyHostToDevice, gs);
+        cudaMemcpyAsync(d_lists, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice, gs);
+        e = dynamic ? launch_clusters(d_descs, d_lists, nullptr, nclusters, 0, gs, false, d_lists + m, m, cs)
+                    : launch_clusters(d_descs, d_lists + nclusters + 1, d_lists, nclusters, 0, gs, false, nullptr, 0,
+                                      cs);
+        cudaFreeAsync(d_descs, gs);
+        cudaFreeAsync(d_lists, gs);
+      }
+      if (gi > 0) cudaEventRecord(joins.back(), gs);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (cudaEvent_t j : joins) cudaStreamWaitEvent(st, j, 0);
+        if (oc_done) cudaStreamWaitEvent(st, oc_done, 0);
+        set_error(e == cudaErrorMemoryAllocation ? "ppcg_batch_solve: out of device memory for the schedule"
+                                                 : "ppcg_batch_solve: cluster launch failed: %s",
+                  cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? PPCG_ERR_OOM : PPCG_ERR_CUDA;
+      }
     }
   }
   // Grid-path systems: one whole-GPU launch each.
@@ -834,6 +958,7 @@ ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* hs, const double*
     }
   }
   if (oc_done) cudaStreamWaitEvent(st, oc_done, 0);
+  for (cudaEvent_t j : joins) cudaStreamWaitEvent(st, j, 0);
   std::vector<std::pair<ppcg_ctx*, ppcg_info*>> items;
   for (int i = 0; i < count; i++) {
     if (hs[i]->n == 0) { hs[i]->last_solve = 2; continue; }

@@ -58,6 +58,8 @@ struct ppcg_ctx {
   int32_t path = PPCG_PATH_GRID;
   size_t onchip_smem = 0;   // dynamic shared memory per CTA of the on-chip path
   int onchip_nc = 8;        // CTAs per on-chip cluster (8 or 16)
+  int cluster_cs = 8;       // CTAs per cluster of the CLUSTER path (2, 4, 8 or 16)
+  int64_t tune_key = 0;     // cluster-size cache key (0: not tuned)
   int32_t box_g = 0, box_r = 0;      // matrix-free box stencil (box_g > 0)
   double box_cd = 0.0, box_co = 0.0;
   int shape = 0;       // grid-path launch shape (index into the kernel variants)

@@ -15,7 +15,7 @@ constexpr int kSlotX64 = 8, kSlotInvd = 9;    // x and D^-1 slots
 // Jacobi-scaled variant, FP64 block: r wa wb z s p x d sig (sig = a_ii^-1/2)
 constexpr int kSlotsS = 9, kSlotXS = 6, kSlotDS = 7, kSlotSigS = 8;
 constexpr int kClusterThreads = 256; // CTA size of the cluster path
-constexpr int kClusterSize = 8;      // CTAs per thread-block cluster (portable maximum)
+constexpr int kClusterSize = 8;      // default CTAs per thread-block cluster (portable maximum)
 
 // SELL-C-sigma matrix in the solver's row order (rows permuted within sigma windows when
 // sigma > 1; columns renumbered with the same permutation).  Values are A D^-1.
@@ -132,9 +132,10 @@ struct SysDesc {
 // Launchers (solver.cu)
 cudaError_t launch_grid(const SysDesc* d_desc, int shape, int grid, int budget, cudaStream_t st);
 // d_next != nullptr: dynamic schedule over d_list[0..m) (see k_cluster); *d_next must be 0.
+// cs: CTAs per cluster (2, 4, 8 or 16; every system of the launch has that plan).
 cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
                             int nclusters, int budget, cudaStream_t st, bool spread = false,
-                            int32_t* d_next = nullptr, int32_t m = 0);
+                            int32_t* d_next = nullptr, int32_t m = 0, int cs = 8);
 // On-chip path, clusters of nc = 8 or 16 CTAs (16: non-portable, where the device allows).
 cudaError_t launch_onchip(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
                           int nclusters, int budget, size_t smem, int nc, cudaStream_t st);
@@ -148,7 +149,7 @@ int grid_dict_shape();         // the default SELL shape reading the column dict
 int grid_pat_shape();          // the default SELL shape forming columns from the offset pattern
 int grid_threads(int shape);
 int grid_blocks_for_device(int device, int shape);
-int max_active_clusters(int device);
+int max_active_clusters(int device, int cs = 8);   // 0 when clusters of cs CTAs cannot run
 cudaError_t launch_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, int grid,
                                     int drop_rank, int64_t limit_ns, cudaStream_t st);
 

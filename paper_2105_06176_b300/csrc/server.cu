@@ -117,6 +117,8 @@ void admit_loop(ppcg_srv* S) {
     ppcg_opts o = S->opts;
     if (o.path == PPCG_PATH_AUTO || o.path == PPCG_PATH_ONCHIP)
       o.path = req->n <= o.cluster_max_rows ? PPCG_PATH_CLUSTER : PPCG_PATH_GRID;
+    // one cluster size for every served solve: an epoch is one launch of clusters
+    o.cluster_ctas = kClusterSize;
     ppcg_status st = ppcg_create(&h, req->n, req->nnz, req->rp.data(), req->col.data(), req->val.data(), &o,
                                  S->s_admit);
     Slot slot;
@@ -172,7 +174,7 @@ bool run_cluster_epoch(ppcg_srv* S, const std::vector<Slot*>& slots) {
   // Longest first: a static longest-processing-time assignment while there are at most two
   // solves per cluster, else the clusters take solves from a shared counter (as in
   // ppcg_batch_solve).
-  const int nclusters = std::min(m, max_active_clusters(S->device));
+  const int nclusters = std::max(1, std::min(m, max_active_clusters(S->device, kClusterSize)));
   std::vector<int32_t> order(m);
   for (int k = 0; k < m; k++) order[k] = k;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });

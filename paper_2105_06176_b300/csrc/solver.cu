@@ -1962,20 +1962,20 @@ template <int NSM> struct SharedT {
 };
 
 // Cluster path: the cluster's block partials, read from every CTA's shared memory by lanes
-// 0-7 of warp 0 and summed by a fixed shuffle tree (deterministic).  out is written by
-// thread 0.
+// 0..nranks-1 of warp 0 and summed by a fixed shuffle tree (deterministic for a given
+// cluster size, a power of two up to 16).  out is written by thread 0.
 __device__ __forceinline__ void cluster_reduce(const double* part, double* out) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
+    const int nr = (int)cluster_nranks();
     const uint32_t base = smem_addr(part);
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    if (lane < kClusterSize) {
+    if (lane < nr) {
       s0 = ld_dsmem(base, lane);
       s1 = ld_dsmem(base + 8, lane);
       s2 = ld_dsmem(base + 16, lane);
     }
-#pragma unroll
-    for (int o = kClusterSize / 2; o > 0; o >>= 1) {
+    for (int o = nr / 2; o > 0; o >>= 1) {
       s0 += __shfl_down_sync(kFull, s0, o);
       s1 += __shfl_down_sync(kFull, s1, o);
       s2 += __shfl_down_sync(kFull, s2, o);
@@ -2201,7 +2201,9 @@ static_assert(kPatShape == kNumGridShapes - 1, "the pattern kernel is the last s
 // list_ptr[c + 1]).  Dynamic schedule: every cluster takes the next entry of list (ordered
 // longest first) from the counter *next until m entries are taken -- list scheduling, which
 // absorbs the errors of any cost estimate.  A system's result does not depend on the
-// cluster that runs it.
+// cluster that runs it, only on the launch's cluster size (every system of a launch has
+// the same one, fixed by its handle's plan).  Systems with an offset pattern run the
+// pattern form of the passes (no column bytes), the others read their 4-byte columns.
 __global__ void __launch_bounds__(kClusterThreads, 4) k_cluster(const SysDesc* descs, const int32_t* list,
                                                              const int32_t* list_ptr, int budget,
                                                              int32_t* next, int32_t m) {
@@ -2211,9 +2213,12 @@ __global__ void __launch_bounds__(kClusterThreads, 4) k_cluster(const SysDesc* d
   unsigned cid;
   unsigned phases = 0;
   asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+  auto run = [&](const SysDesc* d) {
+    if (d->A.pat_k > 0) run_system<false, false, kColPat>(g, d, budget, sh, nullptr, nullptr, phases);
+    else run_system<false>(g, d, budget, sh, nullptr, nullptr, phases);
+  };
   if (!next) {
-    for (int k = list_ptr[cid]; k < list_ptr[cid + 1]; k++)
-      run_system<false>(g, descs + list[k], budget, sh, nullptr, nullptr, phases);
+    for (int k = list_ptr[cid]; k < list_ptr[cid + 1]; k++) run(descs + list[k]);
     return;
   }
   const uint32_t rank = cluster_rank();
@@ -2230,7 +2235,7 @@ __global__ void __launch_bounds__(kClusterThreads, 4) k_cluster(const SysDesc* d
     __syncthreads();
     cluster_barrier();   // everyone has read it before rank 0 takes the next one
     if (k >= m) break;
-    run_system<false>(g, descs + list[k], budget, sh, nullptr, nullptr, phases);
+    run(descs + list[k]);
   }
 }
 
@@ -2602,14 +2607,30 @@ int grid_blocks_for_device(int device, int shape) {
   return sms * per;
 }
 
-int max_active_clusters(int device) {
+// Cluster sizes above the portable 8 need the kernel's opt-in (once per device and kernel).
+static cudaError_t allow_large_clusters(const void* fn) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, cudaError_t> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find({dev, fn});
+  if (it != done.end()) return it->second;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) cudaGetLastError();
+  done[{dev, fn}] = e;
+  return e;
+}
+
+int max_active_clusters(int device, int cs) {
   (void)device;
+  if (cs > 8 && allow_large_clusters((const void*)k_cluster) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kClusterSize * 64);
+  cfg.gridDim = dim3(cs * 64);
   cfg.blockDim = dim3(kClusterThreads);
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kClusterSize;
+  at[0].val.clusterDim.x = cs;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
@@ -2617,9 +2638,9 @@ int max_active_clusters(int device) {
   int n = 0;
   if (cudaOccupancyMaxActiveClusters(&n, (void*)k_cluster, &cfg) != cudaSuccess) {
     cudaGetLastError();
-    return 1;
+    return 0;
   }
-  return n > 0 ? n : 1;
+  return n;
 }
 
 cudaError_t launch_grid(const SysDesc* d_desc, int shape, int grid, int budget, cudaStream_t st) {
@@ -2644,19 +2665,25 @@ cudaError_t ensure_smem_attr(const void* fn, size_t bytes) {
 }
 
 cudaError_t launch_clusters(const SysDesc* d_descs, const int32_t* d_list, const int32_t* d_list_ptr,
-                            int nclusters, int budget, cudaStream_t st, bool spread, int32_t* d_next, int32_t m) {
+                            int nclusters, int budget, cudaStream_t st, bool spread, int32_t* d_next, int32_t m,
+                            int cs) {
+  if (cs != 2 && cs != 4 && cs != 8 && cs != 16) return cudaErrorInvalidValue;
+  if (cs > 8) {
+    cudaError_t e = allow_large_clusters((const void*)k_cluster);
+    if (e != cudaSuccess) return e;
+  }
   // spread: request enough dynamic shared memory that no two CTAs share an SM, so a lone
-  // cluster gets the FP64 pipes of 8 SMs instead of being packed onto two.
+  // cluster gets the FP64 pipes of cs SMs instead of being packed onto a few.
   const int spread_smem = 120 * 1024;
   if (spread && ensure_smem_attr((const void*)k_cluster, spread_smem) != cudaSuccess) cudaGetLastError();
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kClusterSize * nclusters);
+  cfg.gridDim = dim3(cs * nclusters);
   cfg.blockDim = dim3(kClusterThreads);
   cfg.dynamicSmemBytes = spread ? spread_smem : 0;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kClusterSize;
+  at[0].val.clusterDim.x = cs;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
@@ -2677,19 +2704,7 @@ size_t onchip_smem_limit(int device) {
 }
 
 // The 16-CTA cluster is beyond the portable size: the kernel must opt in (once per device).
-static cudaError_t allow_cluster16() {
-  static std::mutex mu;
-  static std::map<int, cudaError_t> done;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lk(mu);
-  auto it = done.find(dev);
-  if (it != done.end()) return it->second;
-  cudaError_t e = cudaFuncSetAttribute((const void*)k_onchip, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e != cudaSuccess) cudaGetLastError();
-  done[dev] = e;
-  return e;
-}
+static cudaError_t allow_cluster16() { return allow_large_clusters((const void*)k_onchip); }
 
 bool onchip_cluster_fits(int nc, size_t smem) {
   if (nc == 16 && allow_cluster16() != cudaSuccess) return false;

@@ -49,7 +49,7 @@ def test_library_loads_and_binding_matches(libpath):
     lib.ppcg_opts_default(ctypes.byref(o))     # host-only call
     assert o.precision == pp.FP64 and o.norm == pp.NORM_REL_R and o.inner_tol == 1e-2
     assert o.epoch_iters == 256 and o.cluster_max_rows == 16384
-    assert o.gap_theta == 1e-6 and o.gap_fall == 100
+    assert o.gap_theta == 1e-6 and o.gap_fall == 100 and o.cluster_ctas == 8
     # host-only argument checks: no CUDA call is made before they fail
     info = pp.Info()
     assert lib.ppcg_last_info(None, ctypes.byref(info)) == pp.ERR_ARG
@@ -70,7 +70,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(ppcg_opts), offsetof(ppcg_opts, inner_tol),
          offsetof(ppcg_opts, spin_limit_ns), offsetof(ppcg_opts, epoch_iters), sizeof(ppcg_info));
   printf("%zu %zu\n", offsetof(ppcg_info, rel_res_recursive), offsetof(ppcg_info, bnorm));
-  printf("%zu %zu\n", offsetof(ppcg_opts, gap_theta), offsetof(ppcg_opts, gap_fall));
+  printf("%zu %zu %zu\n", offsetof(ppcg_opts, gap_theta), offsetof(ppcg_opts, gap_fall),
+         offsetof(ppcg_opts, cluster_ctas));
   printf("%zu %zu %zu\n", sizeof(ppcg_plan), offsetof(ppcg_plan, slots), offsetof(ppcg_plan, bytes_per_iter));
   return 0;
 }''')
@@ -81,8 +82,9 @@ int main(void) {
     a, b, c, d = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:4]
     so, oi, osp, oe, si = map(int, a.split())
     orr, ob = map(int, b.split())
-    og, of = map(int, c.split())
+    og, of, occ = map(int, c.split())
     assert og == pp.Opts.gap_theta.offset and of == pp.Opts.gap_fall.offset
+    assert occ == pp.Opts.cluster_ctas.offset
     sp_, osl, obp = map(int, d.split())
     assert sp_ == ctypes.sizeof(pp.Plan) and osl == pp.Plan.slots.offset and obp == pp.Plan.bytes_per_iter.offset
     assert so == ctypes.sizeof(pp.Opts) and oi == pp.Opts.inner_tol.offset

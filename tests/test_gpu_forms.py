@@ -217,6 +217,49 @@ def test_batch_dynamic_schedule_bitwise_equals_solo():
     assert all(i.status == m.OK for i in infos)
 
 
+@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "fp32_ru"])
+def test_batch_mixed_cluster_sizes_bitwise_equal_solo(precision):
+    """Handles whose plans have different cluster sizes (2, 4, 8, 16 and the create-time
+    tuner) in one batch: one launch per size on its own stream; every result is bitwise the
+    solo result on the same handle, and the fixed-k iterate matches the oracle."""
+    m = pp()
+    specs = synth.batch_mix(24, 31, lo=1e3, hi=4e4)
+    systems = [synth.build_spec(sp) for sp in specs]
+    sizes = [(0, 2, 4, 8, 16)[k % 5] for k in range(len(systems))]
+    solvers = [m.Solver.from_csr(a, precision=precision, path=m.PATH_CLUSTER, cluster_ctas=c)
+               for (a, _), c in zip(systems, sizes)]
+    for s, c in zip(solvers, sizes):
+        assert s.plan().ctas in ((2, 4, 8) if c == 0 else (c,))
+    bs = [dev(b) for _, b in systems]
+    xs = [torch.empty_like(b) for b in bs]
+    infos = m.batch_solve(solvers, bs, xs, tol=1e-8, maxit=20000)
+    for k, (s, b) in enumerate(zip(solvers, bs)):
+        x0, i0 = s.solve(b, tol=1e-8, maxit=20000)
+        assert infos[k].status == i0.status == m.OK and infos[k].iters == i0.iters, k
+        assert np.array_equal(xs[k].cpu().numpy(), x0.cpu().numpy()), k
+    if precision == 0:
+        xk = [torch.empty_like(b) for b in bs]
+        m.batch_solve(solvers[:6], bs[:6], xk[:6], tol=0.0, maxit=25)
+        for (a, b), x in zip(systems[:6], xk[:6]):
+            assert rel(x.cpu().numpy(), oracle.pipecg(a, b, tol=0.0, maxit=25)["x"]) <= 1e-10
+    with pytest.raises(m.PPCGError):
+        m.Solver.from_csr(systems[0][0], path=m.PATH_CLUSTER, cluster_ctas=3)
+
+
+def test_cluster_size_tuner_picks_small_clusters_for_small_systems():
+    """The create-time tuner (cluster_ctas = 0) times 2, 4 and 8 CTAs per system: a
+    1,000-row system, bound by its per-iteration barrier and reduction, gets 2; the choice
+    is cached, so a second handle of the same family and size is not timed again."""
+    m = pp()
+    a, _ = synth.build_spec(("varcoeff2d", 32, 5, 6))
+    s1 = m.Solver.from_csr(a, path=m.PATH_CLUSTER, cluster_ctas=0)
+    s2 = m.Solver.from_csr(a, path=m.PATH_CLUSTER, cluster_ctas=0)
+    assert s1.plan().ctas == 2 and s2.plan().ctas == 2
+    assert s2.plan().create_seconds <= s1.plan().create_seconds + 0.05
+    s1.close()
+    s2.close()
+
+
 def test_batch_fixed_k_parity():
     m = pp()
     systems = _batch_systems()[:6]
