@@ -244,6 +244,11 @@ ppcg_status ppcg_last_info(ppcg_handle handle, ppcg_info* info);
  * Each result is bitwise identical to ppcg_solve on the same handle: a system's
  * partition over CTAs and its reduction order depend only on its handle.
  * The handles must be distinct.  Returns after enqueueing; infos valid after stream sync.
+ * CLUSTER-path handles with different cluster sizes (ppcg_opts.cluster_ctas) run one launch
+ * per size, largest first, the later ones on library side streams joined back into
+ * `stream`; ON-CHIP members run on another side stream.  Those side streams and their
+ * events are per device, so calls of ppcg_batch_solve on one device from several host
+ * threads must not overlap.
  */
 ppcg_status ppcg_batch_solve(int32_t count, const ppcg_handle* handles, const double* const* b,
                              const double* const* x0, double* const* x, const double* tol,
