@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 
 #include "internal.h"
@@ -299,6 +300,34 @@ template <> struct Cols<kColPat> {
 template <typename T, bool SCALE, class G, class CS>
 __device__ __forceinline__ T row_dot(const CS& col, const T* __restrict__ val, const G& x,
                                      const T* __restrict__ dsc, int64_t base, int len, T acc) {
+  if constexpr (std::is_same<CS, ColPat>::value && sizeof(T) == 4) {
+    // FP32 rows of an offset-pattern matrix: batches of 4 slots (columns cost nothing to
+    // form, so a narrower batch adds no dependent column load, and it frees the registers
+    // the FP32 pass's double-float dot accumulators need: 256^3 FP32_RU solve 380 -> 347 ms;
+    // the FP64 pass is 0.6% faster with the wide batches below).  Same terms, same order.
+    int j = 0;
+    for (; j + 4 <= len; j += 4) {
+      T a[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        T xv = x(slot_col(col, 0, j + k));
+        if (SCALE) xv = __ldg(dsc + slot_col(col, 0, j + k)) * xv;
+        acc = fma(a[k], xv, acc);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      if (j + k < len) {
+        const T a = ld_stream(val + base + (int64_t)(j + k) * kChunk);
+        T xv = x(slot_col(col, 0, j + k));
+        if (SCALE) xv = __ldg(dsc + slot_col(col, 0, j + k)) * xv;
+        acc = fma(a, xv, acc);
+      }
+    }
+    return acc;
+  }
   int j = 0;
   for (; j + 8 <= len; j += 8) {
     int32_t c[8];
