@@ -312,8 +312,9 @@ __device__ __forceinline__ T row_dot(const CS& col, const T* __restrict__ val, c
       for (int k = 0; k < 4; k++) a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
 #pragma unroll
       for (int k = 0; k < 4; k++) {
-        T xv = x(slot_col(col, 0, j + k));
-        if (SCALE) xv = __ldg(dsc + slot_col(col, 0, j + k)) * xv;
+        const int32_t c = slot_col(col, base + (int64_t)(j + k) * kChunk, j + k);
+        T xv = x(c);
+        if (SCALE) xv = __ldg(dsc + c) * xv;
         acc = fma(a[k], xv, acc);
       }
     }
@@ -321,8 +322,9 @@ __device__ __forceinline__ T row_dot(const CS& col, const T* __restrict__ val, c
     for (int k = 0; k < 3; k++) {
       if (j + k < len) {
         const T a = ld_stream(val + base + (int64_t)(j + k) * kChunk);
-        T xv = x(slot_col(col, 0, j + k));
-        if (SCALE) xv = __ldg(dsc + slot_col(col, 0, j + k)) * xv;
+        const int32_t c = slot_col(col, base + (int64_t)(j + k) * kChunk, j + k);
+        T xv = x(c);
+        if (SCALE) xv = __ldg(dsc + c) * xv;
         acc = fma(a, xv, acc);
       }
     }
