@@ -583,9 +583,11 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
     if (const char* e = getenv("PPCG_GRID_SHAPE")) k = atoi(e);
     if (k < 0 || k >= nshapes) k = 0;
     h->shape = box ? grid_box_shape_first() + k : k;
-    // the offset pattern or the column dictionary, where the matrix has one, on the default shape
-    if (!box && k == 0 && h->A.pat_k > 0) h->shape = grid_pat_shape();
-    else if (!box && k == 0 && h->A.cidx) h->shape = grid_dict_shape();
+    // the offset pattern or the column dictionary, where the matrix has one, on the default
+    // shape of the handle's precision
+    if (!box && k == 0)
+      h->shape = grid_default_shape(h->A.pat_k > 0 ? PPCG_COLS_PATTERN : h->A.cidx ? PPCG_COLS_DICT : PPCG_COLS_SELL,
+                                    h->opts.precision != PPCG_FP64);
     // One CTA per SM at most for small systems: enough warps for one 32-row chunk each,
     // so the grid barrier spans only the CTAs that have rows to work on.
     const int full = grid_blocks_for_device(h->device, h->shape);
@@ -695,9 +697,8 @@ ppcg_status ppcg_plan_info(ppcg_handle h, ppcg_plan* out) {
   // valid SELL matrix: the cluster and on-chip kernels read its stored columns)
   const bool grid = h->path == PPCG_PATH_GRID;
   out->columns = h->box_g > 0                                ? PPCG_COLS_MATRIX_FREE
-                 : grid && h->shape == grid_pat_shape()  ? PPCG_COLS_PATTERN
-                 : grid && h->shape == grid_dict_shape() ? PPCG_COLS_DICT
-                                                         : PPCG_COLS_SELL;
+                 : grid                                     ? grid_shape_cols(h->shape)
+                                                            : PPCG_COLS_SELL;
   out->sigma = h->sell.sigma;
   out->pattern_k = h->A.pat_k;
   out->dict_size = h->sell.col_dict;

@@ -145,8 +145,10 @@ bool onchip_cluster_fits(int nc, size_t smem);                      // can one s
 int grid_shape_count();        // SELL/CSR plans: shapes [0, grid_shape_count())
 int grid_box_shape_first();    // matrix-free box plans: shapes first + [0, count)
 int grid_box_shape_count();
-int grid_dict_shape();         // the default SELL shape reading the column dictionary
-int grid_pat_shape();          // the default SELL shape forming columns from the offset pattern
+// The default SELL shape for a column source (PPCG_COLS_SELL, PPCG_COLS_DICT or
+// PPCG_COLS_PATTERN) and precision (the FP32 forms run more warps per CTA).
+int grid_default_shape(int cols, bool fp32);
+int grid_shape_cols(int shape);   // the column source (PPCG_COLS_*) a SELL shape's kernel reads
 int grid_threads(int shape);
 int grid_blocks_for_device(int device, int shape);
 int max_active_clusters(int device, int cs = 8);   // 0 when clusters of cs CTAs cannot run

@@ -1807,6 +1807,14 @@ __device__ void box_stage_x(const SysDesc& S, const Lanes& L, int slot_a, int sl
 struct BoxMarch {
   int32_t nseg, len;
 };
+// The group's warps in CTA-interleaved order (warp w of CTA r -> w * ranks + r), so that
+// when the marching items fill only part of the group the idle warps are spread over every
+// SM instead of being the last CTAs' (185^3: 136,900 items for 151,552 threads; with the
+// plain order ~15 SMs had no work in the marching stages).
+__device__ __forceinline__ int64_t box_item0(const Lanes& L) {
+  const int32_t nw = (int32_t)(blockDim.x >> 5), r = L.gw / nw, w = L.gw - r * nw;
+  return ((int64_t)w * (L.W / nw) + r) * 32 + L.lane;
+}
 __device__ __forceinline__ BoxMarch box_march(int32_t g, int32_t threads) {
   const int32_t plane = g * g;
   int32_t nseg = min((g + 7) / 8, threads / plane);
@@ -1834,7 +1842,7 @@ __device__ void box_stage_y(const SysDesc& S, const Lanes& L, bool two) {
   const int32_t plane = g * g;
   const BoxMarch m = box_march(g, L.W * 32);
   const int32_t items = m.nseg * plane;
-  for (int64_t t = (int64_t)L.gw * 32 + L.lane; t < items; t += (int64_t)L.W * 32) {
+  for (int64_t t = box_item0(L); t < items; t += (int64_t)L.W * 32) {
     const int32_t seg = (int32_t)(t / plane), rem = (int32_t)(t - (int64_t)seg * plane);
     const int32_t z = rem / g, x = rem - z * g;
     const int32_t y0 = seg * m.len, y1 = min(g, y0 + m.len);
@@ -1961,7 +1969,7 @@ __device__ bool box_pass(const SysDesc& S, const Ctl& C, const Lanes& L, Dots<do
       const double* t2 = S.box_t + 2 * (int64_t)n;
       const BoxMarch m = box_march(g, L.W * 32);
       const int32_t items = m.nseg * plane;
-      for (int64_t t = (int64_t)L.gw * 32 + L.lane; t < items; t += (int64_t)L.W * 32) {
+      for (int64_t t = box_item0(L); t < items; t += (int64_t)L.W * 32) {
         const int32_t seg = (int32_t)(t / plane), rem = (int32_t)(t - (int64_t)seg * plane);
         const int32_t z0 = seg * m.len, z1 = min(g, z0 + m.len);
         int32_t row = z0 * plane + rem;
@@ -2246,12 +2254,19 @@ const GridShape kGridShapes[] = {
     {k_grid<1024, 1, false, true>, 1024, 0},
     {k_grid<512, 2, false, false, kColDict>, 512, 0},
     {k_grid<512, 2, false, false, kColPat>, 512, 0},
+    // The FP32 forms' defaults: 20 warps per CTA at 48 registers (more spilling, more
+    // warps in flight for the latency-bound FP32 passes: 256^3 stencil FP32_RU 2.6% and
+    // 4M-point graph 6% faster than at 512 threads, where FP64 was 1-4% slower).
+    {k_grid<640, 2, false>, 640, 0},
+    {k_grid<640, 2, false, false, kColDict>, 640, 0},
+    {k_grid<640, 2, false, false, kColPat>, 640, 0},
 };
 constexpr int kNumGridShapes = (int)(sizeof(kGridShapes) / sizeof(kGridShapes[0]));
 constexpr int kFirstBoxShape = 9;
 constexpr int kDictShape = 12;   // the default shape with the column dictionary
 constexpr int kPatShape = 13;    // the default shape with the offset pattern
-static_assert(kPatShape == kNumGridShapes - 1, "the pattern kernel is the last shape");
+constexpr int kF32Shape = 14;    // the FP32 defaults: stored columns, dictionary, pattern
+static_assert(kF32Shape + 3 == kNumGridShapes, "the FP32 defaults are the last shapes");
 
 // Cluster path.  Static schedule (next == nullptr): cluster c runs list[list_ptr[c] ..
 // list_ptr[c + 1]).  Dynamic schedule: every cluster takes the next entry of list (ordered
@@ -2643,8 +2658,15 @@ __global__ void k_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, in
 int grid_shape_count() { return kFirstBoxShape; }
 int grid_box_shape_first() { return kFirstBoxShape; }
 int grid_box_shape_count() { return kDictShape - kFirstBoxShape; }
-int grid_dict_shape() { return kDictShape; }
-int grid_pat_shape() { return kPatShape; }
+int grid_default_shape(int cols, bool fp32) {
+  const int c = cols == PPCG_COLS_PATTERN ? 2 : cols == PPCG_COLS_DICT ? 1 : 0;
+  return fp32 ? kF32Shape + c : c == 2 ? kPatShape : c == 1 ? kDictShape : 0;
+}
+int grid_shape_cols(int shape) {
+  if (shape == kPatShape || shape == kF32Shape + 2) return PPCG_COLS_PATTERN;
+  if (shape == kDictShape || shape == kF32Shape + 1) return PPCG_COLS_DICT;
+  return PPCG_COLS_SELL;
+}
 int grid_threads(int shape) { return kGridShapes[shape].threads; }
 
 cudaError_t ensure_smem_attr(const void* fn, size_t bytes);
