@@ -402,14 +402,22 @@ def measure_serving(pp, nreq=160, hi=2e5, seed=5, rate_factors=(0.5,), buckets=2
     return out
 
 
-def measure_rgg(pp, torch, npts=4_000_000, seed=3):
+def measure_rgg(pp, torch, npts=4_000_000, seed=3, profile_iters=0):
     """Random geometric graph Laplacian (expected degree 14) + 1e-3 I: FP32_RU and FP32_IR to
     1e-8 and FP64 to 1e-8 and 1e-10, time to solution and each result's error against the
-    FP64 1e-10 solution."""
+    FP64 1e-10 solution.  profile_iters > 0: a single FP64 solve stopped after that many
+    iterations instead (one short launch of the solve kernel for a profiler)."""
     radius = (3 * 14.0 / (4 * np.pi * npts)) ** (1 / 3)
     a = synth.rgg_laplacian(npts, radius, 1e-3, seed)
     b = torch.from_numpy(synth.rhs_uniform(a.n, seed)).cuda()
     out = {"workload": f"RGG Laplacian {npts} points, radius {radius:.6f}, shift 1e-3", "N": a.n, "nnz": a.nnz}
+    if profile_iters > 0:
+        s = pp.Solver.from_csr(a)
+        _, info = s.solve(b, None, None, tol=1e-8, maxit=profile_iters)
+        s.close()
+        out["profile_solve"] = {"iters": info.iters, "status": pp.status_name(info.status),
+                                "kernel_s": info.seconds}
+        return out
     runs = {}
     for name, prec, tol in (("fp64_1e-10", pp.FP64, 1e-10), ("fp64_1e-8", pp.FP64, 1e-8),
                             ("fp32_ru_1e-8", pp.FP32_RU, 1e-8), ("fp32_ir_1e-8", pp.FP32_IR, 1e-8)):
@@ -598,6 +606,9 @@ def main():
                          "paper: the paper's stopping rule and exact solution on every config; "
                          "box125: Table II's 125-point family; latency: the 64^2 solve latency")
     ap.add_argument("--batch-count", type=int, default=1024)
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="rgg mode: one FP64 solve stopped after this many iterations (a short "
+                         "kernel launch to capture with a profiler) instead of the figures")
     ap.add_argument("--box-sizes", type=int, nargs="+", default=[165, 170, 181, 185],
                     help="grid sides of the box125 mode (default: Table II's four)")
     args = ap.parse_args()
@@ -610,7 +621,7 @@ def main():
         import paper_2105_06176_b300 as pp
         torch.cuda.set_device(local)
         if args.mode == "rgg":
-            res = {"mode": "rgg", "rgg": measure_rgg(pp, torch)}
+            res = {"mode": "rgg", "rgg": measure_rgg(pp, torch, profile_iters=args.profile_iters)}
         elif args.mode == "box125":
             res = {"mode": "box125", "box125": measure_box125(pp, torch, sizes=tuple(args.box_sizes))}
         elif args.mode == "paper":

@@ -466,24 +466,25 @@ ppcg_status convert_csr_to_sell(int64_t n, int64_t nnz, const int64_t* d_rp, con
   }
 
   // sigma autotune.  Sorting rows by length within a window of sigma > C rows cuts the
-  // padding, but it also scatters the rows of a chunk over the window, so the 32 lanes of
-  // a warp gather from unrelated rows and every gathered value costs its own L2 sector.
-  // Model per iteration: padded slots x (value + column bytes) + a gather penalty per
-  // off-diagonal nonzero of 16 bytes of HBM traffic at sigma = 2048 and 0.65 of that at
-  // sigma = 256 (both measured on a random-geometric-graph Laplacian, where sigma = 1 ran
-  // 17% (FP64) and 27% (FP32) faster than the padding-optimal sigma = 2048 despite 57%
-  // padding).  The smallest-cost window wins.
+  // padding (and with it the padded slots' bytes and FMAs), but it also scatters the rows of
+  // a chunk over the window, so the 32 lanes of a warp gather from less related rows and the
+  // gathers touch more L1/L2 sectors.  Model per iteration: padded slots x (value + column
+  // bytes) + a gather penalty per off-diagonal nonzero, in bytes of equivalent HBM traffic:
+  // 1.4 at sigma = 64, 3.0 at 128, 4.2 at 256 (fitted to the FP64 and FP32_RU solve times of
+  // a 4M-point random-geometric-graph Laplacian, 14.9 nonzeros per row: padding 52% / 30% /
+  // 17% / 9%, FP64 289 / 278 / 279 / 280 ms, FP32_RU 235 / 229 / 235 / 247 ms) and 16 at
+  // 2048 (where sigma = 1 had run 17% (FP64) and 27% (FP32) faster).  The smallest cost wins.
   int64_t sigma = sigma_req;
   if (!pat.empty()) {
     sigma = 1;
   } else if (sigma_req <= 0) {
-    const int64_t cands[] = {1, 256, 2048};
-    const double penalty[] = {0.0, 0.65 * 16.0, 16.0};
+    const int64_t cands[] = {1, 64, 128, 256, 2048};
+    const double penalty[] = {0.0, 1.4, 3.0, 4.2, 16.0};
     const double slot_bytes = want_fp32 ? 8.0 : 12.0;
     int64_t offdiag = 0;
     for (int64_t i = 0; i < n; i++) offdiag += len[i];
     double best = 0.0;
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < 5; k++) {
       const double cost = (double)sell_slots(len, cands[k], nullptr, nullptr) * slot_bytes + penalty[k] * (double)offdiag;
       if (k == 0 || cost < best) { best = cost; sigma = cands[k]; }
     }

@@ -84,7 +84,7 @@ def test_fixed_k_parity(name, k, opts):
     assert rel(x, ref["x"]) <= 1e-10
 
 
-@pytest.mark.parametrize("sigma", [256, 2048])
+@pytest.mark.parametrize("sigma", [64, 256, 2048])
 @pytest.mark.parametrize("opts", PATHS, ids=["grid", "cluster"])
 def test_sorted_sell_parity(sigma, opts):
     """Rows sorted by length inside sigma-row windows: the solver runs on the permuted
