@@ -126,9 +126,10 @@ class ClockSampler:
 
 
 def profiled_traffic(bytes_iter, iters_per_launch):
-    """DRAM bytes per launch from the committed ncu capture of the solve kernel, scaled from
-    the captured grid to this one by algorithmic bytes; None once the kernel source has
-    changed since the capture."""
+    """DRAM bytes per launch from the committed ncu capture of the solve kernel on this
+    workload (the capture's bytes per iteration times this launch's iterations); None once
+    the kernel source has changed since the capture, or for another grid size (the L2 serves
+    a roughly fixed amount per pass, so traffic does not scale with the algorithmic bytes)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "k_grid_traffic.json")) as f:
@@ -139,8 +140,10 @@ def profiled_traffic(bytes_iter, iters_per_launch):
         return None, "no capture"
     if rec.get("kernel_source_sha256") != sha:
         return None, "kernel changed since the last capture"
-    return rec["dram_over_balg"] * bytes_iter * iters_per_launch, \
-        f"ncu capture on {rec['workload']} scaled by algorithmic bytes"
+    if rec.get("b_alg_per_iter") != bytes_iter:
+        return None, "captured on another grid size"
+    return rec["dram_bytes_per_launch"] / rec["iterations"] * iters_per_launch, \
+        f"ncu capture: {rec['workload']}"
 
 
 def dist_setup():

@@ -584,10 +584,13 @@ ppcg_status ppcg_create(ppcg_handle* handle, int64_t n, int64_t nnz, const int64
     if (k < 0 || k >= nshapes) k = 0;
     h->shape = box ? grid_box_shape_first() + k : k;
     // the offset pattern or the column dictionary, where the matrix has one, on the default
-    // shape of the handle's precision
+    // shape of the handle's precision; FP64 systems whose vector block exceeds half the L2
+    // (so the row's own entries are not in L2 from the previous pass) get the pattern
+    // kernel that prefetches them
+    const bool streaming = (double)h->A.nchunks * kChunk * kSlots64 * sizeof(double) > 64.0 * 1024 * 1024;
     if (!box && k == 0)
       h->shape = grid_default_shape(h->A.pat_k > 0 ? PPCG_COLS_PATTERN : h->A.cidx ? PPCG_COLS_DICT : PPCG_COLS_SELL,
-                                    h->opts.precision != PPCG_FP64);
+                                    h->opts.precision != PPCG_FP64, streaming);
     // One CTA per SM at most for small systems: enough warps for one 32-row chunk each,
     // so the grid barrier spans only the CTAs that have rows to work on.
     const int full = grid_blocks_for_device(h->device, h->shape);

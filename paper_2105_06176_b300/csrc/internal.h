@@ -147,7 +147,8 @@ int grid_box_shape_first();    // matrix-free box plans: shapes first + [0, coun
 int grid_box_shape_count();
 // The default SELL shape for a column source (PPCG_COLS_SELL, PPCG_COLS_DICT or
 // PPCG_COLS_PATTERN) and precision (the FP32 forms run more warps per CTA).
-int grid_default_shape(int cols, bool fp32);
+// streaming: the system's FP64 vector block exceeds half the L2 (the own-entry prefetch pays)
+int grid_default_shape(int cols, bool fp32, bool streaming);
 int grid_shape_cols(int shape);   // the column source (PPCG_COLS_*) a SELL shape's kernel reads
 int grid_threads(int shape);
 int grid_blocks_for_device(int device, int shape);

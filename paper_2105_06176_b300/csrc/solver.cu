@@ -301,9 +301,55 @@ template <> struct Cols<kColPat> {
 // acc + sum_j val[slot_j] * x(col[slot_j]) (* dsc[col] when SCALE) over the row's
 // off-diagonal slots base + j*32, j < len, in CSR order; acc enters holding the diagonal
 // term.  CS: the column source (const int32_t* or ColDict).
+// FP64 rows with stored columns: batches of 8 slots, the next batch's columns loaded before
+// the current batch's gathers, so a column load no longer waits behind the gathers of the
+// batch before it (4M-point graph FP64 solve 2.5% faster; the FP32 pass, whose accumulators
+// take more registers, ran 3% slower, and 12-slot batches 8% slower).  Same terms in the
+// same order as row_dot.
+template <typename T, class G>
+__device__ __forceinline__ T row_dot_cols(const int32_t* __restrict__ col, const T* __restrict__ val, const G& x,
+                                          int64_t base, int len, T acc) {
+  int j = 0;
+  int32_t cn[8];
+  if (len >= 8) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) cn[k] = ld_stream(col + base + (int64_t)k * kChunk);
+  }
+  for (; j + 8 <= len; j += 8) {
+    int32_t c[8];
+    T a[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      c[k] = cn[k];
+      a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
+    }
+    if (j + 16 <= len) {
+#pragma unroll
+      for (int k = 0; k < 8; k++) cn[k] = ld_stream(col + base + (int64_t)(j + 8 + k) * kChunk);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) acc = fma(a[k], x(c[k]), acc);
+  }
+  int32_t c[7];
+  T a[7];
+#pragma unroll
+  for (int k = 0; k < 7; k++) {
+    if (j + k < len) {
+      c[k] = ld_stream(col + base + (int64_t)(j + k) * kChunk);
+      a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 7; k++)
+    if (j + k < len) acc = fma(a[k], x(c[k]), acc);
+  return acc;
+}
+
 template <typename T, bool SCALE, class G, class CS>
 __device__ __forceinline__ T row_dot(const CS& col, const T* __restrict__ val, const G& x,
                                      const T* __restrict__ dsc, int64_t base, int len, T acc) {
+  if constexpr (std::is_same<CS, const int32_t*>::value && !SCALE && sizeof(T) == 8)
+    return row_dot_cols(col, val, x, base, len, acc);
   if constexpr (std::is_same<CS, ColPat>::value && sizeof(T) == 4) {
     // FP32 rows of an offset-pattern matrix: batches of 4 slots (columns cost nothing to
     // form, so a narrower batch adds no dependent column load, and it frees the registers
@@ -565,26 +611,38 @@ __device__ __forceinline__ void pass_setup2(const DevMatrix& A, const View<T, NS
 // product (see after()); with stored columns, beside the gathers.
 template <typename T, int NS, bool FIRST, int CM = kColA>
 __device__ __forceinline__ void pass_iter(const DevMatrix& A, const View<T, NS>& V, const Lanes& L, Dots<T>& d,
-                                          T alpha, T beta, int k, bool paper_norm, bool with_rr = true) {
+                                          T alpha, T beta, int k, bool paper_norm, bool with_rr = true,
+                                          bool pf_own = false) {
   const int wcs = (k & 1) ? V_WB : V_WA;
   const int wns = (k & 1) ? V_WA : V_WB;
   const GatherSlot<T, NS> gw{V.v.b + wcs * kChunk};
   const T* __restrict__ val = V.val;
   const int32_t n = (int32_t)A.n;
-  FOR_CHUNKS(A, L) {
+  // Odd iterations walk each warp's chunks in reverse, so a pass starts on the chunks the
+  // previous pass wrote last, whose lines are still in L2 (the ramp-up after the barrier
+  // reads from L2 instead of DRAM).  256^3 FP64 solve 0.5%, FP32_RU 1.7%, 4M-point graph
+  // FP64 2.6% per iteration faster.  The per-lane dot partials then sum in another order
+  // on odd iterations: FP64 iterates change by rounding only.
+  const int32_t nch = (int32_t)A.nchunks;
+  const int32_t cnt = L.gw < nch ? (nch - 1 - L.gw) / L.W + 1 : 0;
+  const bool rev = (k & 1) != 0;
+  for (int32_t ci = 0; ci < cnt; ci++) {
+    const int32_t c = L.gw + (rev ? cnt - 1 - ci : ci) * L.W;
     // FP32 only: the FP32 pass is latency-bound (half the bytes in flight of FP64 at the
     // same occupancy), 433 -> 350 us per 256^3 iteration; the FP64 pass, already near the
     // HBM and FP64-pipe limits, ran 10-20% slower with it.
-    if (PPCG_PREFETCH && sizeof(T) == 4 && c + L.W < (int32_t)A.nchunks)
-      prefetch_chunk<T, NS>(A.cptr, A.col, CM == kColDict ? A.cidx : nullptr, val, V.v.b, c + L.W, L.lane,
-                            CM == kColPat ? A.pat_k : 0);
+    if (PPCG_PREFETCH && sizeof(T) == 4 && ci + 1 < cnt)
+      prefetch_chunk<T, NS>(A.cptr, A.col, CM == kColDict ? A.cidx : nullptr, val, V.v.b, rev ? c - L.W : c + L.W,
+                            L.lane, CM == kColPat ? A.pat_k : 0);
     int64_t base; int len;
     chunk_slots<CM>(A, c, L.lane, base, len);
     if (CM == kColA) prefetch_rest(A.col, val, base - L.lane, len, L.lane);
     // Stencils (the row's own entries are loaded after the product, see after()): an L2
     // prefetch of the chunk's eight own-entry slots (not the two w slots) at the start of the
-    // chunk, so those loads find their lines in L2.  256^3 FP64 solve 611 -> 606 ms.
-    if (CM == kColPat && sizeof(T) == 8 && L.lane < 16) {
+    // chunk, so those loads find their lines in L2.  256^3 FP64 solve 611 -> 606 ms.  Only
+    // for systems whose vectors do not stay in L2 between passes (pf_own): on small ones
+    // the instructions only lengthen the chain (64^2 cluster solve 1.55 -> 1.71 ms).
+    if (CM == kColPat && sizeof(T) == 8 && pf_own && L.lane < 16) {
       const int sl = L.lane >> 1;   // slots r u (z q s p x invd): 0 1 4 .. 9
       const char* line = reinterpret_cast<const char*>(V.v.chunk(c, 0)) + (sl < 2 ? sl : sl + 2) * (kChunk * 8) +
                          (L.lane & 1) * 128;
@@ -2086,7 +2144,8 @@ constexpr int kSmGrid = 3 * 32, kSmCluster = 3 * 32 * (kClusterThreads / 32);
 // passes read the column dictionary (a plan without one ends with PPCG_ERR_ARG); kColPat:
 // every SELL pass forms its columns from the offset pattern (a plan without one ends with
 // PPCG_ERR_ARG).  A pattern matrix is also a valid SELL matrix, so kColA kernels run it too.
-template <bool STAGED, bool BOX = false, int CM = kColA, class G, class Shared>
+// PF: the FP64 iteration pass prefetches each chunk's own entries into L2 (see pass_iter).
+template <bool STAGED, bool BOX = false, int CM = kColA, bool PF = false, class G, class Shared>
 __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsigned char* stage_mem,
                            uint64_t* stage_bars, unsigned& phases) {
   __syncthreads();   // previous system's readers of sh are done
@@ -2170,8 +2229,8 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
             if (C.first) pass_iter_staged<double, kNS64, true>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, wst, bars, phases, S.err);
             else pass_iter_staged<double, kNS64, false>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, wst, bars, phases, S.err);
           } else {
-            if (C.first) pass_iter<double, kNS64, true, CM>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
-            else pass_iter<double, kNS64, false, CM>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0);
+            if (C.first) pass_iter<double, kNS64, true, CM>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0, PF);
+            else pass_iter<double, kNS64, false, CM>(S.A, V, L, d, C.alpha, C.beta, C.iter, paper, C.want_rr != 0, PF);
           }
           break;
         case P_TRUE: pass_true<kNS64, V_X, CMO>(S, L, d); break;
@@ -2246,7 +2305,7 @@ __device__ void run_system(G& g, const SysDesc* Sg, int budget, Shared& sh, unsi
   }
 }
 
-template <int THREADS, int MINB, bool STAGED, bool BOX = false, int CM = kColA>
+template <int THREADS, int MINB, bool STAGED, bool BOX = false, int CM = kColA, bool PF = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_grid(const SysDesc* d, int budget) {
   __shared__ SharedT<kSmGrid> sh;
   __shared__ uint64_t bars[2 * (THREADS / 32)];
@@ -2261,7 +2320,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_grid(const SysDesc* d, int bu
     __syncthreads();
   }
   GridGroup g{d->bar, d->err, (long long)d->spin_limit_ns, 0u};
-  run_system<STAGED, BOX, CM>(g, d, budget, sh, stage_mem, bars, phases);
+  run_system<STAGED, BOX, CM, PF>(g, d, budget, sh, stage_mem, bars, phases);
 }
 
 // Launch shapes of the grid path: (threads per CTA, minimum CTAs per SM for the register
@@ -2290,13 +2349,18 @@ const GridShape kGridShapes[] = {
     {k_grid<640, 2, false>, 640, 0},
     {k_grid<640, 2, false, false, kColDict>, 640, 0},
     {k_grid<640, 2, false, false, kColPat>, 640, 0},
+    // The offset-pattern default with the own-entry prefetch: FP64 systems whose vectors
+    // exceed half the L2 (the prefetch code in the other kernel made small solves up to 7%
+    // slower even when skipped).
+    {k_grid<512, 2, false, false, kColPat, true>, 512, 0},
 };
 constexpr int kNumGridShapes = (int)(sizeof(kGridShapes) / sizeof(kGridShapes[0]));
 constexpr int kFirstBoxShape = 9;
 constexpr int kDictShape = 12;   // the default shape with the column dictionary
 constexpr int kPatShape = 13;    // the default shape with the offset pattern
 constexpr int kF32Shape = 14;    // the FP32 defaults: stored columns, dictionary, pattern
-static_assert(kF32Shape + 3 == kNumGridShapes, "the FP32 defaults are the last shapes");
+constexpr int kPatPfShape = 17;  // the offset-pattern default with the own-entry prefetch
+static_assert(kPatPfShape + 1 == kNumGridShapes, "the prefetching pattern kernel is the last shape");
 
 // Cluster path.  Static schedule (next == nullptr): cluster c runs list[list_ptr[c] ..
 // list_ptr[c + 1]).  Dynamic schedule: every cluster takes the next entry of list (ordered
@@ -2688,12 +2752,12 @@ __global__ void k_barrier_selftest(unsigned* bar, int32_t* err, int32_t* out, in
 int grid_shape_count() { return kFirstBoxShape; }
 int grid_box_shape_first() { return kFirstBoxShape; }
 int grid_box_shape_count() { return kDictShape - kFirstBoxShape; }
-int grid_default_shape(int cols, bool fp32) {
+int grid_default_shape(int cols, bool fp32, bool streaming) {
   const int c = cols == PPCG_COLS_PATTERN ? 2 : cols == PPCG_COLS_DICT ? 1 : 0;
-  return fp32 ? kF32Shape + c : c == 2 ? kPatShape : c == 1 ? kDictShape : 0;
+  return fp32 ? kF32Shape + c : c == 2 ? (streaming ? kPatPfShape : kPatShape) : c == 1 ? kDictShape : 0;
 }
 int grid_shape_cols(int shape) {
-  if (shape == kPatShape || shape == kF32Shape + 2) return PPCG_COLS_PATTERN;
+  if (shape == kPatShape || shape == kPatPfShape || shape == kF32Shape + 2) return PPCG_COLS_PATTERN;
   if (shape == kDictShape || shape == kF32Shape + 1) return PPCG_COLS_DICT;
   return PPCG_COLS_SELL;
 }
