@@ -398,9 +398,17 @@ def measure_serving(pp, nreq=160, hi=2e5, seed=5, rate_factors=(0.5,), buckets=2
         arr = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
         arr -= arr[0]
         lat, wall, st = run_server(pp, reqs, arr)
-        out["rates"].append({"rate_factor": f, "offered_per_s": rate, "solves_per_s": len(reqs) / wall,
-                             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                             "all_ok": all(s == pp.OK for s in st)})
+        entry = {"rate_factor": f, "offered_per_s": rate, "solves_per_s": len(reqs) / wall,
+                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                 "all_ok": all(s == pp.OK for s in st)}
+        # the same split by the path the server gives a request: up to 131,072 rows on
+        # thread-block clusters (all advance in every epoch), larger ones on the whole GPU
+        lat_a, rows = np.asarray(lat), np.array([a.n for a, _ in reqs])
+        for key, sel in (("cluster_path_requests", rows <= 131072), ("grid_path_requests", rows > 131072)):
+            if sel.any():
+                entry[key] = {"count": int(sel.sum()), "p50_s": float(np.percentile(lat_a[sel], 50)),
+                              "p99_s": float(np.percentile(lat_a[sel], 99))}
+        out["rates"].append(entry)
         print(json.dumps({"progress": out["rates"][-1]}), file=sys.stderr, flush=True)
     return out
 

@@ -292,16 +292,21 @@ ppcg_status ppcg_plan_info(ppcg_handle handle, ppcg_plan* plan);
 void ppcg_destroy(ppcg_handle handle);
 
 /*
- * Continuous-batching server.  A background thread admits queued requests while their
- * device footprint fits in hbm_budget bytes (0 = 90% of free HBM at creation), keeps each
- * admitted request's vectors and scalars resident on the device, and advances all
- * resident requests together in epochs of a bounded number of iterations, so requests
- * that arrive while others run join at the next epoch.  opts may be NULL.  With
- * opts->path == PPCG_PATH_AUTO and the default cluster_max_rows, requests of up to 131,072
- * rows run on the CLUSTER path (all of them share one launch per epoch) and larger ones on
- * the GRID path (the two oldest advance each epoch by a slice of about 20 ms); the ONCHIP
- * path is not used by the server.  A solve's result equals ppcg_solve on a handle created
- * with the same options and that path.
+ * Continuous-batching server.  Admission runs on two background threads, one for requests
+ * of up to cluster_max_rows rows and one for larger ones.  Each takes its requests in
+ * arrival order while their device footprint fits in hbm_budget bytes (0 = 90% of free HBM
+ * at creation); an older request of the other class that is waiting for memory keeps its
+ * turn.  Admitted requests keep their vectors and scalars resident on the device and
+ * advance together in epochs of a bounded number of iterations, so requests that arrive
+ * while others run join at the next epoch.  opts may be NULL.  With opts->path ==
+ * PPCG_PATH_AUTO and the default cluster_max_rows, requests of up to 131,072 rows run on
+ * the CLUSTER path (all of them share one launch per epoch) and larger ones on the GRID
+ * path (the two oldest advance each epoch by a slice of about 20 ms); the ONCHIP path is
+ * not used by the server.  Each epoch runs the cluster launch first and then those slices.
+ * A small request therefore never waits for a large solve to finish, nor for the copy and
+ * conversion of a large request's matrix: once admitted, it waits at most for the slices
+ * of the epoch in progress.  A solve's result equals ppcg_solve on a handle created with
+ * the same options and that path.
  */
 ppcg_status ppcg_server_create(ppcg_server* server, size_t hbm_budget, const ppcg_opts* opts);
 

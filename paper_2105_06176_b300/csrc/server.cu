@@ -1,9 +1,13 @@
 // Continuous-batching solve server (ppcg_server_* in include/ppcg.h).
 //
-// Two host threads share one device:
-//   admitter  -- takes queued requests in arrival order while their device footprint fits
-//                in the HBM budget, builds the handle (CSR -> SELL on the device), stages b
-//                and x0, and hands the resident solve to the executor;
+// Three host threads share one device:
+//   admitters -- one for requests the cluster path takes (up to cluster_max_rows rows), one
+//                for larger ones; each takes its class's queued requests in arrival order
+//                while their device footprint fits in the HBM budget (an older request of
+//                the other class that is waiting for memory keeps its turn), builds the
+//                handle (CSR -> SELL on the device) on its own stream, stages b and x0, and
+//                hands the resident solve to the executor, so a small request is never
+//                queued behind the matrix conversion of a large one;
 //   executor  -- runs epochs: every resident CLUSTER-path solve (up to 131,072 rows)
 //                advances inside one persistent cluster launch by its own budget,
 //                epoch_iters * 131072 / n iterations (clamped to [2, 64 epoch_iters]), so
@@ -78,8 +82,8 @@ struct ppcg_srv {
   uint64_t next_ticket = 1;
   bool stop = false;
   int64_t completed = 0, running = 0;
-  std::thread admitter, executor;
-  cudaStream_t s_admit = nullptr, s_exec = nullptr;
+  std::thread admitter[2], executor;
+  cudaStream_t s_admit[2] = {nullptr, nullptr}, s_exec = nullptr;
   // executor scratch for cluster epochs
   SysDesc* d_descs = nullptr;
   int32_t* d_lists = nullptr;
@@ -95,18 +99,34 @@ void finish(ppcg_srv* S, uint64_t ticket, Result&& r) {
   S->completed++;
 }
 
-void admit_loop(ppcg_srv* S) {
+// Admission class of a request: 0 = the cluster path's sizes, 1 = larger.
+int admit_class(const ppcg_srv* S, const Request& r) { return r.n <= S->opts.cluster_max_rows ? 0 : 1; }
+
+// Index of the request admitter `cls` may take now, or -1: the oldest queued request of its
+// class, if it fits the budget and no older request (of the other class) is waiting for
+// memory.  Called with S->mu held.
+long next_admissible(const ppcg_srv* S, int cls) {
+  for (size_t i = 0; i < S->queue.size(); i++) {
+    const Request& r = *S->queue[i];
+    const bool fits = S->in_use + r.footprint <= S->budget;
+    if (admit_class(S, r) == cls) return fits ? (long)i : -1;
+    if (!fits) return -1;
+  }
+  return -1;
+}
+
+void admit_loop(ppcg_srv* S, int cls) {
   cudaSetDevice(S->device);
+  cudaStream_t stream = S->s_admit[cls];
   for (;;) {
     std::unique_ptr<Request> req;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv_admit.wait(lk, [&] {
-        return S->stop || (!S->queue.empty() && S->in_use + S->queue.front()->footprint <= S->budget);
-      });
+      long idx = -1;
+      S->cv_admit.wait(lk, [&] { return S->stop || (idx = next_admissible(S, cls)) >= 0; });
       if (S->stop) return;
-      req = std::move(S->queue.front());
-      S->queue.pop_front();
+      req = std::move(S->queue[(size_t)idx]);
+      S->queue.erase(S->queue.begin() + idx);
       S->in_use += req->footprint;
       S->running++;
     }
@@ -120,17 +140,17 @@ void admit_loop(ppcg_srv* S) {
     // one cluster size for every served solve: an epoch is one launch of clusters
     o.cluster_ctas = kClusterSize;
     ppcg_status st = ppcg_create(&h, req->n, req->nnz, req->rp.data(), req->col.data(), req->val.data(), &o,
-                                 S->s_admit);
+                                 stream);
     Slot slot;
     slot.ticket = req->ticket;
     slot.footprint = req->footprint;
     if (st == PPCG_OK && req->n > 0) {
       slot.h = h;
-      st = stage_inputs(h, req->b.data(), req->has_x0 ? req->x0.data() : nullptr, false, S->s_admit);
+      st = stage_inputs(h, req->b.data(), req->has_x0 ? req->x0.data() : nullptr, false, stream);
       if (st == PPCG_OK) {
-        prepare_control(h, req->tol, req->maxit, S->s_admit);
-        cudaMemcpyAsync(h->d_desc, &h->desc, sizeof(SysDesc), cudaMemcpyHostToDevice, S->s_admit);
-        if (cudaStreamSynchronize(S->s_admit) != cudaSuccess) { cudaGetLastError(); st = PPCG_ERR_CUDA; }
+        prepare_control(h, req->tol, req->maxit, stream);
+        cudaMemcpyAsync(h->d_desc, &h->desc, sizeof(SysDesc), cudaMemcpyHostToDevice, stream);
+        if (cudaStreamSynchronize(stream) != cudaSuccess) { cudaGetLastError(); st = PPCG_ERR_CUDA; }
       }
     }
     if (st != PPCG_OK || req->n == 0) {
@@ -297,14 +317,16 @@ ppcg_status ppcg_server_create(ppcg_server* server, size_t hbm_budget, const ppc
     return PPCG_ERR_CUDA;
   }
   S->budget = hbm_budget ? hbm_budget : (size_t)(0.9 * (double)fr);
-  if (cudaStreamCreateWithFlags(&S->s_admit, cudaStreamNonBlocking) != cudaSuccess ||
+  if (cudaStreamCreateWithFlags(&S->s_admit[0], cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&S->s_admit[1], cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&S->s_exec, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     delete S;
     set_error("ppcg_server_create: stream creation failed");
     return PPCG_ERR_CUDA;
   }
-  S->admitter = std::thread(admit_loop, S);
+  S->admitter[0] = std::thread(admit_loop, S, 0);
+  S->admitter[1] = std::thread(admit_loop, S, 1);
   S->executor = std::thread(exec_loop, S);
   *server = S;
   return PPCG_OK;
@@ -378,12 +400,14 @@ void ppcg_server_destroy(ppcg_server S) {
   }
   S->cv_admit.notify_all();
   S->cv_exec.notify_all();
-  if (S->admitter.joinable()) S->admitter.join();
+  for (std::thread& t : S->admitter)
+    if (t.joinable()) t.join();
   if (S->executor.joinable()) S->executor.join();
   for (Slot& s : S->ready) ppcg_destroy(s.h);
   cudaFree(S->d_descs);
   cudaFree(S->d_lists);
-  cudaStreamDestroy(S->s_admit);
+  cudaStreamDestroy(S->s_admit[0]);
+  cudaStreamDestroy(S->s_admit[1]);
   cudaStreamDestroy(S->s_exec);
   delete S;
 }

@@ -327,6 +327,32 @@ def test_server_results_same_alone_and_in_mix(precision):
     assert np.array_equal(xs.cpu().numpy(), alone[0][1])
 
 
+def test_server_large_and_small_requests_admitted_side_by_side():
+    """A whole-GPU-path request (216,000 rows, above the cluster path's 131,072) submitted
+    together with small ones: the two admission threads take them side by side; every result
+    is OK and bitwise the same as the same request served alone, and the HBM accounting
+    returns to zero."""
+    m = pp()
+    big = synth.varcoeff3d(60, seed=12)
+    systems = [(big, synth.rhs_uniform(big.n, 12))] + _batch_systems()[:5]
+    alone = []
+    srv = m.Server(precision=m.FP32_RU, epoch_iters=64)
+    for a, b in systems:
+        t = srv.submit(a, b, tol=1e-8, maxit=20000)
+        alone.append(_wait(srv, [t], {t: a.n})[t])
+    srv.close()
+    srv = m.Server(precision=m.FP32_RU, epoch_iters=64)
+    tickets = [srv.submit(a, b, tol=1e-8, maxit=20000) for a, b in systems]
+    mix = _wait(srv, tickets, {t: a.n for t, (a, _) in zip(tickets, systems)})
+    assert srv.stats()["hbm_in_use"] == 0 and srv.stats()["completed"] == len(systems)
+    srv.close()
+    for (a, b), (st0, x0, i0), t in zip(systems, alone, tickets):
+        st1, x1, i1 = mix[t]
+        assert st0 == st1 == m.OK, (a.n, i0, i1)
+        assert i0.iters == i1.iters and np.array_equal(x0, x1), a.n
+        assert np.linalg.norm(b - a.to_scipy() @ x1) / np.linalg.norm(b) <= 1e-8
+
+
 def test_injected_allocation_failures_are_reported_and_recovered(monkeypatch):
     """Host-side fault injection (no GPU fault): every device allocation of ppcg_create is
     made to fail in turn; each attempt returns PPCG_ERR_OOM without crashing or leaking into
