@@ -2415,7 +2415,10 @@ __global__ void __launch_bounds__(kClusterThreads, 4) k_cluster(const SysDesc* d
 // those of the other paths; the vector tiles are loaded at launch and written back at exit,
 // so a solve can stop at an iteration budget and resume in a later launch.
 
-constexpr int kOnchipThreads = 256;
+// Eight warps work on the local chunks; a ninth (kOnchipCtl) owns none: it reduces the
+// cluster's partials and runs the control step while the others compute, for the iteration
+// that follows, the product of their first chunk (see k_onchip).
+constexpr int kOnchipWork = 8, kOnchipCtl = kOnchipWork, kOnchipThreads = (kOnchipWork + 1) * 32;
 
 
 // Gather of one slot of the distributed vector tiles: row j is lane j % 32 of chunk j / 32,
@@ -2476,10 +2479,26 @@ struct Onchip {
   int32_t nc, lg;        // cluster size and its log2
 };
 
-#define FOR_LOCAL(O) for (int32_t lc = (int32_t)(threadIdx.x >> 5); lc < (O).nloc; lc += kOnchipThreads / 32)
+// Local chunks of this warp: lc = warp, warp + 8, ...; the control warp takes none.
+#define FOR_LOCAL(O) \
+  for (int32_t lc = (int32_t)(threadIdx.x >> 5); lc < (O).nloc && (threadIdx.x >> 5) < kOnchipWork; lc += kOnchipWork)
 
-// One on-chip pass; returns whether it produced partials.
-__device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dots<double>& d, bool paper) {
+// The product n = Ahat w of local chunk lc, w in slot ws, for its rows (the first part of
+// P_ITER; the same FMA sequence).
+__device__ __forceinline__ double onchip_product(const Onchip& O, int32_t lc, int ws) {
+  const int lane = threadIdx.x & 31;
+  const int32_t c = lc * O.nc + O.rank;
+  const bool in = c * kChunk + lane < O.n;
+  const double* t = O.tile + (int64_t)lc * kNS64 * kChunk + lane;
+  const int base = O.lptr[lc] + lane, len = (O.lptr[lc + 1] - O.lptr[lc]) / kChunk;
+  const GatherDS gw{O.tile_addr, ws, (uint32_t)O.lg};
+  return row_dot_sm<false>(O.col, O.val, gw, nullptr, base, len, in ? t[ws * kChunk] : 0.0);
+}
+
+// One on-chip pass; returns whether it produced partials.  spec: the product of this warp's
+// first local chunk for this P_ITER, computed ahead (see k_onchip).
+__device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dots<double>& d, bool paper,
+                            bool spec_ok = false, double spec = 0.0) {
   const int lane = threadIdx.x & 31;
   const DevMatrix& A = S.A;
   switch (C.pass) {
@@ -2573,7 +2592,8 @@ __device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dot
         double wi = 0.0;
         if (in) wi = t[wcs * kChunk];
         // n_i = (A M^-1 w)_i = w_i + sum_{j != i} ahat_ij w_j
-        const double ni = row_dot_sm<false>(O.col, O.val, gw, nullptr, base, len, wi);
+        const double ni = spec_ok && lc == (int32_t)(threadIdx.x >> 5) ? spec
+                                                                        : row_dot_sm<false>(O.col, O.val, gw, nullptr, base, len, wi);
         if (in) {
           const double id = t[V_INVD * kChunk], ui = t[V_U * kChunk];
           const double mi = id * wi;
@@ -2694,36 +2714,56 @@ __global__ void __launch_bounds__(kOnchipThreads, 1) k_onchip(const SysDesc* des
     const bool paper = S.norm == PPCG_NORM_PAPER_U_ABS;
     __syncthreads();
     cluster_barrier();   // every CTA's tiles are staged before anyone gathers
+    // Speculative product: after a P_ITER pass, while warp kOnchipCtl reduces the partials
+    // and runs the control step, each working warp forms the product its first local chunk
+    // needs in the next iteration (slot wns of the pass just done is that iteration's w).
+    // It is used when the control step indeed continues with P_ITER of that iteration;
+    // nothing can have written the slot in between: the one pass another CTA may run
+    // meanwhile is the one that control step chose (P_ITER, P_NORM, P_GAP, P_TRUE or P_RR1),
+    // and none of them writes wns of the iteration before.
+    const int warp = (int)(threadIdx.x >> 5);
+    bool spec_ok = false;
+    double spec = 0.0;
+    int spec_iter = -1;
     for (;;) {
-      if (threadIdx.x == 0) control(C, S, iter_end);
+      if (threadIdx.x == kOnchipCtl * 32) control(C, S, iter_end);
       __syncthreads();
       if (C.pass == P_NONE) break;
+      const int pass = C.pass, iter = C.iter;
       Dots<double> d;
-      const bool partials = onchip_pass(S, C, O, d, paper);
+      const bool use = spec_ok && pass == P_ITER && iter == spec_iter;
+      const bool partials = onchip_pass(S, C, O, d, paper, use, spec);
       if (partials) {
         write_block_partials<true>(d.get(0), d.get(1), d.get(2), sh.part[C.parity], sh.sm);
       }
       __syncthreads();
       cluster_barrier();
-      if (partials && threadIdx.x < 32) {
-        // lane q < NC reads rank q's partials; a fixed shuffle tree sums them (deterministic)
-        const int lane = threadIdx.x;
-        const uint32_t base = smem_u32(&sh.part[C.parity][0]);
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        if (lane < O.nc) {
-          s0 = ld_dsmem(base, lane);
-          s1 = ld_dsmem(base + 8, lane);
-          s2 = ld_dsmem(base + 16, lane);
+      spec_ok = false;
+      if (warp == kOnchipCtl) {
+        if (partials) {
+          // lane q < NC reads rank q's partials; a fixed shuffle tree sums them (deterministic)
+          const int lane = threadIdx.x & 31;
+          const uint32_t base = smem_u32(&sh.part[C.parity][0]);
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+          if (lane < O.nc) {
+            s0 = ld_dsmem(base, lane);
+            s1 = ld_dsmem(base + 8, lane);
+            s2 = ld_dsmem(base + 16, lane);
+          }
+          for (int o = O.nc / 2; o > 0; o >>= 1) {
+            s0 += __shfl_down_sync(kFull, s0, o);
+            s1 += __shfl_down_sync(kFull, s1, o);
+            s2 += __shfl_down_sync(kFull, s2, o);
+          }
+          if (lane == 0) {
+            C.red[0] = s0; C.red[1] = s1; C.red[2] = s2; C.red[3] = 0.0;
+            C.parity ^= 1;
+          }
         }
-        for (int o = O.nc / 2; o > 0; o >>= 1) {
-          s0 += __shfl_down_sync(kFull, s0, o);
-          s1 += __shfl_down_sync(kFull, s1, o);
-          s2 += __shfl_down_sync(kFull, s2, o);
-        }
-        if (lane == 0) {
-          C.red[0] = s0; C.red[1] = s1; C.red[2] = s2; C.red[3] = 0.0;
-          C.parity ^= 1;
-        }
+      } else if (pass == P_ITER && warp < O.nloc && warp * O.nc + O.rank < O.nchunks) {
+        spec = onchip_product(O, warp, (iter & 1) ? V_WA : V_WB);
+        spec_ok = true;
+        spec_iter = iter + 1;
       }
     }
     cluster_barrier();   // no CTA reads another's shared memory after this point
