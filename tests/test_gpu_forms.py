@@ -353,6 +353,42 @@ def test_server_large_and_small_requests_admitted_side_by_side():
         assert np.linalg.norm(b - a.to_scipy() @ x1) / np.linalg.norm(b) <= 1e-8
 
 
+def test_server_keeps_arrival_order_under_memory_pressure():
+    """Admission by class: a small request A (long-running) is resident; a large request B
+    (above the cluster path's 131,072 rows) does not fit beside A in the budget, a small one
+    C would.  B arrived first, so C is not admitted while B waits for memory: as long as A
+    runs, one request runs and the other two stay queued.  Then B and C are served."""
+    m = pp()
+
+    def footprint(a):      # the library's FP64 admission estimate (ppcg_create's layout)
+        slots = 1.05 * a.nnz + 32.0 * (a.n / 32.0 + 1.0)
+        return int(slots * 13 + a.n * 48 + a.n * 80) + (1 << 20)
+    A, B, C = synth.poisson2d(150), synth.varcoeff3d(52, seed=3), synth.poisson2d(30)
+    assert A.n <= 131072 < B.n and C.n <= 131072
+    budget = footprint(B) + (2 << 20)
+    assert footprint(A) + footprint(B) > budget and footprint(A) + footprint(C) <= budget
+    srv = m.Server(hbm_budget=budget, precision=m.FP64, epoch_iters=64)
+    ta = srv.submit(A, synth.rhs_uniform(A.n, 1), tol=0.0, maxit=20000)
+    tb = srv.submit(B, synth.rhs_uniform(B.n, 2), tol=1e-8, maxit=20000)
+    tc = srv.submit(C, synth.rhs_uniform(C.n, 3), tol=1e-8, maxit=20000)
+    samples = 0
+    t0 = time.time()
+    while time.time() - t0 < 120.0:
+        st = srv.stats()
+        a_st, _, _ = srv.poll(ta, A.n)
+        if a_st != m.PENDING:
+            break
+        # A still runs, so it ran when stats() was taken: B cannot fit, and C may not pass it
+        assert st["running"] <= 1, st
+        samples += 1
+        time.sleep(0.001)
+    assert samples > 0
+    res = _wait(srv, [tb, tc], {tb: B.n, tc: C.n})
+    assert res[tb][0] == m.OK and res[tc][0] == m.OK
+    assert srv.stats()["hbm_in_use"] == 0
+    srv.close()
+
+
 def test_injected_allocation_failures_are_reported_and_recovered(monkeypatch):
     """Host-side fault injection (no GPU fault): every device allocation of ppcg_create is
     made to fail in turn; each attempt returns PPCG_ERR_OOM without crashing or leaking into
