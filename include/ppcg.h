@@ -301,7 +301,7 @@ void ppcg_destroy(ppcg_handle handle);
  * while others run join at the next epoch.  opts may be NULL.  With opts->path ==
  * PPCG_PATH_AUTO and the default cluster_max_rows, requests of up to 131,072 rows run on
  * the CLUSTER path (all of them share one launch per epoch) and larger ones on the GRID
- * path (the two oldest advance each epoch by a slice of about 20 ms); the ONCHIP path is
+ * path (the two oldest advance each epoch by a slice of about 5-10 ms); the ONCHIP path is
  * not used by the server.  Each epoch runs the cluster launch first and then those slices.
  * A small request therefore never waits for a large solve to finish, nor for the copy and
  * conversion of a large request's matrix: once admitted, it waits at most for the slices

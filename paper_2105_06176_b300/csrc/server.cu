@@ -13,7 +13,7 @@
 //                epoch_iters * 131072 / n iterations (clamped to [2, 64 epoch_iters]), so
 //                each gets about the same device time and their work overlaps; GRID-path
 //                solves run in arrival order, the two oldest getting a whole-GPU slice of
-//                clamp(2.5e8 / n, 32, 4000) iterations (about 20 ms) per epoch; finished
+//                clamp(2.5e8 / n, 32, 4000) iterations (2.5e8 row-iterations, about 5-10 ms) per epoch; finished
 //                solves are copied out, their memory released, and requests that arrived
 //                meanwhile join at the next epoch.
 // A solve's vectors, scalars and control block stay on the device between epochs, and its
@@ -250,8 +250,10 @@ void exec_loop(ppcg_srv* S) {
     std::vector<Slot*> cl, gr;
     for (Slot& s : active) (s.h->path == PPCG_PATH_CLUSTER ? cl : gr).push_back(&s);
     bool ok = run_cluster_epoch(S, cl);
-    // Whole-GPU solves in arrival order: the two oldest each get a slice of about 20 ms of
-    // streaming work (iterations inversely proportional to their size); later ones wait.
+    // Whole-GPU solves in arrival order: the two oldest each get a slice of 2.5e8
+    // row-iterations (about 5-10 ms of streaming work); later ones wait.  Slices four times
+    // as long left the large requests' p99 where it was (their own solve time sets it) and
+    // doubled the small requests' median.
     for (size_t k = 0; k < gr.size() && k < 2; k++) {
       Slot* s = gr[k];
       const double n = (double)std::max<int64_t>(s->h->n, 1);
