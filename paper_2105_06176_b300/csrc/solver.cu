@@ -350,11 +350,12 @@ __device__ __forceinline__ T row_dot(const CS& col, const T* __restrict__ val, c
                                      const T* __restrict__ dsc, int64_t base, int len, T acc) {
   if constexpr (std::is_same<CS, const int32_t*>::value && !SCALE && sizeof(T) == 8)
     return row_dot_cols(col, val, x, base, len, acc);
-  if constexpr (std::is_same<CS, ColPat>::value && sizeof(T) == 4) {
-    // FP32 rows of an offset-pattern matrix: batches of 4 slots (columns cost nothing to
-    // form, so a narrower batch adds no dependent column load, and it frees the registers
-    // the FP32 pass's double-float dot accumulators need: 256^3 FP32_RU solve 380 -> 347 ms;
-    // the FP64 pass is 0.6% faster with the wide batches below).  Same terms, same order.
+  if constexpr (sizeof(T) == 4) {
+    // FP32 rows: batches of 4 slots, which free the registers the FP32 pass's double-float
+    // dot accumulators need (offset pattern, 256^3 FP32_RU solve 380 -> 347 ms; stored
+    // columns, 4M-point graph 225 -> 215 ms; column dictionary, 125-point box 165^3 180 ->
+    // 175 ms); the FP64 pass is 0.6% faster with the wide batches below.  Same terms, same
+    // order.
     int j = 0;
     for (; j + 4 <= len; j += 4) {
       T a[4];
