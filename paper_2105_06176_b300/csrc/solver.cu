@@ -301,46 +301,46 @@ template <> struct Cols<kColPat> {
 // acc + sum_j val[slot_j] * x(col[slot_j]) (* dsc[col] when SCALE) over the row's
 // off-diagonal slots base + j*32, j < len, in CSR order; acc enters holding the diagonal
 // term.  CS: the column source (const int32_t* or ColDict).
-// FP64 rows with stored columns: batches of 8 slots, the next batch's columns loaded before
+// FP64 rows with stored columns: batches of 6 slots, the next batch's columns loaded before
 // the current batch's gathers, so a column load no longer waits behind the gathers of the
-// batch before it (4M-point graph FP64 solve 2.5% faster; the FP32 pass, whose accumulators
-// take more registers, ran 3% slower, and 12-slot batches 8% slower).  Same terms in the
-// same order as row_dot.
+// batch before it.  4M-point graph FP64 solve to 1e-8 with 5 / 6 / 7 / 8-slot batches: 281 /
+// 251 / 260 / 267 ms (12-slot batches without the early columns 8% slower than 8; the FP32
+// pass takes its own 4-slot batches).  Same terms in the same order as row_dot.
 template <typename T, class G>
 __device__ __forceinline__ T row_dot_cols(const int32_t* __restrict__ col, const T* __restrict__ val, const G& x,
                                           int64_t base, int len, T acc) {
   int j = 0;
-  int32_t cn[8];
-  if (len >= 8) {
+  int32_t cn[6];
+  if (len >= 6) {
 #pragma unroll
-    for (int k = 0; k < 8; k++) cn[k] = ld_stream(col + base + (int64_t)k * kChunk);
+    for (int k = 0; k < 6; k++) cn[k] = ld_stream(col + base + (int64_t)k * kChunk);
   }
-  for (; j + 8 <= len; j += 8) {
-    int32_t c[8];
-    T a[8];
+  for (; j + 6 <= len; j += 6) {
+    int32_t c[6];
+    T a[6];
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
+    for (int k = 0; k < 6; k++) {
       c[k] = cn[k];
       a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
-    if (j + 16 <= len) {
+    if (j + 12 <= len) {
 #pragma unroll
-      for (int k = 0; k < 8; k++) cn[k] = ld_stream(col + base + (int64_t)(j + 8 + k) * kChunk);
+      for (int k = 0; k < 6; k++) cn[k] = ld_stream(col + base + (int64_t)(j + 6 + k) * kChunk);
     }
 #pragma unroll
-    for (int k = 0; k < 8; k++) acc = fma(a[k], x(c[k]), acc);
+    for (int k = 0; k < 6; k++) acc = fma(a[k], x(c[k]), acc);
   }
-  int32_t c[7];
-  T a[7];
+  int32_t c[5];
+  T a[5];
 #pragma unroll
-  for (int k = 0; k < 7; k++) {
+  for (int k = 0; k < 5; k++) {
     if (j + k < len) {
       c[k] = ld_stream(col + base + (int64_t)(j + k) * kChunk);
       a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
     }
   }
 #pragma unroll
-  for (int k = 0; k < 7; k++)
+  for (int k = 0; k < 5; k++)
     if (j + k < len) acc = fma(a[k], x(c[k]), acc);
   return acc;
 }
