@@ -351,18 +351,21 @@ __device__ __forceinline__ T row_dot(const CS& col, const T* __restrict__ val, c
   if constexpr (std::is_same<CS, const int32_t*>::value && !SCALE && sizeof(T) == 8)
     return row_dot_cols(col, val, x, base, len, acc);
   if constexpr (sizeof(T) == 4) {
-    // FP32 rows: batches of 4 slots, which free the registers the FP32 pass's double-float
-    // dot accumulators need (offset pattern, 256^3 FP32_RU solve 380 -> 347 ms; stored
-    // columns, 4M-point graph 225 -> 215 ms; column dictionary, 125-point box 165^3 180 ->
-    // 175 ms); the FP64 pass is 0.6% faster with the wide batches below.  Same terms, same
-    // order.
+    // FP32 rows: narrow batches, which free the registers the FP32 pass's double-float dot
+    // accumulators need.  4 slots (8 before): offset pattern, 256^3 FP32_RU solve 380 -> 347
+    // ms; stored columns, 4M-point graph 225 -> 215 ms; column dictionary, 125-point box
+    // 165^3 180 -> 175 ms.  Offset-pattern rows take 3 (344 -> 333 ms at 256^3, whose six
+    // slots make two full batches; a 2048^2 2-D system with four slots is unchanged);
+    // stored columns stay at 4 (3 / 5 / 6 slots: 7% / 2% / 4% slower).  The FP64 pass is
+    // 0.6% faster with the wide batches below.  Same terms, same order.
+    constexpr int FB = std::is_same<CS, ColPat>::value ? 3 : 4;
     int j = 0;
-    for (; j + 4 <= len; j += 4) {
-      T a[4];
+    for (; j + FB <= len; j += FB) {
+      T a[FB];
 #pragma unroll
-      for (int k = 0; k < 4; k++) a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
+      for (int k = 0; k < FB; k++) a[k] = ld_stream(val + base + (int64_t)(j + k) * kChunk);
 #pragma unroll
-      for (int k = 0; k < 4; k++) {
+      for (int k = 0; k < FB; k++) {
         const int32_t c = slot_col(col, base + (int64_t)(j + k) * kChunk, j + k);
         T xv = x(c);
         if (SCALE) xv = __ldg(dsc + c) * xv;
@@ -370,7 +373,7 @@ __device__ __forceinline__ T row_dot(const CS& col, const T* __restrict__ val, c
       }
     }
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < FB - 1; k++) {
       if (j + k < len) {
         const T a = ld_stream(val + base + (int64_t)(j + k) * kChunk);
         const int32_t c = slot_col(col, base + (int64_t)(j + k) * kChunk, j + k);
