@@ -2524,10 +2524,26 @@ __device__ __forceinline__ double onchip_product(const Onchip& O, int32_t lc, in
   return row_dot_sm<false>(O.col, O.val, gw, nullptr, base, len, in ? t[ws * kChunk] : 0.0);
 }
 
-// One on-chip pass; returns whether it produced partials.  spec: the product of this warp's
-// first local chunk for this P_ITER, computed ahead (see k_onchip).
+// Products of a warp's first local chunks, formed ahead (see k_onchip): at most kOnchipSpec
+// chunks, and beyond the first only while their slots add up to kOnchipSpecSlots -- about
+// what fits in the control step's time.  4 chunks of a 3-D 24^3 stencil (6 slots each):
+// solve 1289 -> 1110 us; 2 chunks of an 8k-point graph (~20 slots each) made it 2.7% slower.
+constexpr int kOnchipSpec = 4, kOnchipSpecSlots = 24;
+struct OnchipSpec {
+  int n;                 // chunks formed
+  double v[kOnchipSpec];
+  __device__ __forceinline__ double get(int i) const {   // i < kOnchipSpec, register-resident
+    double r = v[0];
+#pragma unroll
+    for (int k = 1; k < kOnchipSpec; k++) r = i == k ? v[k] : r;
+    return r;
+  }
+};
+
+// One on-chip pass; returns whether it produced partials.  spec: the products of this warp's
+// first local chunks for this P_ITER, computed ahead (see k_onchip).
 __device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dots<double>& d, bool paper,
-                            bool spec_ok = false, double spec = 0.0) {
+                            bool spec_ok = false, const OnchipSpec* spec = nullptr) {
   const int lane = threadIdx.x & 31;
   const DevMatrix& A = S.A;
   switch (C.pass) {
@@ -2621,8 +2637,9 @@ __device__ bool onchip_pass(const SysDesc& S, const Ctl& C, const Onchip& O, Dot
         double wi = 0.0;
         if (in) wi = t[wcs * kChunk];
         // n_i = (A M^-1 w)_i = w_i + sum_{j != i} ahat_ij w_j
-        const double ni = spec_ok && lc == (int32_t)(threadIdx.x >> 5) ? spec
-                                                                        : row_dot_sm<false>(O.col, O.val, gw, nullptr, base, len, wi);
+        const int si = (lc - (int32_t)(threadIdx.x >> 5)) / kOnchipWork;   // this warp's i-th chunk
+        const double ni = spec_ok && si < spec->n ? spec->get(si)
+                                                      : row_dot_sm<false>(O.col, O.val, gw, nullptr, base, len, wi);
         if (in) {
           const double id = t[V_INVD * kChunk], ui = t[V_U * kChunk];
           const double mi = id * wi;
@@ -2743,16 +2760,17 @@ __global__ void __launch_bounds__(kOnchipThreads, 1) k_onchip(const SysDesc* des
     const bool paper = S.norm == PPCG_NORM_PAPER_U_ABS;
     __syncthreads();
     cluster_barrier();   // every CTA's tiles are staged before anyone gathers
-    // Speculative product: after a P_ITER pass, while warp kOnchipCtl reduces the partials
-    // and runs the control step, each working warp forms the product its first local chunk
-    // needs in the next iteration (slot wns of the pass just done is that iteration's w).
+    // Speculative products: after a P_ITER pass, while warp kOnchipCtl reduces the partials
+    // and runs the control step, each working warp forms the products its first
+    // kOnchipSpec local chunks need in the next iteration (slot wns of the pass just done is
+    // that iteration's w), in registers.
     // It is used when the control step indeed continues with P_ITER of that iteration;
     // nothing can have written the slot in between: the one pass another CTA may run
     // meanwhile is the one that control step chose (P_ITER, P_NORM, P_GAP, P_TRUE or P_RR1),
     // and none of them writes wns of the iteration before.
     const int warp = (int)(threadIdx.x >> 5);
     bool spec_ok = false;
-    double spec = 0.0;
+    OnchipSpec spec;
     int spec_iter = -1;
     for (;;) {
       if (threadIdx.x == kOnchipCtl * 32) control(C, S, iter_end);
@@ -2761,7 +2779,7 @@ __global__ void __launch_bounds__(kOnchipThreads, 1) k_onchip(const SysDesc* des
       const int pass = C.pass, iter = C.iter;
       Dots<double> d;
       const bool use = spec_ok && pass == P_ITER && iter == spec_iter;
-      const bool partials = onchip_pass(S, C, O, d, paper, use, spec);
+      const bool partials = onchip_pass(S, C, O, d, paper, use, &spec);
       if (partials) {
         write_block_partials<true>(d.get(0), d.get(1), d.get(2), sh.part[C.parity], sh.sm);
       }
@@ -2789,8 +2807,18 @@ __global__ void __launch_bounds__(kOnchipThreads, 1) k_onchip(const SysDesc* des
             C.parity ^= 1;
           }
         }
-      } else if (pass == P_ITER && warp < O.nloc && warp * O.nc + O.rank < O.nchunks) {
-        spec = onchip_product(O, warp, (iter & 1) ? V_WA : V_WB);
+      } else if (pass == P_ITER) {
+        spec.n = 0;
+        int slots = 0;
+#pragma unroll
+        for (int i = 0; i < kOnchipSpec; i++) {
+          const int32_t lc = warp + i * kOnchipWork;
+          if (lc >= O.nloc || lc * O.nc + O.rank >= O.nchunks) break;
+          slots += (O.lptr[lc + 1] - O.lptr[lc]) / kChunk;
+          if (i > 0 && slots > kOnchipSpecSlots) break;
+          spec.v[i] = onchip_product(O, lc, (iter & 1) ? V_WA : V_WB);
+          spec.n = i + 1;
+        }
         spec_ok = true;
         spec_iter = iter + 1;
       }
