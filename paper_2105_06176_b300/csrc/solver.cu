@@ -82,7 +82,8 @@ struct GridGroup {
 };
 
 // One thread-block cluster.  barrier.cluster with release/acquire orders the global
-// writes of each pass before the next pass's gathers (which use ld.global.cg, L2).
+// writes of each pass before the next pass's gathers (which may then be served by L1; see
+// GatherSlot).
 // Distributed shared memory of a thread-block cluster.
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
