@@ -13,9 +13,9 @@
 //                epoch_iters * 131072 / n iterations (clamped to [2, 64 epoch_iters]), so
 //                each gets about the same device time and their work overlaps; GRID-path
 //                solves run in arrival order, the two oldest getting a whole-GPU slice of
-//                clamp(2.5e8 / n, 32, 4000) iterations (2.5e8 row-iterations, about 5-10 ms) per epoch; finished
-//                solves are copied out, their memory released, and requests that arrived
-//                meanwhile join at the next epoch.
+//                clamp(2.5e8 / n, 32, 4000) iterations (2.5e8 row-iterations, about 5-10
+//                ms) per epoch; finished solves are copied out, their memory released, and
+//                requests that arrived meanwhile join at the next epoch.
 // A solve's vectors, scalars and control block stay on the device between epochs, and its
 // partition over CTAs depends only on its handle, so a result is bitwise the same alone or
 // in any mix.
